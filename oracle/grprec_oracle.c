@@ -1,0 +1,838 @@
+/*
+ * ORACLE — test infrastructure only; see grprec_oracle.h.
+ *
+ * Plain FP64, no blocking, no fusion: every function follows one passage of
+ * the paper (arXiv 2602.21911) or a textbook definition, cited beside it, in
+ * the order the method states it.  Readings of points the paper leaves open
+ * are marked READING and listed in the design notes of the repository.
+ *
+ * Built with -O2 -ffp-contract=off so that x86 and Arm hosts give the same
+ * bits.  The file is valid C99 and C++ (an op-counting build includes it with
+ * `real` defined as a counting type).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include "grprec_oracle.h"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef OR_REAL_DEFINED
+typedef double real;
+#endif
+
+#define MAXM 4
+#define MAXC 3
+#ifndef OR_MAX_REPAIR
+#define OR_MAX_REPAIR 4
+#endif
+
+/* ------------------------------------------------------------------------- */
+/* Small dense linear algebra: Gaussian elimination with partial pivoting.   */
+/* ------------------------------------------------------------------------- */
+static int solve_dense(int n, real *A /* n*n row-major, destroyed */, real *x /* rhs in, sol out */)
+{
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    real best = fabs(A[k * n + k]);
+    for (int r = k + 1; r < n; ++r) {
+      real v = fabs(A[r * n + k]);
+      if (v > best) { best = v; piv = r; }
+    }
+    if (!(best > 0)) return -1;
+    if (piv != k) {
+      for (int c = 0; c < n; ++c) { real tmp = A[k * n + c]; A[k * n + c] = A[piv * n + c]; A[piv * n + c] = tmp; }
+      real tmp = x[k]; x[k] = x[piv]; x[piv] = tmp;
+    }
+    for (int r = k + 1; r < n; ++r) {
+      real f = A[r * n + k] / A[k * n + k];
+      for (int c = k; c < n; ++c) A[r * n + c] = A[r * n + c] - f * A[k * n + c];
+      x[r] = x[r] - f * x[k];
+    }
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    real s = x[k];
+    for (int c = k + 1; c < n; ++c) s = s - A[k * n + c] * x[c];
+    x[k] = s / A[k * n + k];
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Section 3.1, GRPrec.  Polynomial p(xi) = sum_k coef[k] xi^k on cell i,     */
+/* xi = (x - x_i)/dx in [-1/2, 1/2].  Every condition of the paper is a row:  */
+/*   point value  p(xi0)                    -> [xi0^k]                        */
+/*   cell average (1/dx) int p dx over [a,b] -> [(b^{k+1}-a^{k+1})/(k+1)]      */
+/* ------------------------------------------------------------------------- */
+static void row_point(int M, real xi0, real *row)
+{
+  real v = 1;
+  for (int k = 0; k <= M; ++k) { row[k] = v; v = v * xi0; }
+}
+
+static void row_average(int M, real a, real b, real *row)
+{
+  real pa = a, pb = b;
+  for (int k = 0; k <= M; ++k) { row[k] = (pb - pa) / (k + 1); pa = pa * a; pb = pb * b; }
+}
+
+/*
+ * Degree 1 (first-degree paragraph of Section 3.1): least squares on the two
+ *   interface values, cell-i conservation held by a Lagrange multiplier.
+ * Degree 2: both interface values and cell-i conservation imposed exactly.
+ * Degree 3: least squares on the two interface values and the averages of
+ *   cells i-1 and i+1, cell-i conservation by a Lagrange multiplier.
+ * Degree 4: both interface values and conservation in cells i-1, i, i+1.
+ * READING: the least-squares terms are unweighted, exactly as the functionals
+ * are printed.  The minimiser of |A c - b|^2 subject to C c = d solves the
+ * KKT system [2 A^T A, -C^T; C, 0] [c; mu] = [2 A^T b; d].
+ */
+int or_recon(int M, const double *qbar, const double *g, double *coef)
+{
+  real Arows[4][MAXM + 1], b[4];
+  real Crows[5][MAXM + 1], d[5];
+  int nA = 0, nC = 0;
+  const real half = 0.5, three_half = 1.5;
+  if (M < 1 || M > MAXM) return -1;
+
+  if (M == 1 || M == 3) {
+    row_point(M, -half, Arows[nA]); b[nA++] = g[0];
+    row_point(M, half, Arows[nA]); b[nA++] = g[1];
+    if (M == 3) {
+      row_average(M, half, three_half, Arows[nA]); b[nA++] = qbar[2];
+      row_average(M, -three_half, -half, Arows[nA]); b[nA++] = qbar[0];
+    }
+    row_average(M, -half, half, Crows[nC]); d[nC++] = qbar[1];
+  } else {
+    row_point(M, -half, Crows[nC]); d[nC++] = g[0];
+    row_point(M, half, Crows[nC]); d[nC++] = g[1];
+    row_average(M, -half, half, Crows[nC]); d[nC++] = qbar[1];
+    if (M == 4) {
+      row_average(M, -three_half, -half, Crows[nC]); d[nC++] = qbar[0];
+      row_average(M, half, three_half, Crows[nC]); d[nC++] = qbar[2];
+    }
+  }
+
+  int nu = M + 1, n = nu + nC;
+  real K[(MAXM + 1 + 5) * (MAXM + 1 + 5)], rhs[MAXM + 1 + 5];
+  for (int i = 0; i < n * n; ++i) K[i] = 0;
+  for (int i = 0; i < n; ++i) rhs[i] = 0;
+  for (int r = 0; r < nu; ++r) {
+    for (int c = 0; c < nu; ++c) {
+      real s = 0;
+      for (int k = 0; k < nA; ++k) s = s + Arows[k][r] * Arows[k][c];
+      K[r * n + c] = 2 * s;
+    }
+    real s = 0;
+    for (int k = 0; k < nA; ++k) s = s + Arows[k][r] * b[k];
+    rhs[r] = 2 * s;
+    for (int j = 0; j < nC; ++j) K[r * n + nu + j] = -Crows[j][r];
+  }
+  for (int j = 0; j < nC; ++j) {
+    for (int c = 0; c < nu; ++c) K[(nu + j) * n + c] = Crows[j][c];
+    rhs[nu + j] = d[j];
+  }
+  if (solve_dense(n, K, rhs) != 0) return -1;
+  for (int k = 0; k <= M; ++k) coef[k] = rhs[k];
+  for (int k = M + 1; k <= MAXM; ++k) coef[k] = 0;
+  return 0;
+}
+
+/* k-th xi-derivative of the polynomial at xi0 */
+static real poly_deriv(int M, const real *coef, int k, real xi0)
+{
+  real s = 0;
+  for (int j = M; j >= k; --j) {
+    real fall = 1;
+    for (int r = 0; r < k; ++r) fall = fall * (j - r);
+    s = s * xi0 + coef[j] * fall;
+  }
+  return s;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Euler equations, ideal gas (Section 4.3): Q = (rho, rho u, E),            */
+/* F = (rho u, rho u^2 + p, u (E + p)), E = rho (u^2/2 + e), e = p/((g-1) rho) */
+/* ------------------------------------------------------------------------- */
+static void cons_to_prim(real gamma, const real *Q, real *W)
+{
+  real rho = Q[0];
+  real u = Q[1] / rho;
+  real p = (gamma - 1) * (Q[2] - 0.5 * Q[1] * u);
+  W[0] = rho; W[1] = u; W[2] = p;
+}
+
+static void prim_to_cons(real gamma, const real *W, real *Q)
+{
+  Q[0] = W[0];
+  Q[1] = W[0] * W[1];
+  Q[2] = W[2] / (gamma - 1) + 0.5 * W[0] * W[1] * W[1];
+}
+
+static void euler_flux(real gamma, const real *Q, real *F)
+{
+  real W[3];
+  cons_to_prim(gamma, Q, W);
+  F[0] = Q[1];
+  F[1] = Q[1] * W[1] + W[2];
+  F[2] = W[1] * (Q[2] + W[2]);
+}
+
+static int euler_admissible(real gamma, const real *Q)
+{
+  real W[3];
+  if (!(Q[0] > 0)) return 0;
+  cons_to_prim(gamma, Q, W);
+  return W[2] > 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Exact Riemann solver for the ideal gas (textbook solver; Section 4.1 takes */
+/* its interface data from classical Riemann solutions).                     */
+/* ------------------------------------------------------------------------- */
+/* pressure function f_K(p) and its derivative */
+static void pressure_function(real gamma, real p, const real *W, real c, real *f, real *df)
+{
+  real rhoK = W[0], pK = W[2];
+  if (p > pK) { /* shock */
+    real A = 2 / ((gamma + 1) * rhoK);
+    real B = (gamma - 1) / (gamma + 1) * pK;
+    real s = sqrt(A / (p + B));
+    *f = (p - pK) * s;
+    *df = s * (1 - (p - pK) / (2 * (B + p)));
+  } else { /* rarefaction */
+    real ratio = p / pK;
+    *f = 2 * c / (gamma - 1) * (pow(ratio, (gamma - 1) / (2 * gamma)) - 1);
+    *df = 1 / (rhoK * c) * pow(ratio, -(gamma + 1) / (2 * gamma));
+  }
+}
+
+/*
+ * Newton on f(p) = f_L(p) + f_R(p) + u_R - u_L.
+ * READING (the paper is silent): start from PVRS floored at 1e-14 max(pL,pR)
+ * (or from the two-rarefaction value, or from a given guess); stop when
+ * 2|p_{k+1}-p_k|/(p_{k+1}+p_k) < rtol and then take one more iteration; a
+ * non-positive iterate halves the step towards the previous iterate.
+ */
+static int star_pressure(real gamma, const real *WL, const real *WR, int guess_kind, real guess,
+                         real rtol, int max_iter, real *pstar, real *ustar, int *iters)
+{
+  real cL = sqrt(gamma * WL[2] / WL[0]);
+  real cR = sqrt(gamma * WR[2] / WR[0]);
+  real du = WR[1] - WL[1];
+  *iters = 0;
+  if (2 * (cL + cR) / (gamma - 1) <= du) return OR_VACUUM;
+
+  real p;
+  real pfloor = 1e-14 * (WL[2] > WR[2] ? WL[2] : WR[2]);
+  if (guess_kind == OR_GUESS_GIVEN && guess > 0 && isfinite((double)guess)) {
+    p = guess;
+  } else if (guess_kind == OR_GUESS_TRRS) {
+    real z = (gamma - 1) / (2 * gamma);
+    real num = cL + cR - 0.5 * (gamma - 1) * du;
+    real den = cL * pow(WL[2], -z) + cR * pow(WR[2], -z);
+    p = pow(num / den, 1 / z);
+  } else {
+    real ppv = 0.5 * (WL[2] + WR[2]) - 0.125 * du * (WL[0] + WR[0]) * (cL + cR);
+    p = ppv > pfloor ? ppv : pfloor;
+  }
+  if (!(p > pfloor)) p = pfloor;
+
+  int converged = 0, it = 0;
+  while (it < max_iter) {
+    real fL, dfL, fR, dfR;
+    pressure_function(gamma, p, WL, cL, &fL, &dfL);
+    pressure_function(gamma, p, WR, cR, &fR, &dfR);
+    real step = -(fL + fR + du) / (dfL + dfR);
+    real pn = p + step;
+    for (int h = 0; h < 64 && !(pn > 0); ++h) { step = 0.5 * step; pn = p + step; }
+    ++it;
+    real change = 2 * fabs(pn - p) / (pn + p);
+    p = pn;
+    if (converged) break;          /* the one extra iteration is done */
+    if (change < rtol) converged = 1;
+  }
+  *iters = it;
+  if (!converged) return OR_NEWTON_NO_CONV;
+  real fL, dfL, fR, dfR;
+  pressure_function(gamma, p, WL, cL, &fL, &dfL);
+  pressure_function(gamma, p, WR, cR, &fR, &dfR);
+  *pstar = p;
+  *ustar = 0.5 * (WL[1] + WR[1]) + 0.5 * (fR - fL);
+  return OR_OK;
+}
+
+/* Self-similar solution sampled at x/t = 0.  READING: u* = 0 takes the left side. */
+static void sample_at_zero(real gamma, const real *WL, const real *WR, real pstar, real ustar, real *W)
+{
+  real g1 = (gamma - 1) / (2 * gamma), g6 = (gamma - 1) / (gamma + 1);
+  if (ustar >= 0) {
+    real c = sqrt(gamma * WL[2] / WL[0]);
+    real ratio = pstar / WL[2];
+    if (pstar > WL[2]) {
+      real S = WL[1] - c * sqrt((gamma + 1) / (2 * gamma) * ratio + g1);
+      if (S >= 0) { W[0] = WL[0]; W[1] = WL[1]; W[2] = WL[2]; return; }
+      W[0] = WL[0] * (ratio + g6) / (g6 * ratio + 1); W[1] = ustar; W[2] = pstar; return;
+    }
+    real head = WL[1] - c;
+    if (head >= 0) { W[0] = WL[0]; W[1] = WL[1]; W[2] = WL[2]; return; }
+    real cstar = c * pow(ratio, g1);
+    real tail = ustar - cstar;
+    if (tail < 0) { W[0] = WL[0] * pow(ratio, 1 / gamma); W[1] = ustar; W[2] = pstar; return; }
+    /* inside the left fan, at the sonic ray */
+    real cs = 2 / (gamma + 1) * (c + (gamma - 1) / 2 * WL[1]);
+    W[0] = WL[0] * pow(cs / c, 2 / (gamma - 1));
+    W[1] = cs;
+    W[2] = WL[2] * pow(cs / c, 2 * gamma / (gamma - 1));
+    return;
+  }
+  real c = sqrt(gamma * WR[2] / WR[0]);
+  real ratio = pstar / WR[2];
+  if (pstar > WR[2]) {
+    real S = WR[1] + c * sqrt((gamma + 1) / (2 * gamma) * ratio + g1);
+    if (S <= 0) { W[0] = WR[0]; W[1] = WR[1]; W[2] = WR[2]; return; }
+    W[0] = WR[0] * (ratio + g6) / (g6 * ratio + 1); W[1] = ustar; W[2] = pstar; return;
+  }
+  real head = WR[1] + c;
+  if (head <= 0) { W[0] = WR[0]; W[1] = WR[1]; W[2] = WR[2]; return; }
+  real cstar = c * pow(ratio, g1);
+  real tail = ustar + cstar;
+  if (tail > 0) { W[0] = WR[0] * pow(ratio, 1 / gamma); W[1] = ustar; W[2] = pstar; return; }
+  real cs = 2 / (gamma + 1) * (c - (gamma - 1) / 2 * WR[1]);
+  W[0] = WR[0] * pow(cs / c, 2 / (gamma - 1));
+  W[1] = -cs;
+  W[2] = WR[2] * pow(cs / c, 2 * gamma / (gamma - 1));
+}
+
+/* Two rarefactions separated by vacuum (the data generate vacuum), sampled at
+ * x/t = 0 (textbook vacuum-generation solution). */
+static void sample_vacuum_at_zero(real gamma, const real *WL, const real *WR, real *W)
+{
+  real cL = sqrt(gamma * WL[2] / WL[0]), cR = sqrt(gamma * WR[2] / WR[0]);
+  real tailL = WL[1] + 2 * cL / (gamma - 1), tailR = WR[1] - 2 * cR / (gamma - 1);
+  if (WL[1] - cL >= 0) { W[0] = WL[0]; W[1] = WL[1]; W[2] = WL[2]; return; }
+  if (tailL > 0) {                  /* inside the left fan */
+    real cs = 2 / (gamma + 1) * (cL + (gamma - 1) / 2 * WL[1]);
+    W[0] = WL[0] * pow(cs / cL, 2 / (gamma - 1));
+    W[1] = cs;
+    W[2] = WL[2] * pow(cs / cL, 2 * gamma / (gamma - 1));
+    return;
+  }
+  if (WR[1] + cR <= 0) { W[0] = WR[0]; W[1] = WR[1]; W[2] = WR[2]; return; }
+  if (tailR < 0) {                  /* inside the right fan */
+    real cs = 2 / (gamma + 1) * (cR - (gamma - 1) / 2 * WR[1]);
+    W[0] = WR[0] * pow(cs / cR, 2 / (gamma - 1));
+    W[1] = -cs;
+    W[2] = WR[2] * pow(cs / cR, 2 * gamma / (gamma - 1));
+    return;
+  }
+  W[0] = 0; W[1] = 0; W[2] = 0;      /* vacuum */
+}
+
+/* Conserved state at x/t = 0.  With allow_vacuum, vacuum-generating data are
+ * sampled (status OR_VACUUM, Q valid); otherwise OR_VACUUM is a failure. */
+static int riemann_state(real gamma, const real *QL, const real *QR, int guess_kind, real guess,
+                         real rtol, int max_iter, int allow_vacuum, real *Q, int *iters)
+{
+  real WL[3], WR[3], W[3], ps, us;
+  cons_to_prim(gamma, QL, WL);
+  cons_to_prim(gamma, QR, WR);
+  int st = star_pressure(gamma, WL, WR, guess_kind, guess, rtol, max_iter, &ps, &us, iters);
+  if (st == OR_VACUUM && allow_vacuum) {
+    sample_vacuum_at_zero(gamma, WL, WR, W);
+    prim_to_cons(gamma, W, Q);
+    return OR_VACUUM;
+  }
+  if (st != OR_OK) return st;
+  sample_at_zero(gamma, WL, WR, ps, us, W);
+  prim_to_cons(gamma, W, Q);
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Derivative Riemann problems (Toro-Titarev solver, Section 2): linear RP    */
+/* d_t D + A(Q0) d_x D = 0, Godunov state at x/t = 0 in the eigenbasis.      */
+/* READING: a zero eigenvalue averages the two sides.                        */
+/* ------------------------------------------------------------------------- */
+static void deriv_rp(real gamma, const real *Q0, const real *DL, const real *DR, real *D)
+{
+  real W[3];
+  cons_to_prim(gamma, Q0, W);
+  real u = W[1], c = sqrt(gamma * W[2] / W[0]);
+  real H = (Q0[2] + W[2]) / W[0];
+  /* right eigenvectors of the Jacobian, as columns */
+  real R[9] = { 1, 1, 1,
+                u - c, u, u + c,
+                H - u * c, 0.5 * u * u, H + u * c };
+  real lam[3] = { u - c, u, u + c };
+  /* left eigenvectors: rows of R^{-1}, by elimination on R e_j */
+  real Linv[9];
+  for (int j = 0; j < 3; ++j) {
+    real A[9], e[3] = { 0, 0, 0 };
+    for (int i = 0; i < 9; ++i) A[i] = R[i];
+    e[j] = 1;
+    solve_dense(3, A, e);           /* column j of R^{-1} */
+    for (int i = 0; i < 3; ++i) Linv[i * 3 + j] = e[i];
+  }
+  for (int c0 = 0; c0 < 3; ++c0) D[c0] = 0;
+  for (int j = 0; j < 3; ++j) {
+    real wl = 0, wr = 0;
+    for (int k = 0; k < 3; ++k) { wl = wl + Linv[j * 3 + k] * DL[k]; wr = wr + Linv[j * 3 + k] * DR[k]; }
+    real w = lam[j] > 0 ? wl : (lam[j] < 0 ? wr : 0.5 * (wl + wr));
+    for (int k = 0; k < 3; ++k) D[k] = D[k] + R[k * 3 + j] * w;
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Cauchy-Kovalevskaya by truncated bivariate power series.                  */
+/* Q(x,tau) = sum_{a+b<=M} q[a][b] x^a tau^b; the PDE d_tau Q = -d_x F(Q)     */
+/* gives q[a][b+1] = -(a+1)/(b+1) f[a+1][b], the series of F built from the   */
+/* known q[.][<=b] by series products and the series quotient u = m/rho.     */
+/* ------------------------------------------------------------------------- */
+#define SIDX(a, b) ((a) * (MAXM + 1) + (b))
+
+static real series_product(const real *x, const real *y, int a, int b)
+{
+  real s = 0;
+  for (int i = 0; i <= a; ++i)
+    for (int j = 0; j <= b; ++j) s = s + x[SIDX(i, j)] * y[SIDX(a - i, b - j)];
+  return s;
+}
+
+static void ck_series(int system, real lambda, real gamma, int M, real q[][MAXC])
+{
+  if (system == OR_ADVECTION) {
+    for (int b = 0; b < M; ++b)
+      for (int a = 0; a + b + 1 <= M; ++a)
+        q[SIDX(a, b + 1)][0] = -(real)(a + 1) / (b + 1) * lambda * q[SIDX(a + 1, b)][0];
+    return;
+  }
+  real rho[(MAXM + 1) * (MAXM + 1)], m[(MAXM + 1) * (MAXM + 1)], E[(MAXM + 1) * (MAXM + 1)];
+  real u[(MAXM + 1) * (MAXM + 1)], mu[(MAXM + 1) * (MAXM + 1)], p[(MAXM + 1) * (MAXM + 1)];
+  real Ep[(MAXM + 1) * (MAXM + 1)], F[3][(MAXM + 1) * (MAXM + 1)];
+  for (int i = 0; i < (MAXM + 1) * (MAXM + 1); ++i) {
+    rho[i] = m[i] = E[i] = u[i] = mu[i] = p[i] = Ep[i] = 0;
+    F[0][i] = F[1][i] = F[2][i] = 0;
+  }
+  for (int b = 0; b < M; ++b) {
+    for (int a = 0; a + b <= M; ++a) {
+      rho[SIDX(a, b)] = q[SIDX(a, b)][0];
+      m[SIDX(a, b)] = q[SIDX(a, b)][1];
+      E[SIDX(a, b)] = q[SIDX(a, b)][2];
+    }
+    for (int a = 0; a + b <= M; ++a) {
+      /* series quotient: rho * u = m */
+      real s = m[SIDX(a, b)];
+      for (int i = 0; i <= a; ++i)
+        for (int j = 0; j <= b; ++j)
+          if (i || j) s = s - rho[SIDX(i, j)] * u[SIDX(a - i, b - j)];
+      u[SIDX(a, b)] = s / rho[SIDX(0, 0)];
+      mu[SIDX(a, b)] = series_product(m, u, a, b);
+      p[SIDX(a, b)] = (gamma - 1) * (E[SIDX(a, b)] - 0.5 * mu[SIDX(a, b)]);
+      Ep[SIDX(a, b)] = E[SIDX(a, b)] + p[SIDX(a, b)];
+      F[0][SIDX(a, b)] = m[SIDX(a, b)];
+      F[1][SIDX(a, b)] = mu[SIDX(a, b)] + p[SIDX(a, b)];
+      F[2][SIDX(a, b)] = series_product(u, Ep, a, b);
+    }
+    for (int a = 0; a + b + 1 <= M; ++a)
+      for (int c = 0; c < 3; ++c)
+        q[SIDX(a, b + 1)][c] = -(real)(a + 1) / (b + 1) * F[c][SIDX(a + 1, b)];
+  }
+}
+
+void or_ck_series(int system, double lambda, double gamma, int M, const double *qa0, double *qout)
+{
+  int C = system == OR_EULER ? 3 : 1;
+  real q[(MAXM + 1) * (MAXM + 1)][MAXC];
+  for (int i = 0; i < (MAXM + 1) * (MAXM + 1); ++i) q[i][0] = q[i][1] = q[i][2] = 0;
+  for (int a = 0; a <= M; ++a)
+    for (int c = 0; c < C; ++c) q[SIDX(a, 0)][c] = qa0[a * C + c];
+  ck_series(system, lambda, gamma, M, q);
+  for (int a = 0; a <= M; ++a)
+    for (int b = 0; b <= M; ++b)
+      for (int c = 0; c < C; ++c) qout[(a * (M + 1) + b) * C + c] = q[SIDX(a, b)][c];
+}
+
+/* ------------------------------------------------------------------------- */
+/* One GRP_m at an interface (Toro-Titarev structure, Section 2) and its flux */
+/* time integral (numerical flux definition, Section 2).                     */
+/* READING: G = ceil((M+1)/2) Gauss-Legendre points on [0, dt]; the interface */
+/* datum written back is the Taylor value at tau = dt.                       */
+/* ------------------------------------------------------------------------- */
+static int gauss_rule(int M, real *s, real *w)
+{
+  int G = (M + 2) / 2;
+  if (G == 1) { s[0] = 0; w[0] = 1; }
+  else if (G == 2) { s[0] = -1 / sqrt((real)3); s[1] = 1 / sqrt((real)3); w[0] = w[1] = 0.5; }
+  else { s[0] = -sqrt((real)0.6); s[1] = 0; s[2] = sqrt((real)0.6); w[0] = 5.0 / 18; w[1] = 8.0 / 18; w[2] = 5.0 / 18; }
+  return G;
+}
+
+static int grp_interface(int system, real lambda, real gamma, int M, real dt,
+                         const real *trL, const real *trR, real rtol, int max_iter, int guess_kind,
+                         real *flux, real *gnew, int *iters, int *truncated)
+{
+  int C = system == OR_EULER ? 3 : 1;
+  real q[(MAXM + 1) * (MAXM + 1)][MAXC];
+  for (int i = 0; i < (MAXM + 1) * (MAXM + 1); ++i) q[i][0] = q[i][1] = q[i][2] = 0;
+  *iters = 0;
+  *truncated = 0;
+  /* leading term: classical Riemann problem of the traces */
+  if (system == OR_ADVECTION) {
+    for (int k = 0; k <= M; ++k) {
+      real D = lambda > 0 ? trL[k] : (lambda < 0 ? trR[k] : 0.5 * (trL[k] + trR[k]));
+      real fact = 1;
+      for (int r = 2; r <= k; ++r) fact = fact * r;
+      q[SIDX(k, 0)][0] = D / fact;
+    }
+  } else {
+    real Q0[3];
+    int st = riemann_state(gamma, trL, trR, guess_kind, 0, rtol, max_iter, 0, Q0, iters);
+    if (st != OR_OK) return st;
+    for (int c = 0; c < 3; ++c) q[SIDX(0, 0)][c] = Q0[c];
+    for (int k = 1; k <= M; ++k) {
+      real D[3];
+      deriv_rp(gamma, Q0, trL + k * 3, trR + k * 3, D);
+      real fact = 1;
+      for (int r = 2; r <= k; ++r) fact = fact * r;
+      for (int c = 0; c < 3; ++c) q[SIDX(k, 0)][c] = D[c] / fact;
+    }
+  }
+  ck_series(system, lambda, gamma, M, q);
+
+  real s[3], w[3], Qt[MAXC][4];
+  int G = gauss_rule(M, s, w);
+  for (int al = 0; al <= G; ++al) {     /* G Gauss points, then tau = dt */
+    real tau = al < G ? dt * (1 + s[al]) / 2 : dt;
+    for (int c = 0; c < C; ++c) {
+      real v = 0;
+      for (int b = M; b >= 0; --b) v = v * tau + q[SIDX(0, b)][c];
+      Qt[c][al] = v;
+    }
+  }
+  if (system == OR_EULER) {
+    int ok = 1;
+    for (int al = 0; al <= G; ++al) {
+      real Qa[3] = { Qt[0][al], Qt[1][al], Qt[2][al] };
+      if (!euler_admissible(gamma, Qa)) ok = 0;
+    }
+    if (!ok) {       /* READING: truncate this interface's series to its leading term */
+      *truncated = 1;
+      for (int al = 0; al <= G; ++al)
+        for (int c = 0; c < 3; ++c) Qt[c][al] = q[SIDX(0, 0)][c];
+    }
+  }
+  for (int c = 0; c < C; ++c) flux[c] = 0;
+  for (int al = 0; al < G; ++al) {
+    real F[3];
+    if (system == OR_EULER) {
+      real Qa[3] = { Qt[0][al], Qt[1][al], Qt[2][al] };
+      euler_flux(gamma, Qa, F);
+    } else {
+      F[0] = lambda * Qt[0][al];
+    }
+    for (int c = 0; c < C; ++c) flux[c] = flux[c] + w[al] * F[c];
+  }
+  for (int c = 0; c < C; ++c) gnew[c] = Qt[c][G];
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Exported unit entry points                                                */
+/* ------------------------------------------------------------------------- */
+int or_star_pressure(double gamma, const double *WL, const double *WR, int guess_kind,
+                     double guess, double rtol, int max_iter, double *out)
+{
+  real wl[3] = { WL[0], WL[1], WL[2] }, wr[3] = { WR[0], WR[1], WR[2] }, ps = 0, us = 0;
+  int it = 0;
+  int st = star_pressure(gamma, wl, wr, guess_kind, guess, rtol, max_iter, &ps, &us, &it);
+  out[0] = ps; out[1] = us; out[2] = it;
+  return st;
+}
+
+int or_riemann_state(double gamma, const double *QL, const double *QR, double rtol, int max_iter,
+                     double *Q, int *iters)
+{
+  real ql[3] = { QL[0], QL[1], QL[2] }, qr[3] = { QR[0], QR[1], QR[2] }, q[3];
+  int st = riemann_state(gamma, ql, qr, OR_GUESS_PVRS, 0, rtol, max_iter, 1, q, iters);
+  Q[0] = q[0]; Q[1] = q[1]; Q[2] = q[2];
+  return st;
+}
+
+void or_deriv_rp(double gamma, const double *Q0, const double *DL, const double *DR, double *D)
+{
+  real q0[3] = { Q0[0], Q0[1], Q0[2] }, dl[3] = { DL[0], DL[1], DL[2] }, dr[3] = { DR[0], DR[1], DR[2] }, d[3];
+  deriv_rp(gamma, q0, dl, dr, d);
+  D[0] = d[0]; D[1] = d[1]; D[2] = d[2];
+}
+
+int or_grp_interface(int system, double lambda, double gamma, int M, double dt,
+                     const double *trL, const double *trR, double rtol, int max_iter,
+                     int guess_kind, double *flux, double *gnew, int *iters, int *truncated)
+{
+  int C = system == OR_EULER ? 3 : 1;
+  real tl[(MAXM + 1) * MAXC], tr[(MAXM + 1) * MAXC], f[MAXC], g[MAXC];
+  for (int i = 0; i < (M + 1) * C; ++i) { tl[i] = trL[i]; tr[i] = trR[i]; }
+  int st = grp_interface(system, lambda, gamma, M, dt, tl, tr, rtol, max_iter, guess_kind, f, g,
+                         iters, truncated);
+  for (int c = 0; c < C; ++c) { flux[c] = f[c]; gnew[c] = g[c]; }
+  return st;
+}
+
+int or_init_iface(int system, double lambda, double gamma, int n_ifaces,
+                  const double *lim_minus, const double *lim_plus, double *iface)
+{
+  int worst = OR_OK;
+  if (system == OR_ADVECTION) {
+    for (int j = 0; j < n_ifaces; ++j)
+      iface[j] = lambda > 0 ? lim_minus[j] : (lambda < 0 ? lim_plus[j] : 0.5 * (lim_minus[j] + lim_plus[j]));
+    return OR_OK;
+  }
+  for (int j = 0; j < n_ifaces; ++j) {
+    real ql[3], qr[3], q[3];
+    int it;
+    for (int c = 0; c < 3; ++c) { ql[c] = lim_minus[c * n_ifaces + j]; qr[c] = lim_plus[c * n_ifaces + j]; }
+    int st = riemann_state(gamma, ql, qr, OR_GUESS_PVRS, 0, 1e-12, 50, 1, q, &it);
+    if (st != OR_OK && st != OR_VACUUM) { worst = st; q[0] = ql[0]; q[1] = ql[1]; q[2] = ql[2]; }
+    for (int c = 0; c < 3; ++c) iface[c * n_ifaces + j] = q[c];
+  }
+  return worst;
+}
+
+/* ------------------------------------------------------------------------- */
+/* One step of one domain: FV update (eq. eq_finite_volume, Section 2).      */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int system; real lambda, gamma; int M; real cfl;
+  real rtol; int max_iter; int guess_kind; int dt_hold;
+} params;
+
+/* Time-step rule (Section 4.1): dt = C dx / S_max, S_max over the cell averages.
+ * READING: the last step is clipped to t_end; dt is recomputed every dt_hold steps. */
+static real domain_smax(const params *P, int N, const real *avg, long stride)
+{
+  if (P->system == OR_ADVECTION) return fabs(P->lambda);
+  real smax = 0;
+  for (int i = 0; i < N; ++i) {
+    real Q[3] = { avg[i], avg[stride + i], avg[2 * stride + i] }, W[3];
+    cons_to_prim(P->gamma, Q, W);
+    real s = fabs(W[1]) + sqrt(P->gamma * W[2] / W[0]);
+    if (s > smax) smax = s;
+  }
+  return smax;
+}
+
+/* First-order Godunov flux at interface j: exact Riemann problem of the two
+ * adjacent cell averages (a transmissive end uses the boundary cell twice). */
+static int first_order_interface(const params *P, int N, int bc, int j, const real *avg, long cstride,
+                                 real *flux, real *gnew, long long *st)
+{
+  int cl = bc == OR_BC_PERIODIC ? (j - 1 + N) % N : (j - 1 < 0 ? 0 : j - 1);
+  int cr = bc == OR_BC_PERIODIC ? j : (j > N - 1 ? N - 1 : j);
+  real QL[3], QR[3], Q0[3];
+  for (int c = 0; c < 3; ++c) { QL[c] = avg[c * cstride + cl]; QR[c] = avg[c * cstride + cr]; }
+  int it = 0;
+  int s = riemann_state(P->gamma, QL, QR, P->guess_kind, 0, P->rtol, P->max_iter, 1, Q0, &it);
+  st[OR_ST_RS_CALLS] += 1;
+  st[OR_ST_NEWTON_SUM] += it;
+  if (it > st[OR_ST_NEWTON_MAX]) st[OR_ST_NEWTON_MAX] = it;
+  st[OR_ST_LOW_ORDER] += 1;
+  if (s != OR_OK && s != OR_VACUUM) return s;
+  if (Q0[0] > 0) euler_flux(P->gamma, Q0, flux);
+  else flux[0] = flux[1] = flux[2] = 0;            /* vacuum carries no flux */
+  for (int c = 0; c < 3; ++c) gnew[c] = Q0[c];
+  return OR_OK;
+}
+
+/*
+ * avg, iface point at this domain's first cell / interface; strides are the
+ * plane lengths.  Returns a status; on success the domain holds step n+1.
+ */
+static int step_domain(const params *P, int N, int bc, real dx, real dt, real *avg, long cstride,
+                       real *iface, long istride, long long *st)
+{
+  const int M = P->M, C = P->system == OR_EULER ? 3 : 1;
+  const int nif = bc == OR_BC_PERIODIC ? N : N + 1;
+  real *coef = (real *)malloc(sizeof(real) * N * C * (MAXM + 1));
+  real *flux = (real *)malloc(sizeof(real) * nif * C);
+  real *gnew = (real *)malloc(sizeof(real) * nif * C);
+  char *low = (char *)calloc(nif, 1);
+  int status = OR_OK;
+
+  /* reconstruction, cell by cell, component by component (READING: conserved
+   * variables; linear GRPrec commutes with a per-cell characteristic projection) */
+  for (int i = 0; i < N; ++i) {
+    int im = i - 1, ip = i + 1;
+    if (bc == OR_BC_PERIODIC) { im = (im + N) % N; ip = ip % N; }
+    else { if (im < 0) im = 0; if (ip > N - 1) ip = N - 1; }  /* ghost = copy */
+    int jl = i, jr = (bc == OR_BC_PERIODIC) ? (i + 1) % N : i + 1;
+    for (int c = 0; c < C; ++c) {
+      double qb[3] = { (double)avg[c * cstride + im], (double)avg[c * cstride + i], (double)avg[c * cstride + ip] };
+      double g[2] = { (double)iface[c * istride + jl], (double)iface[c * istride + jr] };
+      double cf[MAXM + 1];
+      or_recon(M, qb, g, cf);
+      for (int k = 0; k <= MAXM; ++k) coef[(i * C + c) * (MAXM + 1) + k] = cf[k];
+    }
+    if (P->system == OR_EULER) {   /* READING: inadmissible trace -> degree 0 */
+      int ok = 1;
+      for (int side = 0; side < 2; ++side) {
+        real Q[3];
+        for (int c = 0; c < 3; ++c)
+          Q[c] = poly_deriv(M, coef + (i * C + c) * (MAXM + 1), 0, side ? (real)0.5 : (real)-0.5);
+        if (!euler_admissible(P->gamma, Q)) ok = 0;
+      }
+      if (!ok) {
+        for (int c = 0; c < 3; ++c)
+          for (int k = 0; k <= MAXM; ++k)
+            coef[(i * C + c) * (MAXM + 1) + k] = k == 0 ? avg[c * cstride + i] : 0;
+        st[OR_ST_RECON_FB] += 1;
+      }
+    }
+  }
+
+  /* one GRP per interface.  READING (transmissive ends): the outside cell is a
+   * ghost holding the boundary cell's average as a constant polynomial. */
+  for (int j = 0; j < nif && status == OR_OK; ++j) {
+    int cl, cr;
+    if (bc == OR_BC_PERIODIC) { cl = (j - 1 + N) % N; cr = j; }
+    else { cl = j - 1; cr = j; }                  /* -1 or N: the ghost */
+    real trL[(MAXM + 1) * MAXC], trR[(MAXM + 1) * MAXC];
+    real scale = 1;
+    for (int k = 0; k <= M; ++k) {
+      for (int c = 0; c < C; ++c) {
+        if (cl < 0) trL[k * C + c] = k == 0 ? avg[c * cstride + 0] : 0;
+        else trL[k * C + c] = poly_deriv(M, coef + (cl * C + c) * (MAXM + 1), k, (real)0.5) / scale;
+        if (cr > N - 1) trR[k * C + c] = k == 0 ? avg[c * cstride + N - 1] : 0;
+        else trR[k * C + c] = poly_deriv(M, coef + (cr * C + c) * (MAXM + 1), k, (real)-0.5) / scale;
+      }
+      scale = scale * dx;
+    }
+    int it = 0, tr = 0;
+    int s = grp_interface(P->system, P->lambda, P->gamma, M, dt, trL, trR, P->rtol, P->max_iter,
+                          P->guess_kind, flux + j * C, gnew + j * C, &it, &tr);
+    if (P->system == OR_EULER) {
+      st[OR_ST_RS_CALLS] += 1;
+      st[OR_ST_NEWTON_SUM] += it;
+      if (it > st[OR_ST_NEWTON_MAX]) st[OR_ST_NEWTON_MAX] = it;
+      st[OR_ST_FLUX_FB] += tr;
+      /* READING: a Riemann problem of the traces with no solution (vacuum,
+       * no convergence) sends this interface to the first-order flux */
+      if (s != OR_OK) {
+        s = first_order_interface(P, N, bc, j, avg, cstride, flux + j * C, gnew + j * C, st);
+        low[j] = 1;
+      }
+    }
+    if (s != OR_OK) status = s;
+  }
+
+  real *cand = (real *)malloc(sizeof(real) * N * C);
+  if (status == OR_OK) {
+    /* conservative update, eq. eq_finite_volume with S = 0 */
+    for (int pass = 0; ; ++pass) {
+      int bad = 0, changed = 0;
+      for (int i = 0; i < N; ++i) {
+        int jl = i, jr = (bc == OR_BC_PERIODIC) ? (i + 1) % N : i + 1;
+        for (int c = 0; c < C; ++c)
+          cand[c * N + i] = avg[c * cstride + i] - dt / dx * (flux[jr * C + c] - flux[jl * C + c]);
+      }
+      if (P->system != OR_EULER) break;
+      /* READING (a posteriori, MOOD-like): an inadmissible candidate average
+       * marks its cell troubled; both of its interfaces are recomputed with the
+       * first-order Godunov flux of the cell averages, in at most OR_MAX_REPAIR
+       * rounds; a cell still inadmissible after that freezes the domain. */
+      for (int i = 0; i < N && status == OR_OK; ++i) {
+        real Q[3] = { cand[i], cand[N + i], cand[2 * N + i] };
+        if (euler_admissible(P->gamma, Q)) continue;
+        bad = 1;
+        if (pass >= OR_MAX_REPAIR) continue;
+        int js[2] = { i, (bc == OR_BC_PERIODIC) ? (i + 1) % N : i + 1 };
+        for (int e = 0; e < 2; ++e) {
+          int j = js[e];
+          if (low[j]) continue;
+          int s = first_order_interface(P, N, bc, j, avg, cstride, flux + j * C, gnew + j * C, st);
+          if (s != OR_OK) { status = s; break; }
+          low[j] = 1;
+          changed = 1;
+        }
+      }
+      if (!bad || status != OR_OK) break;
+      if (!changed) { status = OR_NONPHYSICAL; break; }
+    }
+  }
+  if (status == OR_OK || status == OR_NONPHYSICAL) {
+    for (int i = 0; i < N; ++i)
+      for (int c = 0; c < C; ++c) avg[c * cstride + i] = cand[c * N + i];
+    for (int j = 0; j < nif; ++j)
+      for (int c = 0; c < C; ++c) iface[c * istride + j] = gnew[j * C + c];
+  }
+  free(cand); free(low);
+  free(coef); free(flux); free(gnew);
+  return status;
+}
+
+int or_run(int system, double lambda, double gamma, int M, double cfl,
+           int n_domains, const int *n_cells, const double *x_left, const double *x_right,
+           const int *bc, double newton_rtol, int newton_max_iter, int guess_kind, int dt_hold,
+           double *avg, double *iface, double *t, int *nstep, double *dt_prev, int *status,
+           int n_steps, double t_end, long long *stats, const double *dt_fixed, int n_threads)
+{
+  params P;
+  P.system = system; P.lambda = lambda; P.gamma = gamma; P.M = M; P.cfl = cfl;
+  P.rtol = newton_rtol; P.max_iter = newton_max_iter; P.guess_kind = guess_kind;
+  P.dt_hold = dt_hold < 1 ? 1 : dt_hold;
+  if (M < 1 || M > MAXM) return -1;
+  const int C = system == OR_EULER ? 3 : 1;
+  long *coff = (long *)malloc(sizeof(long) * (n_domains + 1));
+  long *ioff = (long *)malloc(sizeof(long) * (n_domains + 1));
+  coff[0] = ioff[0] = 0;
+  for (int d = 0; d < n_domains; ++d) {
+    coff[d + 1] = coff[d] + n_cells[d];
+    ioff[d + 1] = ioff[d] + n_cells[d] + (bc[d] == OR_BC_TRANSMISSIVE ? 1 : 0);
+  }
+  const long ctot = coff[n_domains], itot = ioff[n_domains];
+  (void)n_threads;
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int d = 0; d < n_domains; ++d) {
+    const int N = n_cells[d];
+    const real dx = (x_right[d] - x_left[d]) / N;
+    /* this domain's planes, copied to contiguous real arrays */
+    real *a = (real *)malloc(sizeof(real) * N * C);
+    real *g = (real *)malloc(sizeof(real) * (N + 1) * C);
+    const int nif = (int)(ioff[d + 1] - ioff[d]);
+    for (int c = 0; c < C; ++c) {
+      for (int i = 0; i < N; ++i) a[c * N + i] = avg[c * ctot + coff[d] + i];
+      for (int j = 0; j < nif; ++j) g[c * nif + j] = iface[c * itot + ioff[d] + j];
+    }
+    long long *st = stats + (long)d * OR_NSTATS;
+    for (int s = 0; s < n_steps; ++s) {
+      if (status[d] != OR_OK) break;
+      real td = t[d];
+      if (!(td < t_end)) break;
+      real dt_cfl;
+      if (dt_fixed) dt_cfl = dt_fixed[s];
+      else if (nstep[d] % P.dt_hold == 0 || !(dt_prev[d] > 0)) dt_cfl = P.cfl * dx / domain_smax(&P, N, a, N);
+      else dt_cfl = dt_prev[d];
+      real dt = dt_cfl;
+      int last = 0;
+      if (td + dt >= t_end) { dt = t_end - td; last = 1; }
+      int rc = step_domain(&P, N, bc[d], dx, dt, a, N, g, nif, st);
+      if (rc != OR_OK && rc != OR_NONPHYSICAL) { status[d] = rc; break; }
+      t[d] = last ? t_end : td + dt;
+      nstep[d] += 1;
+      dt_prev[d] = dt_cfl;
+      st[OR_ST_STEPS] += 1;
+      if (rc == OR_NONPHYSICAL) { status[d] = rc; break; }
+    }
+    for (int c = 0; c < C; ++c) {
+      for (int i = 0; i < N; ++i) avg[c * ctot + coff[d] + i] = a[c * N + i];
+      for (int j = 0; j < nif; ++j) iface[c * itot + ioff[d] + j] = g[c * nif + j];
+    }
+    free(a); free(g);
+  }
+  free(coff); free(ioff);
+  return 0;
+}
