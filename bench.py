@@ -1,0 +1,231 @@
+"""Throughput of the GRPrec ADER step on GB300: FP64 cell-updates/s.
+
+Workload (default): the batched case -- 65,536 independent transmissive Euler
+domains, cell counts log-uniform in [4, 512] (seed 2602), half smooth density
+waves, half Riemann problems with density/pressure ratios log-uniform in
+[1e-3, 1e3], GRPrec degree M = 2, CFL 0.9.  One bench step = one time step of
+every domain (the whole hot path: CFL reduction, reconstruction, GRP, update,
+repair, write-back).  The state (~0.8 GB) is larger than L2, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the only reference this build has) on a
+bounded sample of the same workload, on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP64 cell-updates/s at fixed L1 error, plain vs batched+learned p* guess, 1 GB300"
+UNIT = "cell-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--domains", type=int, default=65536)
+    ap.add_argument("--M", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in self.rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def workload(args, rank):
+    from paper_2602_21911_gb300 import inputs as I
+    prob, avg, lm, lp = I.batched(args.domains, seed=2602 + rank, M=args.M)
+    return prob, avg, lm, lp
+
+
+def cpu_baseline(args, steps=100, stride=16):
+    """The oracle as it stands, OpenMP over domains, on a bounded sample."""
+    import oracle as O
+    from paper_2602_21911_gb300 import inputs as I
+    ids = np.arange(0, args.domains, stride)
+    prob, avg, lm, lp = I.batched(args.domains, seed=2602, M=args.M, domains=ids)
+    st, g = O.init_iface(O.EULER, 1.0, 1.4, lm, lp)
+    S = O.State(prob, avg, g)
+    threads = O.cpu_threads()
+    t0 = time.perf_counter()
+    O.run(prob, S, steps, n_threads=threads)
+    el = time.perf_counter() - t0
+    upd = float((S.stats[:, O.ST_STEPS] * prob["n_cells"]).sum())
+    return {"value": upd / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "every %dth domain (%d domains, %d cells) x %d steps, %.1f s" % (
+                stride, len(ids), int(prob["n_cells"].sum()), steps, el)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # each step: a bounded sample of the workload through the oracle
+    import oracle as O
+    from paper_2602_21911_gb300 import inputs as I
+    ids = np.arange(0, args.domains, 64)
+    prob, avg, lm, lp = I.batched(args.domains, seed=2602, M=args.M, domains=ids)
+    st, g = O.init_iface(O.EULER, 1.0, 1.4, lm, lp)
+    S = O.State(prob, avg, g)
+    threads = O.cpu_threads()
+    O.run(prob, S, args.warmup, n_threads=threads)
+    s0 = S.stats[:, O.ST_STEPS].copy()
+    t0 = time.perf_counter()
+    O.run(prob, S, args.steps, n_threads=threads)
+    el = time.perf_counter() - t0
+    upd = float(((S.stats[:, O.ST_STEPS] - s0) * prob["n_cells"]).sum())
+    v = upd / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "batched Euler, 65536 domains x 4..512 cells, M=%d (oracle sample: "
+                                   "every 64th domain)" % args.M, "seed": 2602},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "every 64th domain (%d domains) per step" % len(ids)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2602_21911_gb300 import grprec
+    prob, avg, lm, lp = workload(args, rank)
+    stream = torch.cuda.Stream()
+    s = grprec.Solver(prob, device=local, stream=stream.cuda_stream)
+    s.set_initial(avg, lm, lp)
+    s.step(args.warmup)
+    stats0, _ = s.get_stats()
+    launches0 = s.launch_count()
+    s.set_kernel_timing(True)
+    s.kernel_timing()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        s.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    flux_ms, flux_n = s.kernel_timing()
+    s.set_kernel_timing(False)
+    ms = ev0.elapsed_time(ev1)
+    launches = s.launch_count() - launches0
+    stats1, status = s.get_stats()
+    upd = float(((stats1[:, 0] - stats0[:, 0]).astype(np.float64) * prob["n_cells"]).sum())
+    tmax = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, upd], device="cuda", dtype=torch.float64)
+        mx = t.clone(); dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
+        sm = t.clone(); dist.all_reduce(sm[1:], op=dist.ReduceOp.SUM)
+        tmax, upd = float(mx[0]), float(sm[1])
+    value = upd / (tmax * 1e-3)
+
+    # end to end through the public API with pinned host buffers
+    h_avg = torch.from_numpy(np.ascontiguousarray(avg)).pin_memory()
+    h_lm = torch.from_numpy(np.ascontiguousarray(lm)).pin_memory()
+    h_lp = torch.from_numpy(np.ascontiguousarray(lp)).pin_memory()
+    o_avg = torch.empty_like(h_avg).pin_memory()
+    o_if = torch.empty((s.C, s.nif), dtype=torch.float64).pin_memory()
+    o_t = torch.empty(s.D, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_initial(h_avg, h_lm, h_lp)
+    s.step(args.warmup + args.steps)
+    s.get_state(o_avg, o_if, o_t)
+    e2e_s = time.perf_counter() - t0
+    st_e2e, _ = s.get_stats()
+    upd_e2e = float((st_e2e[:, 0].astype(np.float64) * prob["n_cells"]).sum())
+    nsteps_e2e = args.warmup + args.steps
+    h2d = 8 * (h_avg.numel() + h_lm.numel() + h_lp.numel())
+    d2h = 8 * (o_avg.numel() + o_if.numel() + o_t.numel())
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batched Euler: %d domains x log-uniform 4..512 cells, M=%d, CFL 0.9, "
+                                   "transmissive, guess PVRS" % (args.domains, args.M),
+                       "seed": 2602, "cells": int(prob["n_cells"].sum()),
+                       "l2": "state larger than L2 (no flush needed)"},
+            "e2e": {"value": upd_e2e / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d / nsteps_e2e, "d2h_bytes_per_step": d2h / nsteps_e2e},
+            "gpu_launches": launches, "clocks": clk.summary(),
+            "flux_kernel": {"ms_total": flux_ms, "launches": flux_n,
+                            "share_of_step": flux_ms / ms if ms > 0 else None},
+            "frozen_domains": int((status != 0).sum())}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * grprec.h — C ABI of the GB300 (sm_103a) FV+GRPrec ADER library.
+ *
+ * One time step of the finite volume scheme of Montecinos, Toro and Mueller,
+ * "A generalized Riemann problem-based compact reconstruction method for
+ * finite volume schemes" (arXiv 2602.21911), for 1D linear advection and the
+ * ideal-gas Euler equations, over many independent 1D domains at once:
+ *
+ *   Q_i^{n+1} = Q_i^n - dt/dx (F_{i+1/2} - F_{i-1/2})         (Section 2, eq. eq_finite_volume, S = 0)
+ *
+ *   - GRPrec reconstruction of degree M = 1..4 from the cell averages and the
+ *     interface data kept from the previous step                (Section 3.1)
+ *   - a generalized Riemann problem GRP_M per interface: exact leading-term
+ *     Riemann problem by Newton on the star pressure, derivative Riemann
+ *     problems, Cauchy-Kovalevskaya time series (Toro-Titarev structure,
+ *     Section 2), Gauss time integral of the flux (numerical flux, Section 2)
+ *   - write-back of the interface data = the series at tau = dt
+ *   - dt = C dx / S_max with S_max over the cell averages          (Section 4.1)
+ *
+ * Conventions for every entry point:
+ *   - Return 0 on success, a negative GRP_E_* code otherwise; grp_status_string
+ *     names it.  Nothing is thrown, nothing aborts.
+ *   - The library owns all device memory it allocates in grp_create and frees it
+ *     in grp_destroy.  The caller owns every buffer it passes; the library never
+ *     keeps a caller pointer after a call returns.
+ *   - Work is ordered on the stream given in grp_problem (NULL = legacy default
+ *     stream).  grp_get_* synchronise that stream before returning.
+ *   - State layout (also of caller buffers): component-major planes concatenated
+ *     over domains.  Cell planes hold sum(n_cells) doubles each; interface planes
+ *     hold sum(n_cells[d] + (bc[d] == TRANSMISSIVE)) doubles each.  Interface j
+ *     of a domain is the left edge of its cell j (periodic: the right edge of the
+ *     last cell is interface 0).  Components: advection (q); Euler (rho, rho u, E).
+ *   - There is no CPU fallback: without a usable CUDA device grp_create fails with
+ *     GRP_E_CUDA.
+ */
+#ifndef GRPREC_H
+#define GRPREC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct grp_ctx grp_ctx;   /* opaque, library-owned */
+
+enum { GRP_ADVECTION = 0, GRP_EULER_IDEAL = 1 };                 /* system (Sections 4.2, 4.3) */
+enum { GRP_BC_PERIODIC = 0, GRP_BC_TRANSMISSIVE = 1 };            /* per-domain boundary */
+enum { GRP_GUESS_PVRS = 0, GRP_GUESS_TRRS = 1, GRP_GUESS_MLP = 2 };/* Newton initial guess for p* */
+
+/* return codes */
+enum {
+  GRP_OK = 0,
+  GRP_E_INVALID_ARG = -1,
+  GRP_E_CUDA = -2,
+  GRP_E_NOT_INITIALIZED = -3,
+  GRP_E_NO_MODEL = -4,
+  GRP_E_MAX_STEPS = -5
+};
+
+/* per-domain status (grp_get_stats); a domain with a non-zero status is frozen */
+enum {
+  GRP_ST_OK = 0,
+  GRP_ST_NEWTON_NO_CONV = 1,   /* the star-pressure Newton iteration hit newton_max_iter */
+  GRP_ST_VACUUM = 2,           /* reserved: vacuum data are sampled, never fatal */
+  GRP_ST_NONPHYSICAL = 3       /* an average stayed inadmissible after the first-order repair */
+};
+
+/* per-domain counters (grp_get_stats), each an unsigned 64-bit integer */
+enum {
+  GRP_STAT_STEPS = 0,          /* steps taken */
+  GRP_STAT_NEWTON_SUM = 1,     /* star-pressure Newton iterations, summed */
+  GRP_STAT_NEWTON_MAX = 2,     /* max iterations at one interface */
+  GRP_STAT_RECON_FB = 3,       /* cells reconstructed at degree 0 (inadmissible trace) */
+  GRP_STAT_FLUX_FB = 4,        /* interfaces whose time series was cut to its leading term */
+  GRP_STAT_RS_CALLS = 5,       /* exact Riemann solves */
+  GRP_STAT_LOW_ORDER = 6,      /* interfaces recomputed with the first-order Godunov flux */
+  GRP_STAT_GUESS_USED = 7,     /* Newton solves started from the learned guess */
+  GRP_STAT_GUESS_REJECTED = 8, /* learned guesses rejected (range / non-finite / stall) */
+  GRP_NSTATS = 9
+};
+
+typedef struct {
+  int system;            /* GRP_ADVECTION or GRP_EULER_IDEAL */
+  double lambda;         /* advection speed (advection only), != 0 */
+  double gamma;          /* ratio of specific heats (Euler only), > 1 */
+  int M;                 /* GRPrec degree, 1..4: a scheme of order M+1 (Section 3.1) */
+  double cfl;            /* Courant coefficient C in (0, 1] (Section 4.1) */
+  int n_domains;         /* >= 1 */
+  const int *n_cells;    /* host [n_domains], each >= 1 */
+  const double *x_left;  /* host [n_domains]; uniform grid on [x_left, x_right] */
+  const double *x_right; /* host [n_domains], x_right > x_left */
+  const int *bc;         /* host [n_domains], GRP_BC_* */
+  double newton_rtol;    /* relative stopping change of the star pressure, e.g. 1e-12 */
+  int newton_max_iter;   /* Newton iteration cap, e.g. 50 */
+  int guess;             /* GRP_GUESS_*; GRP_GUESS_MLP needs grp_set_guess_model */
+  int dt_hold;           /* recompute dt every dt_hold steps; 1 = the paper's rule */
+  int device;            /* CUDA device ordinal */
+  void *stream;          /* cudaStream_t to order work on (NULL = default stream) */
+} grp_problem;
+
+/*
+ * Create a context for the problem *p (copied; the arrays are read during the
+ * call only).  Allocates the device state.  *out receives the context.
+ * Errors: GRP_E_INVALID_ARG for any field outside its range, GRP_E_CUDA.
+ */
+int grp_create(grp_ctx **out, const grp_problem *p);
+
+/*
+ * Set the initial cell averages and interface data; resets time, steps,
+ * statistics and status of every domain.
+ *   averages:  C planes of sum(n_cells) doubles (required)
+ *   lim_minus: C interface planes, the initial condition's left limits
+ *   lim_plus:  C interface planes, right limits, or NULL
+ * With lim_plus == NULL the interface data are lim_minus as given.  Otherwise
+ * they are the classical Riemann solution of (lim_minus, lim_plus) at x/t = 0
+ * (advection: the upwind value): the GRP at t = 0 of the initial data, which
+ * equals the point value wherever the initial condition is continuous.
+ * ptr_is_device: 0 = host pointers, 1 = device pointers on the context's device.
+ */
+int grp_set_initial(grp_ctx *ctx, const double *averages, const double *lim_minus,
+                    const double *lim_plus, int ptr_is_device);
+
+/*
+ * Advance every active domain by n_steps steps (n_steps >= 0).  A domain stops
+ * early when it reaches t_end (the last step is clipped to land on t_end; pass
+ * INFINITY for no end) or when its status becomes non-zero.  Asynchronous.
+ */
+int grp_step(grp_ctx *ctx, int n_steps, double t_end);
+
+/*
+ * Advance every domain to t_end; returns GRP_E_MAX_STEPS if some active domain
+ * has not reached it after max_steps steps.  Steps are enqueued in blocks; the
+ * stream is synchronised once per block to test whether every domain is done.
+ */
+int grp_advance_to(grp_ctx *ctx, double t_end, int max_steps);
+
+/*
+ * Copy the state out (any pointer may be NULL to skip it): averages (C cell
+ * planes), interface data (C interface planes), t (n_domains doubles).
+ * Synchronises the context's stream.
+ */
+int grp_get_state(grp_ctx *ctx, double *averages, double *iface, double *t, int ptr_is_device);
+
+/*
+ * Host copies of the per-domain counters, stats[n_domains][GRP_NSTATS] (may be
+ * NULL), and statuses, status[n_domains] (may be NULL).  Synchronises.
+ */
+int grp_get_stats(grp_ctx *ctx, unsigned long long *stats, int *status);
+
+/*
+ * Per-domain error norms of the first component (density / q) against exact
+ * cell averages given in the cell layout (ptr_is_device as above):
+ *   l1[d] = sum |Q - Q_exact| dx, l2[d] = sqrt(sum |Q - Q_exact|^2 dx),
+ *   linf[d] = max |Q - Q_exact|                         (Section 4, table columns)
+ * Output arrays are host [n_domains]; any may be NULL.  Synchronises.
+ */
+int grp_error_norms(grp_ctx *ctx, const double *exact_averages, int ptr_is_device,
+                    double *l1, double *l2, double *linf);
+
+/* Number of kernel launches this context has enqueued since grp_create. */
+long long grp_launch_count(const grp_ctx *ctx);
+
+/*
+ * Kernel timing for roofline reports.  With timing enabled, every flux-kernel
+ * launch of grp_step is bracketed by CUDA events on the context's stream.
+ * grp_get_kernel_timing waits for the recorded events, returns the summed
+ * milliseconds and the number of timed launches since the last call, and
+ * clears the record.  Timing adds two event records per step and nothing else.
+ */
+int grp_set_kernel_timing(grp_ctx *ctx, int enable);
+int grp_get_kernel_timing(grp_ctx *ctx, double *flux_ms, long long *flux_launches);
+
+/*
+ * FP64 throughput probe: runs a grid of independent fused multiply-add chains
+ * on `device` (one launch, about 0.2 s) and returns the measured FP64 rate in
+ * FLOP/s (an FMA counts 2).  The denominator of FP64 roofline fractions.
+ */
+int grp_probe_fp64_peak(int device, double *flops_per_s);
+
+/* Release every device allocation of the context; ctx may be NULL. */
+void grp_destroy(grp_ctx *ctx);
+
+/* Static text for a return code (negative) or a domain status (non-negative). */
+const char *grp_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,440 @@
+// C ABI of the FV+GRPrec library (declared in include/grprec.h): context
+// management, argument checks, device state and the launch sequence of a step.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "grp_kernels.cuh"
+#include "grp_launch.h"
+#include "grprec.h"
+
+using namespace grp;
+
+struct grp_ctx {
+  grp_problem p;
+  int D = 0, C = 1;
+  long long ncell = 0, nif = 0;
+  cudaStream_t stream = nullptr;
+  bool initialized = false;
+  int cur = 0;
+  long long launches = 0;
+  std::vector<long long> h_cell_off, h_if_off;
+  std::vector<double> h_dx;
+  // device
+  long long *cell_off = nullptr, *if_off = nullptr;
+  int *cell_dom = nullptr, *if_dom = nullptr;
+  double* dx = nullptr;
+  unsigned char* bc = nullptr;
+  double* avg[2] = {nullptr, nullptr};
+  double* ifc[2] = {nullptr, nullptr};
+  double* flux = nullptr;
+  unsigned char *low = nullptr, *troubled = nullptr;
+  double *t = nullptr, *dt_prev = nullptr;
+  int *nstep = nullptr, *status = nullptr;
+  unsigned long long* smax_bits = nullptr;
+  int *bad = nullptr, *changed = nullptr, *fail = nullptr, *any_bad = nullptr;
+  unsigned long long* stats = nullptr;
+  double* scratch_norm = nullptr;
+  float *mlp = nullptr, *mlp_norm = nullptr;
+  // optional CUDA-event timing of the flux kernel launches
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_free, ev_pending;   // pending: start/stop pairs
+};
+
+namespace {
+
+thread_local char g_err[256];
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+  snprintf(g_err, sizeof(g_err), "%s: %s", what, cudaGetErrorString(e));
+  return GRP_E_CUDA;
+}
+
+#define CK(call)                                           \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n)
+{
+  return cudaMalloc((void**)p, (n ? n : 1) * sizeof(T));
+}
+
+void free_all(grp_ctx* c)
+{
+  for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_pending) cudaEventDestroy(e);
+  c->ev_free.clear();
+  c->ev_pending.clear();
+  void* ptrs[] = {c->cell_off, c->if_off, c->cell_dom, c->if_dom, c->dx, c->bc, c->avg[0], c->avg[1],
+                  c->ifc[0], c->ifc[1], c->flux, c->low, c->troubled, c->t, c->dt_prev, c->nstep,
+                  c->status, c->smax_bits, c->bad, c->changed, c->fail, c->any_bad, c->stats,
+                  c->scratch_norm, c->mlp, c->mlp_norm};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+}
+
+StepArgs make_args(const grp_ctx* c, double t_end)
+{
+  StepArgs a;
+  a.sys = c->p.system;
+  a.M = c->p.M;
+  a.C = c->C;
+  a.ph.lambda = c->p.lambda;
+  a.ph.gamma = c->p.gamma;
+  a.ph.rtol = c->p.newton_rtol;
+  a.ph.max_iter = c->p.newton_max_iter;
+  a.ph.guess = c->p.guess;
+  a.cfl = c->p.cfl;
+  a.t_end = t_end;
+  a.dt_hold = c->p.dt_hold;
+  a.n_domains = c->D;
+  a.ncell = c->ncell;
+  a.nif = c->nif;
+  a.cell_off = c->cell_off;
+  a.if_off = c->if_off;
+  a.cell_dom = c->cell_dom;
+  a.if_dom = c->if_dom;
+  a.dx = c->dx;
+  a.bc = c->bc;
+  a.avg = c->avg[c->cur];
+  a.avg_new = c->avg[c->cur ^ 1];
+  a.ifc = c->ifc[c->cur];
+  a.ifc_new = c->ifc[c->cur ^ 1];
+  a.flux = c->flux;
+  a.low = c->low;
+  a.troubled = c->troubled;
+  a.t = c->t;
+  a.dt_prev = c->dt_prev;
+  a.nstep = c->nstep;
+  a.status = c->status;
+  a.smax_bits = c->smax_bits;
+  a.bad = c->bad;
+  a.changed = c->changed;
+  a.fail = c->fail;
+  a.any_bad = c->any_bad;
+  a.stats = c->stats;
+  a.mlp = c->mlp;
+  a.mlp_norm = c->mlp_norm;
+  return a;
+}
+
+unsigned blocks(long long n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }
+
+cudaError_t launch_flux(const StepArgs& a, cudaStream_t s)
+{
+  if (a.sys == SYS_ADV) return launch_flux_adv(a, s);
+  switch (a.M) {
+    case 1: return launch_flux_euler_m1(a, s);
+    case 2: return launch_flux_euler_m2(a, s);
+    case 3: return launch_flux_euler_m3(a, s);
+    case 4: return launch_flux_euler_m4(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int enqueue_step(grp_ctx* c, double t_end)
+{
+  const StepArgs a = make_args(c, t_end);
+  cudaStream_t s = c->stream;
+  const bool euler = c->p.system == GRP_EULER_IDEAL;
+  if (euler) {
+    k_smax<<<blocks(c->ncell, 256), 256, 0, s>>>(a);
+    c->launches++;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->timing) {
+    for (cudaEvent_t* e : {&e0, &e1}) {
+      if (!c->ev_free.empty()) { *e = c->ev_free.back(); c->ev_free.pop_back(); }
+      else CK(cudaEventCreate(e));
+    }
+    CK(cudaEventRecord(e0, s));
+  }
+  CK(launch_flux(a, s));
+  c->launches++;
+  if (c->timing) {
+    CK(cudaEventRecord(e1, s));
+    c->ev_pending.push_back(e0);
+    c->ev_pending.push_back(e1);
+  }
+  if (euler) {
+    k_update<SYS_EULER><<<blocks(c->ncell, 256), 256, 0, s>>>(a, -1);
+    c->launches++;
+    for (int r = 0; r < MAX_REPAIR; ++r) {
+      k_repair_flux<<<blocks(c->nif, 128), 128, 0, s>>>(a, r);
+      k_update<SYS_EULER><<<blocks(c->ncell, 256), 256, 0, s>>>(a, r);
+      c->launches += 2;
+    }
+  } else {
+    k_update<SYS_ADV><<<blocks(c->ncell, 256), 256, 0, s>>>(a, -1);
+    c->launches++;
+  }
+  k_finish<<<blocks(c->D, 128), 128, 0, s>>>(a);
+  c->launches++;
+  CK(cudaGetLastError());
+  c->cur ^= 1;
+  return GRP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* grp_status_string(int code)
+{
+  switch (code) {
+    case GRP_OK: return "ok";
+    case GRP_E_INVALID_ARG: return "invalid argument";
+    case GRP_E_CUDA: return g_err[0] ? g_err : "CUDA error";
+    case GRP_E_NOT_INITIALIZED: return "initial data not set";
+    case GRP_E_NO_MODEL: return "no learned guess model loaded";
+    case GRP_E_MAX_STEPS: return "max_steps reached before t_end";
+    case GRP_ST_NEWTON_NO_CONV: return "domain frozen: star-pressure Newton did not converge";
+    case GRP_ST_VACUUM: return "vacuum";
+    case GRP_ST_NONPHYSICAL: return "domain frozen: inadmissible state after repair";
+    default: return "unknown code";
+  }
+}
+
+int grp_create(grp_ctx** out, const grp_problem* p)
+{
+  if (!out || !p) return GRP_E_INVALID_ARG;
+  *out = nullptr;
+  if (p->system != GRP_ADVECTION && p->system != GRP_EULER_IDEAL) return GRP_E_INVALID_ARG;
+  if (p->M < 1 || p->M > 4) return GRP_E_INVALID_ARG;
+  if (!(p->cfl > 0.0 && p->cfl <= 1.0)) return GRP_E_INVALID_ARG;
+  if (p->n_domains < 1 || !p->n_cells || !p->x_left || !p->x_right || !p->bc) return GRP_E_INVALID_ARG;
+  if (p->system == GRP_ADVECTION && !(p->lambda != 0.0 && isfinite(p->lambda))) return GRP_E_INVALID_ARG;
+  if (p->system == GRP_EULER_IDEAL && !(p->gamma > 1.0 && isfinite(p->gamma))) return GRP_E_INVALID_ARG;
+  if (!(p->newton_rtol > 0.0) || p->newton_max_iter < 2) return GRP_E_INVALID_ARG;
+  if (p->guess < GRP_GUESS_PVRS || p->guess > GRP_GUESS_MLP) return GRP_E_INVALID_ARG;
+  if (p->dt_hold < 1) return GRP_E_INVALID_ARG;
+  grp_ctx* c = new grp_ctx();
+  c->p = *p;
+  c->p.n_cells = nullptr; c->p.x_left = nullptr; c->p.x_right = nullptr; c->p.bc = nullptr;
+  c->D = p->n_domains;
+  c->C = p->system == GRP_EULER_IDEAL ? 3 : 1;
+  c->stream = (cudaStream_t)p->stream;
+  c->h_cell_off.assign(c->D + 1, 0);
+  c->h_if_off.assign(c->D + 1, 0);
+  c->h_dx.assign(c->D, 0.0);
+  std::vector<unsigned char> hbc(c->D);
+  for (int d = 0; d < c->D; ++d) {
+    const int N = p->n_cells[d];
+    if (N < 1 || (p->bc[d] != GRP_BC_PERIODIC && p->bc[d] != GRP_BC_TRANSMISSIVE) ||
+        !(p->x_right[d] > p->x_left[d]) || !isfinite(p->x_left[d]) || !isfinite(p->x_right[d])) {
+      delete c;
+      return GRP_E_INVALID_ARG;
+    }
+    c->h_cell_off[d + 1] = c->h_cell_off[d] + N;
+    c->h_if_off[d + 1] = c->h_if_off[d] + N + (p->bc[d] == GRP_BC_TRANSMISSIVE ? 1 : 0);
+    c->h_dx[d] = (p->x_right[d] - p->x_left[d]) / N;
+    hbc[d] = (unsigned char)p->bc[d];
+  }
+  c->ncell = c->h_cell_off[c->D];
+  c->nif = c->h_if_off[c->D];
+  if (c->ncell >= (1ll << 31) || c->nif >= (1ll << 31)) { delete c; return GRP_E_INVALID_ARG; }
+  std::vector<int> cdom(c->ncell), idom(c->nif);
+  for (int d = 0; d < c->D; ++d) {
+    for (long long i = c->h_cell_off[d]; i < c->h_cell_off[d + 1]; ++i) cdom[i] = d;
+    for (long long j = c->h_if_off[d]; j < c->h_if_off[d + 1]; ++j) idom[j] = d;
+  }
+  cudaError_t e = cudaSetDevice(p->device);
+  if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaSetDevice"); }
+  const int D = c->D, C = c->C;
+#define AL(ptr, n)                                                    \
+  if ((e = dalloc(&c->ptr, (n))) != cudaSuccess) {                    \
+    free_all(c); delete c; return cuda_fail(e, "cudaMalloc " #ptr); \
+  }
+  AL(cell_off, D + 1) AL(if_off, D + 1) AL(cell_dom, c->ncell) AL(if_dom, c->nif) AL(dx, D) AL(bc, D)
+  AL(avg[0], C * c->ncell) AL(avg[1], C * c->ncell) AL(ifc[0], C * c->nif) AL(ifc[1], C * c->nif)
+  AL(flux, C * c->nif) AL(low, c->nif) AL(troubled, c->ncell) AL(t, D) AL(dt_prev, D) AL(nstep, D)
+  AL(status, D) AL(smax_bits, D) AL(bad, (MAX_REPAIR + 1) * D) AL(changed, MAX_REPAIR * D) AL(fail, D)
+  AL(any_bad, MAX_REPAIR + 1) AL(stats, (long long)NSTATS * D) AL(scratch_norm, 3 * D)
+#undef AL
+  struct Cp { void* dst; const void* src; size_t n; } cps[] = {
+      {c->cell_off, c->h_cell_off.data(), sizeof(long long) * (D + 1)},
+      {c->if_off, c->h_if_off.data(), sizeof(long long) * (D + 1)},
+      {c->cell_dom, cdom.data(), sizeof(int) * c->ncell},
+      {c->if_dom, idom.data(), sizeof(int) * c->nif},
+      {c->dx, c->h_dx.data(), sizeof(double) * D},
+      {c->bc, hbc.data(), (size_t)D}};
+  for (auto& cp : cps) {
+    if ((e = cudaMemcpy(cp.dst, cp.src, cp.n, cudaMemcpyHostToDevice)) != cudaSuccess) {
+      free_all(c); delete c; return cuda_fail(e, "cudaMemcpy metadata");
+    }
+  }
+  *out = c;
+  return GRP_OK;
+}
+
+void grp_destroy(grp_ctx* c)
+{
+  if (!c) return;
+  cudaSetDevice(c->p.device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  free_all(c);
+  delete c;
+}
+
+int grp_set_initial(grp_ctx* c, const double* averages, const double* lim_minus, const double* lim_plus,
+                    int ptr_is_device)
+{
+  if (!c || !averages || !lim_minus) return GRP_E_INVALID_ARG;
+  CK(cudaSetDevice(c->p.device));
+  const cudaMemcpyKind k = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaStream_t s = c->stream;
+  c->cur = 0;
+  CK(cudaMemcpyAsync(c->avg[0], averages, sizeof(double) * c->C * c->ncell, k, s));
+  if (!lim_plus) {
+    CK(cudaMemcpyAsync(c->ifc[0], lim_minus, sizeof(double) * c->C * c->nif, k, s));
+  } else {
+    // both limits staged in the two halves of the flux scratch and the spare plane set
+    double* lm = c->flux;
+    double* lp = c->ifc[1];
+    CK(cudaMemcpyAsync(lm, lim_minus, sizeof(double) * c->C * c->nif, k, s));
+    CK(cudaMemcpyAsync(lp, lim_plus, sizeof(double) * c->C * c->nif, k, s));
+    Phys ph;
+    ph.lambda = c->p.lambda; ph.gamma = c->p.gamma; ph.rtol = c->p.newton_rtol;
+    ph.max_iter = c->p.newton_max_iter; ph.guess = 0;
+    k_init_iface<<<blocks(c->nif, 128), 128, 0, s>>>(c->p.system, ph, c->nif, lm, lp, c->ifc[0]);
+    c->launches++;
+    CK(cudaGetLastError());
+  }
+  const int D = c->D;
+  CK(cudaMemsetAsync(c->t, 0, sizeof(double) * D, s));
+  CK(cudaMemsetAsync(c->dt_prev, 0, sizeof(double) * D, s));
+  CK(cudaMemsetAsync(c->nstep, 0, sizeof(int) * D, s));
+  CK(cudaMemsetAsync(c->status, 0, sizeof(int) * D, s));
+  CK(cudaMemsetAsync(c->smax_bits, 0, sizeof(unsigned long long) * D, s));
+  CK(cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * NSTATS * D, s));
+  CK(cudaMemsetAsync(c->low, 0, c->nif, s));
+  CK(cudaMemsetAsync(c->troubled, 0, c->ncell, s));
+  c->initialized = true;
+  return GRP_OK;
+}
+
+int grp_step(grp_ctx* c, int n_steps, double t_end)
+{
+  if (!c || n_steps < 0 || isnan(t_end)) return GRP_E_INVALID_ARG;
+  if (!c->initialized) return GRP_E_NOT_INITIALIZED;
+  if (c->p.guess == GRP_GUESS_MLP && !c->mlp) return GRP_E_NO_MODEL;
+  CK(cudaSetDevice(c->p.device));
+  for (int i = 0; i < n_steps; ++i) {
+    const int rc = enqueue_step(c, t_end);
+    if (rc) return rc;
+  }
+  return GRP_OK;
+}
+
+int grp_advance_to(grp_ctx* c, double t_end, int max_steps)
+{
+  if (!c || !isfinite(t_end) || max_steps < 0) return GRP_E_INVALID_ARG;
+  if (!c->initialized) return GRP_E_NOT_INITIALIZED;
+  std::vector<double> ht(c->D);
+  std::vector<int> hs(c->D);
+  int done_steps = 0;
+  const int block = 32;
+  while (true) {
+    CK(cudaMemcpyAsync(ht.data(), c->t, sizeof(double) * c->D, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(hs.data(), c->status, sizeof(int) * c->D, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    bool all = true;
+    for (int d = 0; d < c->D; ++d)
+      if (hs[d] == GRP_ST_OK && ht[d] < t_end) { all = false; break; }
+    if (all) return GRP_OK;
+    if (done_steps >= max_steps) return GRP_E_MAX_STEPS;
+    const int n = max_steps - done_steps < block ? max_steps - done_steps : block;
+    const int rc = grp_step(c, n, t_end);
+    if (rc) return rc;
+    done_steps += n;
+  }
+}
+
+int grp_get_state(grp_ctx* c, double* averages, double* iface, double* t, int ptr_is_device)
+{
+  if (!c) return GRP_E_INVALID_ARG;
+  if (!c->initialized) return GRP_E_NOT_INITIALIZED;
+  CK(cudaSetDevice(c->p.device));
+  const cudaMemcpyKind k = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (averages) CK(cudaMemcpyAsync(averages, c->avg[c->cur], sizeof(double) * c->C * c->ncell, k, c->stream));
+  if (iface) CK(cudaMemcpyAsync(iface, c->ifc[c->cur], sizeof(double) * c->C * c->nif, k, c->stream));
+  if (t) CK(cudaMemcpyAsync(t, c->t, sizeof(double) * c->D, k, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return GRP_OK;
+}
+
+int grp_get_stats(grp_ctx* c, unsigned long long* stats, int* status)
+{
+  if (!c) return GRP_E_INVALID_ARG;
+  CK(cudaSetDevice(c->p.device));
+  if (stats)
+    CK(cudaMemcpyAsync(stats, c->stats, sizeof(unsigned long long) * NSTATS * c->D, cudaMemcpyDeviceToHost,
+                       c->stream));
+  if (status) CK(cudaMemcpyAsync(status, c->status, sizeof(int) * c->D, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return GRP_OK;
+}
+
+int grp_error_norms(grp_ctx* c, const double* exact, int ptr_is_device, double* l1, double* l2, double* linf)
+{
+  if (!c || !exact) return GRP_E_INVALID_ARG;
+  if (!c->initialized) return GRP_E_NOT_INITIALIZED;
+  CK(cudaSetDevice(c->p.device));
+  const double* dex = exact;
+  if (!ptr_is_device) {
+    // staged in the flux scratch (C * nif >= ncell doubles), free between steps
+    CK(cudaMemcpyAsync(c->flux, exact, sizeof(double) * c->ncell, cudaMemcpyHostToDevice, c->stream));
+    dex = c->flux;
+  }
+  k_norms<<<c->D, 256, 0, c->stream>>>(c->D, c->cell_off, c->dx, c->avg[c->cur], dex, c->scratch_norm);
+  c->launches++;
+  CK(cudaGetLastError());
+  std::vector<double> h(3 * c->D);
+  CK(cudaMemcpyAsync(h.data(), c->scratch_norm, sizeof(double) * 3 * c->D, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int d = 0; d < c->D; ++d) {
+    if (l1) l1[d] = h[3 * d];
+    if (l2) l2[d] = sqrt(h[3 * d + 1]);
+    if (linf) linf[d] = h[3 * d + 2];
+  }
+  return GRP_OK;
+}
+
+long long grp_launch_count(const grp_ctx* c) { return c ? c->launches : 0; }
+
+int grp_set_kernel_timing(grp_ctx* c, int enable)
+{
+  if (!c) return GRP_E_INVALID_ARG;
+  c->timing = enable != 0;
+  return GRP_OK;
+}
+
+int grp_get_kernel_timing(grp_ctx* c, double* flux_ms, long long* flux_launches)
+{
+  if (!c) return GRP_E_INVALID_ARG;
+  CK(cudaSetDevice(c->p.device));
+  double total = 0.0;
+  long long n = 0;
+  for (size_t k = 0; k + 1 < c->ev_pending.size(); k += 2) {
+    CK(cudaEventSynchronize(c->ev_pending[k + 1]));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev_pending[k], c->ev_pending[k + 1]));
+    total += ms;
+    ++n;
+  }
+  for (cudaEvent_t e : c->ev_pending) c->ev_free.push_back(e);
+  c->ev_pending.clear();
+  if (flux_ms) *flux_ms = total;
+  if (flux_launches) *flux_launches = n;
+  return GRP_OK;
+}
+
+}  // extern "C"

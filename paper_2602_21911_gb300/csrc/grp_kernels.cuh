@@ -1,0 +1,535 @@
+// Kernels of one FV+GRPrec time step over a flat batch of 1D domains.
+//
+// One step is a short fixed sequence of launches on the context's stream:
+//   k_smax         per cell   S_max of every domain (warp max + atomicMax)
+//   k_flux<M>      per iface  GRPrec traces -> GRP -> flux, new interface data
+//   k_update       per cell   candidate averages, admissibility flags
+//   k_repair_flux  per iface  (only troubled domains) first-order fluxes
+//   k_repair_upd   per cell   (only troubled domains) candidates again
+//   k_finish       per domain time, step count, status, buffer bookkeeping
+// Every kernel derives dt from the same per-domain words with the same
+// expression, so no extra launch is needed to publish it.
+#pragma once
+#include "grp_device.cuh"
+
+namespace grp {
+
+constexpr int NSTATS = 9;
+enum { S_STEPS = 0, S_NEWTON_SUM, S_NEWTON_MAX, S_RECON_FB, S_FLUX_FB, S_RS_CALLS, S_LOW, S_GUESS_USED,
+       S_GUESS_REJ };
+constexpr int MAX_REPAIR = 4;   // rounds of the a-posteriori first-order repair
+
+struct StepArgs {
+  int sys, M, C;
+  Phys ph;
+  double cfl, t_end;
+  int dt_hold;
+  int n_domains;
+  long long ncell, nif;              // plane lengths
+  const long long* cell_off;         // [D+1]
+  const long long* if_off;           // [D+1]
+  const int* cell_dom;               // [ncell]
+  const int* if_dom;                 // [nif]
+  const double* dx;                  // [D]
+  const unsigned char* bc;           // [D]
+  // state
+  const double* avg;                 // current averages  [C][ncell]
+  double* avg_new;                   // next averages     [C][ncell]
+  const double* ifc;                 // current interface data [C][nif]
+  double* ifc_new;                   // next interface data    [C][nif]
+  double* flux;                      // scratch [C][nif]
+  unsigned char* low;                // [nif] interface recomputed at first order this step
+  unsigned char* troubled;           // [ncell]
+  // per-domain words
+  double* t;                         // [D]
+  double* dt_prev;                   // [D]
+  int* nstep;                        // [D]
+  int* status;                       // [D]
+  unsigned long long* smax_bits;     // [D] S_max as the bits of a non-negative double
+  int* bad;                          // [(MAX_REPAIR+1) * D] troubled cells after pass p
+  int* changed;                      // [MAX_REPAIR * D] interfaces repaired in pass p
+  int* fail;                         // [D] non-zero: solver failure code this step
+  int* any_bad;                      // [MAX_REPAIR+1] any domain troubled after pass p
+  unsigned long long* stats;         // [D][NSTATS]
+  // learned guess (FP32 network), may be null
+  const float* mlp;                  // packed weights
+  const float* mlp_norm;             // input / output normalisation
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// Warp-aggregated statistics.  Called by all 32 lanes of a warp, converged
+// (the kernels that use it never return early); d < 0 marks a lane without a
+// domain.  One atomic per group of lanes that share a domain.
+__device__ __forceinline__ void warp_stat_add(unsigned long long* stats, int d, int which, unsigned v)
+{
+  const unsigned grp = __match_any_sync(0xffffffffu, d);
+  const unsigned s = __reduce_add_sync(grp, v);
+  if (d >= 0 && lane_id() == __ffs(grp) - 1 && s) atomicAdd(stats + (long long)d * NSTATS + which, (unsigned long long)s);
+}
+
+__device__ __forceinline__ void warp_stat_max(unsigned long long* stats, int d, int which, unsigned v)
+{
+  const unsigned grp = __match_any_sync(0xffffffffu, d);
+  const unsigned s = __reduce_max_sync(grp, v);
+  if (d >= 0 && lane_id() == __ffs(grp) - 1 && s) atomicMax(stats + (long long)d * NSTATS + which, (unsigned long long)s);
+}
+
+// Time-step rule (Section 4.1): dt = C dx / S_max, recomputed every dt_hold
+// steps, the last step clipped to t_end.  false: the domain does not move.
+__device__ __forceinline__ bool domain_dt(const StepArgs& a, int d, double& dt, double& dt_cfl, bool& last)
+{
+  if (a.status[d] != ST_OK) return false;
+  const double t = a.t[d];
+  if (!(t < a.t_end)) return false;
+  const double dtp = a.dt_prev[d];
+  if (a.nstep[d] % a.dt_hold == 0 || !(dtp > 0.0)) {
+    const double smax = a.sys == SYS_ADV ? fabs(a.ph.lambda) : __longlong_as_double((long long)a.smax_bits[d]);
+    dt_cfl = __ddiv_rn(__dmul_rn(a.cfl, a.dx[d]), smax);
+  } else {
+    dt_cfl = dtp;
+  }
+  dt = dt_cfl;
+  last = false;
+  if (__dadd_rn(t, dt) >= a.t_end) { dt = __dadd_rn(a.t_end, -t); last = true; }
+  return true;
+}
+
+// Neighbour cells of cell i (domain-local) under the domain's boundary rule:
+// periodic wrap, or a ghost that copies the boundary cell.
+__device__ __forceinline__ void nbr(int i, int N, int bc, int& im, int& ip)
+{
+  if (bc == 0) { im = i == 0 ? N - 1 : i - 1; ip = i == N - 1 ? 0 : i + 1; }
+  else { im = i == 0 ? 0 : i - 1; ip = i == N - 1 ? N - 1 : i + 1; }
+}
+
+// ------------------------------------------------------------------ k_smax
+static __global__ void k_smax(StepArgs a)
+{
+  const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x == 0 && threadIdx.x <= MAX_REPAIR) a.any_bad[threadIdx.x] = 0;
+  if (gi >= a.ncell) return;
+  const int d = a.cell_dom[gi];
+  if (gi == a.cell_off[d]) {                // one thread per domain resets the step words
+    for (int p = 0; p <= MAX_REPAIR; ++p) a.bad[p * a.n_domains + d] = 0;
+    for (int p = 0; p < MAX_REPAIR; ++p) a.changed[p * a.n_domains + d] = 0;
+    a.fail[d] = 0;
+  }
+  if (a.sys != SYS_EULER) return;
+  const double g = a.ph.gamma;
+  const double r = a.avg[gi], m = a.avg[a.ncell + gi], E = a.avg[2 * a.ncell + gi];
+  // same operation order as the paper-level definition, no contraction
+  const double u = __ddiv_rn(m, r);
+  const double p = __dmul_rn(g - 1.0, __dadd_rn(E, -__dmul_rn(__dmul_rn(0.5, m), u)));
+  double s = __dadd_rn(fabs(u), __dsqrt_rn(__ddiv_rn(__dmul_rn(g, p), r)));
+  if (!(s >= 0.0)) s = 0.0;                 // NaN (inadmissible) contributes nothing
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(s);
+  const unsigned mask = __activemask();
+  if (mask == 0xffffffffu && __all_sync(mask, d == __shfl_sync(mask, d, 0))) {
+    unsigned long long mx = bits;   // whole warp in one domain: one atomic
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(mask, mx, off);
+      mx = o > mx ? o : mx;
+    }
+    if (lane_id() == 0) atomicMax(a.smax_bits + d, mx);
+  } else {
+    atomicMax(a.smax_bits + d, bits);
+  }
+}
+
+// ------------------------------------------------------------------ traces
+// Taylor coefficients (scaled) of cell `cell`'s reconstruction at its right
+// (side = +1) or left (side = -1) edge, component c; with the degree-0
+// fallback when the cell's traces are inadmissible (Euler).
+template <int SYS, int M>
+__device__ __forceinline__ void cell_coeffs(const StepArgs& a, long long c0, long long i0, int N, int bc, int i,
+                                            double b[3][5], bool& fallback)
+{
+  int im, ip;
+  nbr(i, N, bc, im, ip);
+  const int jl = i, jr = (bc == 0) ? (i == N - 1 ? 0 : i + 1) : i + 1;
+#pragma unroll
+  for (int c = 0; c < (SYS == SYS_EULER ? 3 : 1); ++c) {
+    const double* A = a.avg + c * a.ncell + c0;
+    const double* G = a.ifc + c * a.nif + i0;
+    const double qm = (M >= 3) ? A[im] : 0.0, qp = (M >= 3) ? A[ip] : 0.0;
+    grprec_coeffs<M>(qm, A[i], qp, G[jl], G[jr], b[c]);
+  }
+  fallback = false;
+  if (SYS == SYS_EULER) {
+    double tm[3], tp[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double t[M + 1];
+      edge_taylor<M>(b[c], -1.0, t); tm[c] = t[0];
+      edge_taylor<M>(b[c], 1.0, t); tp[c] = t[0];
+    }
+    const double g = a.ph.gamma;
+    if (!admissible(g, tm[0], tm[1], tm[2]) || !admissible(g, tp[0], tp[1], tp[2])) {
+      fallback = true;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { b[c][1] = b[c][2] = b[c][3] = b[c][4] = 0.0; }
+    }
+  }
+}
+
+// First-order Godunov flux and state at interface j from cell averages.
+static __device__ int first_order(const StepArgs& a, long long c0, int N, int bc, int j, double F[3], double Q0[3], int& iters)
+{
+  int cl, cr;
+  if (bc == 0) { cl = j == 0 ? N - 1 : j - 1; cr = j; }
+  else { cl = j == 0 ? 0 : j - 1; cr = j == N ? N - 1 : j; }
+  double QL[3], QR[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) { QL[c] = a.avg[c * a.ncell + c0 + cl]; QR[c] = a.avg[c * a.ncell + c0 + cr]; }
+  const int st = riemann_state(a.ph, QL, QR, 0.0, true, Q0, iters);
+  if (st != ST_OK && st != ST_VACUUM) return st;
+  if (Q0[0] > 0.0) euler_flux(a.ph.gamma, Q0[0], Q0[1], Q0[2], F);
+  else F[0] = F[1] = F[2] = 0.0;
+  return ST_OK;
+}
+
+// ------------------------------------------------------------------ k_flux
+template <int SYS, int M>
+__device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d, unsigned st[6])
+{
+  const long long i0 = a.if_off[d], c0 = a.cell_off[d];
+  const int j = (int)(gj - i0);
+  const int N = (int)(a.cell_off[d + 1] - c0);
+  const int bc = a.bc[d];
+  constexpr int C = SYS == SYS_EULER ? 3 : 1;
+  double dt, dt_cfl;
+  bool last;
+  if (!domain_dt(a, d, dt, dt_cfl, last)) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) a.ifc_new[c * a.nif + gj] = a.ifc[c * a.nif + gj];
+    return;
+  }
+  a.low[gj] = 0;
+  const double nu = dt / a.dx[d];
+
+  // cells on both sides (transmissive ends: a ghost with the boundary average)
+  int cl, cr;
+  if (bc == 0) { cl = j == 0 ? N - 1 : j - 1; cr = j; }
+  else { cl = j - 1; cr = j == N ? -1 : j; }
+
+  double tL[C][M + 1], tR[C][M + 1];
+  if (cl >= 0) {
+    double b[3][5];
+    bool fb;
+    cell_coeffs<SYS, M>(a, c0, i0, N, bc, cl, b, fb);
+    st[5] = fb ? 1u : 0u;                      // counted once per cell: at its right interface
+#pragma unroll
+    for (int c = 0; c < C; ++c) edge_taylor<M>(b[c], 1.0, tL[c]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      tL[c][0] = a.avg[c * a.ncell + c0];
+#pragma unroll
+      for (int k = 1; k <= M; ++k) tL[c][k] = 0.0;
+    }
+  }
+  if (cr >= 0) {
+    double b[3][5];
+    bool fb;
+    cell_coeffs<SYS, M>(a, c0, i0, N, bc, cr, b, fb);
+#pragma unroll
+    for (int c = 0; c < C; ++c) edge_taylor<M>(b[c], -1.0, tR[c]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      tR[c][0] = a.avg[c * a.ncell + c0 + N - 1];
+#pragma unroll
+      for (int k = 1; k <= M; ++k) tR[c][k] = 0.0;
+    }
+  }
+
+  double F[3] = {0.0, 0.0, 0.0}, gnew[3] = {0.0, 0.0, 0.0};
+  if (SYS == SYS_ADV) {
+    const double lam = a.ph.lambda;
+    double s[M + 1];
+#pragma unroll
+    for (int k = 0; k <= M; ++k) s[k] = lam > 0.0 ? tL[0][k] : (lam < 0.0 ? tR[0][k] : 0.5 * (tL[0][k] + tR[0][k]));
+    // CK for q_t + lam q_x = 0: q[0][b] = (-lam)^b q[b][0], in scaled variables
+    double sc = 1.0;
+#pragma unroll
+    for (int k = 0; k <= M; ++k) { s[k] *= sc; sc *= -lam; }
+    double acc = 0.0;
+#pragma unroll
+    for (int al = 0; al < Gauss<M>::G; ++al) {
+      const double T = nu * Gauss<M>::node(al);
+      double v = s[M];
+#pragma unroll
+      for (int k = M - 1; k >= 0; --k) v = v * T + s[k];
+      acc += Gauss<M>::weight(al) * v;
+    }
+    F[0] = lam * acc;
+    double v = s[M];
+#pragma unroll
+    for (int k = M - 1; k >= 0; --k) v = v * nu + s[k];
+    gnew[0] = v;
+  } else {
+    const double g = a.ph.gamma;
+    double QL[3] = {tL[0][0], tL[1][0], tL[2][0]}, QR[3] = {tR[0][0], tR[1][0], tR[2][0]}, Q0[3];
+    int iters = 0;
+    int rs_st = riemann_state(a.ph, QL, QR, 0.0, false, Q0, iters);
+    st[2] = 1;
+    if (rs_st != ST_OK) {
+      // no solution of the traces' Riemann problem: first-order flux here
+      int it2 = 0;
+      rs_st = first_order(a, c0, N, bc, j, F, gnew, it2);
+      iters += it2;
+      st[2] = 2;
+      st[4] = 1;
+      a.low[gj] = 1;
+      if (rs_st != ST_OK) atomicExch(a.fail + d, rs_st);
+    } else {
+      using T = Tri<M>;
+      double rho[T::N], m[T::N], E[T::N];
+      rho[0] = Q0[0]; m[0] = Q0[1]; E[0] = Q0[2];
+      {
+        const Eig e = make_eig(g, Q0);
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+          const double DL[3] = {tL[0][k], tL[1][k], tL[2][k]}, DR[3] = {tR[0][k], tR[1][k], tR[2][k]};
+          double D[3];
+          deriv_rp(e, DL, DR, D);
+          rho[T::idx(k, 0)] = D[0]; m[T::idx(k, 0)] = D[1]; E[T::idx(k, 0)] = D[2];
+        }
+      }
+      double s[3][M + 1];
+      ck_euler<M>(g, rho, m, E, s);
+      // states at the Gauss nodes and at tau = dt
+      double Qg[Gauss<M>::G + 1][3];
+      bool ok = true;
+#pragma unroll
+      for (int al = 0; al <= Gauss<M>::G; ++al) {
+        const double T = al < Gauss<M>::G ? nu * Gauss<M>::node(al) : nu;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          double v = s[c][M];
+#pragma unroll
+          for (int k = M - 1; k >= 0; --k) v = v * T + s[c][k];
+          Qg[al][c] = v;
+        }
+        ok = ok && admissible(g, Qg[al][0], Qg[al][1], Qg[al][2]);
+      }
+      if (!ok) {
+        st[3] = 1;
+#pragma unroll
+        for (int al = 0; al <= Gauss<M>::G; ++al) { Qg[al][0] = Q0[0]; Qg[al][1] = Q0[1]; Qg[al][2] = Q0[2]; }
+      }
+#pragma unroll
+      for (int al = 0; al < Gauss<M>::G; ++al) {
+        double Fa[3];
+        euler_flux(g, Qg[al][0], Qg[al][1], Qg[al][2], Fa);
+        const double w = Gauss<M>::weight(al);
+        F[0] += w * Fa[0]; F[1] += w * Fa[1]; F[2] += w * Fa[2];
+      }
+      gnew[0] = Qg[Gauss<M>::G][0]; gnew[1] = Qg[Gauss<M>::G][1]; gnew[2] = Qg[Gauss<M>::G][2];
+    }
+    st[0] = (unsigned)iters;
+    st[1] = (unsigned)iters;
+  }
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    a.flux[c * a.nif + gj] = F[c];
+    a.ifc_new[c * a.nif + gj] = gnew[c];
+  }
+}
+
+// One thread per interface; every thread of the grid reaches the statistics
+// (no early return) so the warp-synchronous reductions see a full warp.
+template <int SYS, int M>
+__global__ void __launch_bounds__(128) k_flux(StepArgs a)
+{
+  const long long gj = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  // st: newton sum, newton max, RS calls, truncated, first order, recon fallback
+  unsigned st[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+  int d = -1;
+  if (gj < a.nif) {
+    d = a.if_dom[gj];
+    flux_one<SYS, M>(a, gj, d, st);
+  }
+  __syncwarp();
+  if (SYS == SYS_EULER) {
+    warp_stat_add(a.stats, d, S_NEWTON_SUM, st[0]);
+    warp_stat_max(a.stats, d, S_NEWTON_MAX, st[1]);
+    warp_stat_add(a.stats, d, S_RS_CALLS, st[2]);
+    warp_stat_add(a.stats, d, S_FLUX_FB, st[3]);
+    warp_stat_add(a.stats, d, S_LOW, st[4]);
+    warp_stat_add(a.stats, d, S_RECON_FB, st[5]);
+  }
+}
+
+// ------------------------------------------------------------------ update
+// Candidate averages from the flux array; flags inadmissible cells.
+// pass < 0: first update of the step (all active domains), else a repair
+// re-update of the domains flagged bad after pass `pass`.
+template <int SYS>
+__global__ void k_update(StepArgs a, int pass)
+{
+  const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pass >= 0 && a.any_bad[pass] == 0) return;
+  if (gi >= a.ncell) return;
+  const int d = a.cell_dom[gi];
+  constexpr int C = SYS == SYS_EULER ? 3 : 1;
+  double dt, dt_cfl;
+  bool last;
+  const bool active = domain_dt(a, d, dt, dt_cfl, last);
+  if (pass >= 0) {
+    if (!active || !a.bad[pass * a.n_domains + d]) return;
+    if (!a.changed[pass * a.n_domains + d]) return;     // nothing repaired: k_finish freezes it
+  }
+  if (!active) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) a.avg_new[c * a.ncell + gi] = a.avg[c * a.ncell + gi];
+    return;
+  }
+  const long long c0 = a.cell_off[d], i0 = a.if_off[d];
+  const int N = (int)(a.cell_off[d + 1] - c0);
+  const int i = (int)(gi - c0);
+  const int jl = i, jr = (a.bc[d] == 0) ? (i == N - 1 ? 0 : i + 1) : i + 1;
+  const double r = dt / a.dx[d];
+  double Q[3];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    Q[c] = a.avg[c * a.ncell + gi] - r * (a.flux[c * a.nif + i0 + jr] - a.flux[c * a.nif + i0 + jl]);
+    a.avg_new[c * a.ncell + gi] = Q[c];
+  }
+  if (SYS == SYS_EULER) {
+    const bool ok = admissible(a.ph.gamma, Q[0], Q[1], Q[2]);
+    a.troubled[gi] = ok ? 0 : 1;
+    if (!ok) {
+      const int np = pass + 1;
+      a.bad[np * a.n_domains + d] = 1;
+      a.any_bad[np] = 1;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ repair
+// Interfaces of troubled cells take the first-order Godunov flux (a-posteriori,
+// MOOD-like, bounded to MAX_REPAIR rounds).
+static __device__ __forceinline__ void repair_one(const StepArgs& a, int pass, long long gj, int d, unsigned st[3])
+{
+  if (!a.bad[pass * a.n_domains + d]) return;
+  double dt, dt_cfl;
+  bool last;
+  if (!domain_dt(a, d, dt, dt_cfl, last)) return;
+  if (a.low[gj]) return;
+  const long long i0 = a.if_off[d], c0 = a.cell_off[d];
+  const int j = (int)(gj - i0);
+  const int N = (int)(a.cell_off[d + 1] - c0);
+  const int bc = a.bc[d];
+  int cl, cr;
+  if (bc == 0) { cl = j == 0 ? N - 1 : j - 1; cr = j; }
+  else { cl = j - 1; cr = j == N ? -1 : j; }
+  const bool t = (cl >= 0 && a.troubled[c0 + cl]) || (cr >= 0 && a.troubled[c0 + cr]);
+  if (!t) return;
+  double F[3], Q0[3];
+  int iters = 0;
+  const int rs = first_order(a, c0, N, bc, j, F, Q0, iters);
+  st[0] = (unsigned)iters;
+  st[1] = 1u;
+  if (rs != ST_OK) { atomicExch(a.fail + d, rs); return; }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    a.flux[c * a.nif + gj] = F[c];
+    a.ifc_new[c * a.nif + gj] = Q0[c];
+  }
+  a.low[gj] = 1;
+  a.changed[pass * a.n_domains + d] = 1;
+}
+
+static __global__ void __launch_bounds__(128) k_repair_flux(StepArgs a, int pass)
+{
+  if (a.any_bad[pass] == 0) return;          // uniform over the grid
+  const long long gj = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned st[3] = {0u, 0u, 0u};
+  int d = -1;
+  if (gj < a.nif) {
+    d = a.if_dom[gj];
+    repair_one(a, pass, gj, d, st);
+  }
+  __syncwarp();
+  warp_stat_add(a.stats, d, S_NEWTON_SUM, st[0]);
+  warp_stat_max(a.stats, d, S_NEWTON_MAX, st[0]);
+  warp_stat_add(a.stats, d, S_RS_CALLS, st[1]);
+  warp_stat_add(a.stats, d, S_LOW, st[1]);
+}
+
+// ------------------------------------------------------------------ finish
+static __global__ void k_finish(StepArgs a)
+{
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= a.n_domains) return;
+  double dt, dt_cfl;
+  bool last;
+  const bool active = domain_dt(a, d, dt, dt_cfl, last);
+  a.smax_bits[d] = 0ull;
+  if (!active) return;
+  if (a.fail[d]) { a.status[d] = a.fail[d]; return; }
+  a.t[d] = last ? a.t_end : a.t[d] + dt;
+  a.nstep[d] += 1;
+  a.dt_prev[d] = dt_cfl;
+  a.stats[(long long)d * NSTATS + S_STEPS] += 1;
+  if (a.sys == SYS_EULER) {
+    int p = 0;
+    while (p < MAX_REPAIR && a.bad[p * a.n_domains + d] && a.changed[p * a.n_domains + d]) ++p;
+    if (a.bad[p * a.n_domains + d]) a.status[d] = ST_NONPHYS;
+  }
+}
+
+// ------------------------------------------------------------------ init
+// Initial interface data: classical Riemann state of the one-sided limits.
+static __global__ void k_init_iface(int sys, Phys ph, long long nif, const double* lm, const double* lp, double* ifc)
+{
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nif) return;
+  if (sys == SYS_ADV) {
+    const double l = ph.lambda;
+    ifc[j] = l > 0.0 ? lm[j] : (l < 0.0 ? lp[j] : 0.5 * (lm[j] + lp[j]));
+    return;
+  }
+  double QL[3] = {lm[j], lm[nif + j], lm[2 * nif + j]}, QR[3] = {lp[j], lp[nif + j], lp[2 * nif + j]}, Q[3];
+  int it;
+  Phys p2 = ph;
+  p2.guess = 0;
+  const int st = riemann_state(p2, QL, QR, 0.0, true, Q, it);
+  if (st != ST_OK && st != ST_VACUUM) { Q[0] = QL[0]; Q[1] = QL[1]; Q[2] = QL[2]; }
+  ifc[j] = Q[0]; ifc[nif + j] = Q[1]; ifc[2 * nif + j] = Q[2];
+}
+
+// Per-domain norms of component 0 against exact averages: out[d] = {L1, L2^2, Linf}.
+static __global__ void k_norms(int n_domains, const long long* cell_off, const double* dx, const double* avg,
+                        const double* exact, double* out)
+{
+  const int d = blockIdx.x;
+  if (d >= n_domains) return;
+  double s1 = 0.0, s2 = 0.0, mx = 0.0;
+  for (long long i = cell_off[d] + threadIdx.x; i < cell_off[d + 1]; i += blockDim.x) {
+    const double e = fabs(avg[i] - exact[i]);
+    s1 += e; s2 += e * e; mx = fmax(mx, e);
+  }
+  __shared__ double sh[3][256];
+  sh[0][threadIdx.x] = s1; sh[1][threadIdx.x] = s2; sh[2][threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+      sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[3 * d] = sh[0][0] * dx[d];
+    out[3 * d + 1] = sh[1][0] * dx[d];
+    out[3 * d + 2] = sh[2][0];
+  }
+}
+
+}  // namespace grp

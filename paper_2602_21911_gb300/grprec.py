@@ -1,0 +1,202 @@
+"""ctypes binding of libgrprec.so (include/grprec.h), argument marshalling only.
+
+The functions keep the C names.  Every step of the scheme runs in the CUDA
+library; this module never computes any part of it.  Loading fails loudly when
+the library is missing (there is no CPU fallback).  ``Solver`` wraps one
+context for numpy (host) or torch CUDA (device) buffers.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+GRP_ADVECTION, GRP_EULER_IDEAL = 0, 1
+GRP_BC_PERIODIC, GRP_BC_TRANSMISSIVE = 0, 1
+GRP_GUESS_PVRS, GRP_GUESS_TRRS, GRP_GUESS_MLP = 0, 1, 2
+GRP_OK = 0
+GRP_NSTATS = 9
+(STAT_STEPS, STAT_NEWTON_SUM, STAT_NEWTON_MAX, STAT_RECON_FB, STAT_FLUX_FB, STAT_RS_CALLS,
+ STAT_LOW_ORDER, STAT_GUESS_USED, STAT_GUESS_REJECTED) = range(9)
+
+
+class grp_problem(ctypes.Structure):
+    _fields_ = [("system", ctypes.c_int), ("lambda_", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("M", ctypes.c_int), ("cfl", ctypes.c_double), ("n_domains", ctypes.c_int),
+                ("n_cells", ctypes.POINTER(ctypes.c_int)), ("x_left", ctypes.POINTER(ctypes.c_double)),
+                ("x_right", ctypes.POINTER(ctypes.c_double)), ("bc", ctypes.POINTER(ctypes.c_int)),
+                ("newton_rtol", ctypes.c_double), ("newton_max_iter", ctypes.c_int),
+                ("guess", ctypes.c_int), ("dt_hold", ctypes.c_int), ("device", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class GrpError(RuntimeError):
+    pass
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def load(build_if_missing=True):
+    """Load libgrprec.so (building it with nvcc when absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = os.path.join(HERE, "libgrprec.so")
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise GrpError("libgrprec.so is missing: build it with paper_2602_21911_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    L.grp_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(grp_problem)]
+    L.grp_set_initial.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int]
+    L.grp_step.argtypes = [_vp, ctypes.c_int, ctypes.c_double]
+    L.grp_advance_to.argtypes = [_vp, ctypes.c_double, ctypes.c_int]
+    L.grp_get_state.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int]
+    L.grp_get_stats.argtypes = [_vp, _vp, _vp]
+    L.grp_error_norms.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, _vp]
+    L.grp_launch_count.argtypes = [_vp]
+    L.grp_launch_count.restype = ctypes.c_longlong
+    L.grp_set_kernel_timing.argtypes = [_vp, ctypes.c_int]
+    L.grp_get_kernel_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+    L.grp_probe_fp64_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.grp_destroy.argtypes = [_vp]
+    L.grp_destroy.restype = None
+    L.grp_status_string.argtypes = [ctypes.c_int]
+    L.grp_status_string.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def grp_probe_fp64_peak(device=0):
+    """Measured FP64 FLOP/s of the device (FMA chains; an FMA counts 2)."""
+    v = ctypes.c_double(0.0)
+    _check(load().grp_probe_fp64_peak(int(device), ctypes.byref(v)), "grp_probe_fp64_peak")
+    return v.value
+
+
+def grp_status_string(code):
+    return load().grp_status_string(int(code)).decode()
+
+
+def _check(rc, what):
+    if rc != GRP_OK:
+        raise GrpError("%s failed: %s (%d)" % (what, grp_status_string(rc), rc))
+
+
+def _ptr(x):
+    """(address, is_device) of a numpy array or a torch tensor."""
+    if x is None:
+        return None, 0
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise GrpError("tensor must be contiguous")
+        return x.data_ptr(), 1 if x.is_cuda else 0
+    return x.ctypes.data, 0
+
+
+class Solver:
+    """One grp_ctx.  ``prob`` uses the keys of ``inputs`` problems."""
+
+    def __init__(self, prob, device=0, stream=None, guess=None, dt_hold=None):
+        L = load()
+        self._keep = dict(n=np.ascontiguousarray(prob["n_cells"], dtype=np.int32),
+                          xl=np.ascontiguousarray(prob["x_left"], dtype=np.float64),
+                          xr=np.ascontiguousarray(prob["x_right"], dtype=np.float64),
+                          bc=np.ascontiguousarray(prob["bc"], dtype=np.int32))
+        k = self._keep
+        p = grp_problem()
+        p.system = int(prob["system"])
+        p.lambda_ = float(prob.get("lam", 1.0))
+        p.gamma = float(prob.get("gamma", 1.4))
+        p.M = int(prob["M"])
+        p.cfl = float(prob["cfl"])
+        p.n_domains = len(k["n"])
+        p.n_cells = k["n"].ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        p.x_left = k["xl"].ctypes.data_as(_D)
+        p.x_right = k["xr"].ctypes.data_as(_D)
+        p.bc = k["bc"].ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        p.newton_rtol = float(prob.get("newton_rtol", 1e-12))
+        p.newton_max_iter = int(prob.get("newton_max_iter", 50))
+        p.guess = int(prob.get("guess", 0) if guess is None else guess)
+        p.dt_hold = int(prob.get("dt_hold", 1) if dt_hold is None else dt_hold)
+        p.device = int(device)
+        p.stream = stream
+        self.prob = prob
+        self.C = 3 if p.system == GRP_EULER_IDEAL else 1
+        self.D = p.n_domains
+        self.ncell = int(k["n"].sum())
+        self.nif = int(np.sum(k["n"] + (k["bc"] == GRP_BC_TRANSMISSIVE)))
+        h = _vp()
+        _check(L.grp_create(ctypes.byref(h), ctypes.byref(p)), "grp_create")
+        self.h = h
+        self.L = L
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.grp_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def set_initial(self, avg, lim_minus, lim_plus=None):
+        a, da = _ptr(avg)
+        m, dm = _ptr(lim_minus)
+        q, dq = _ptr(lim_plus)
+        if not (da == dm and (q is None or dq == da)):
+            raise GrpError("all initial buffers must live on the same side")
+        for x, n in ((avg, self.C * self.ncell), (lim_minus, self.C * self.nif), (lim_plus, self.C * self.nif)):
+            if x is not None and (x.dtype != np.float64 if isinstance(x, np.ndarray) else str(x.dtype) != "torch.float64"):
+                raise GrpError("buffers must be float64")
+            if x is not None and (x.size if isinstance(x, np.ndarray) else x.numel()) != n:
+                raise GrpError("buffer size mismatch")
+        _check(self.L.grp_set_initial(self.h, a, m, q, da), "grp_set_initial")
+
+    def step(self, n, t_end=np.inf):
+        _check(self.L.grp_step(self.h, int(n), float(t_end)), "grp_step")
+
+    def advance_to(self, t_end, max_steps=10 ** 7):
+        _check(self.L.grp_advance_to(self.h, float(t_end), int(max_steps)), "grp_advance_to")
+
+    def get_state(self, avg=None, iface=None, t=None):
+        """Host numpy copies (allocated here when not given) or device tensors."""
+        if avg is None and iface is None and t is None:
+            avg = np.empty((self.C, self.ncell))
+            iface = np.empty((self.C, self.nif))
+            t = np.empty(self.D)
+        a, da = _ptr(avg)
+        i, di = _ptr(iface)
+        tt, dt = _ptr(t)
+        dev = max(da, di, dt)
+        _check(self.L.grp_get_state(self.h, a, i, tt, dev), "grp_get_state")
+        return avg, iface, t
+
+    def get_stats(self):
+        stats = np.zeros((self.D, GRP_NSTATS), dtype=np.uint64)
+        status = np.zeros(self.D, dtype=np.int32)
+        _check(self.L.grp_get_stats(self.h, stats.ctypes.data, status.ctypes.data), "grp_get_stats")
+        return stats, status
+
+    def error_norms(self, exact):
+        e, de = _ptr(exact)
+        l1, l2, li = np.zeros(self.D), np.zeros(self.D), np.zeros(self.D)
+        _check(self.L.grp_error_norms(self.h, e, de, l1.ctypes.data, l2.ctypes.data, li.ctypes.data),
+               "grp_error_norms")
+        return l1, l2, li
+
+    def set_kernel_timing(self, on=True):
+        _check(self.L.grp_set_kernel_timing(self.h, 1 if on else 0), "grp_set_kernel_timing")
+
+    def kernel_timing(self):
+        """(summed flux-kernel milliseconds, timed launches) since the last call."""
+        ms, n = ctypes.c_double(0.0), ctypes.c_longlong(0)
+        _check(self.L.grp_get_kernel_timing(self.h, ctypes.byref(ms), ctypes.byref(n)), "grp_get_kernel_timing")
+        return ms.value, n.value
+
+    def launch_count(self):
+        return int(self.L.grp_launch_count(self.h))

@@ -1,0 +1,60 @@
+"""Shared helpers of the GPU-vs-oracle parity tests."""
+import numpy as np
+
+import oracle as O
+from paper_2602_21911_gb300 import inputs as I
+
+SMOOTH_TOL = 1e-11        # max relative cell difference on smooth runs
+DISC_TOL = 1e-9           # ... on discontinuous runs
+
+
+def oracle_run(prob, avg, lm, lp, n_steps, t_end=np.inf, threads=1):
+    st, g = O.init_iface(prob["system"], prob.get("lam", 1.0), prob.get("gamma", 1.4), lm, lp)
+    S = O.State(prob, avg, g)
+    O.run(prob, S, n_steps, t_end=t_end, n_threads=threads)
+    return S
+
+
+def gpu_run(prob, avg, lm, lp, n_steps, t_end=np.inf, solver=None, **kw):
+    from paper_2602_21911_gb300 import grprec
+    s = solver or grprec.Solver(prob, **kw)
+    s.set_initial(np.ascontiguousarray(avg), np.ascontiguousarray(lm), np.ascontiguousarray(lp))
+    s.step(n_steps, t_end)
+    a, g, t = s.get_state()
+    stats, status = s.get_stats()
+    return s, a, g, t, stats, status
+
+
+def rel_diff(a, b, prob):
+    """Per domain and component: max_i |a_i - b_i| / max_i |b_i| (normwise)."""
+    co = I.cell_offsets(prob)
+    out = np.zeros((len(co) - 1, a.shape[0]))
+    for d in range(len(co) - 1):
+        sa, sb = a[:, co[d]:co[d + 1]], b[:, co[d]:co[d + 1]]
+        den = np.maximum(np.abs(sb).max(axis=1), 1e-300)
+        out[d] = np.abs(sa - sb).max(axis=1) / den
+    return out
+
+
+def rel_diff_iface(a, b, prob):
+    io = I.iface_offsets(prob)
+    out = np.zeros((len(io) - 1, a.shape[0]))
+    for d in range(len(io) - 1):
+        sa, sb = a[:, io[d]:io[d + 1]], b[:, io[d]:io[d + 1]]
+        den = np.maximum(np.abs(sb).max(axis=1), 1e-300)
+        out[d] = np.abs(sa - sb).max(axis=1) / den
+    return out
+
+
+def check_parity(prob, avg, lm, lp, n_steps, tol, t_end=np.inf, **kw):
+    S = oracle_run(prob, avg, lm, lp, n_steps, t_end)
+    s, a, g, t, stats, status = gpu_run(prob, avg, lm, lp, n_steps, t_end, **kw)
+    assert np.array_equal(status, S.status), (status, S.status)
+    ok = S.status == 0
+    assert np.array_equal(stats[ok, 0].astype(np.int64), S.stats[ok, 0]), "step counts differ"
+    assert np.allclose(t[ok], S.t[ok], rtol=1e-12, atol=0)
+    rd = rel_diff(a, S.avg, prob)[ok]
+    ri = rel_diff_iface(g, S.iface, prob)[ok]
+    assert rd.max() <= tol, ("averages", rd.max())
+    assert ri.max() <= tol, ("interface data", ri.max())
+    return S, (a, g, t, stats, status), rd.max()

@@ -1,0 +1,135 @@
+"""GPU (C-ABI library) against the CPU oracle on the same seeded inputs.
+
+Tolerances: max relative cell difference 1e-11 on smooth runs and 1e-9 on
+discontinuous runs, per domain and component, for the averages and the
+interface data; step counts and statuses must agree exactly."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2602_21911_gb300 import inputs as I
+
+from parity import DISC_TOL, SMOOTH_TOL, check_parity, gpu_run, oracle_run, rel_diff
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+def test_advection_sine_to_t1(M):
+    prob, avg, lm, lp = I.advection_sine(100, M=M)
+    S, G, rd = check_parity(prob, avg, lm, lp, 10 ** 6, SMOOTH_TOL, t_end=1.0)
+    assert S.t[0] == 1.0
+
+
+def test_advection_many_tiles_ragged_tail():
+    prob, avg, lm, lp = I.advection_sine(1000 + 37, M=2)
+    check_parity(prob, avg, lm, lp, 60, SMOOTH_TOL)
+
+
+def test_advection_negative_speed():
+    prob, avg, lm, lp = I.advection_sine(77, M=3)
+    prob = dict(prob, lam=-1.3)
+    check_parity(prob, avg, lm, lp, 10 ** 6, SMOOTH_TOL, t_end=0.5)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+@pytest.mark.parametrize("N", [64, 100])
+def test_euler_wave_to_t1(M, N):
+    prob, avg, lm, lp = I.euler_wave(N, M)
+    check_parity(prob, avg, lm, lp, 10 ** 6, SMOOTH_TOL, t_end=1.0)
+
+
+def test_euler_wave_transmissive_ragged():
+    prob, avg, lm, lp = I.euler_wave(301, 2, bc=I.TRANSMISSIVE)
+    check_parity(prob, avg, lm, lp, 80, SMOOTH_TOL)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+def test_sod(M):
+    prob, avg, lm, lp = I.sod(256, M=M)
+    S, G, rd = check_parity(prob, avg, lm, lp, 10 ** 6, DISC_TOL, t_end=0.2)
+    assert S.stats[0, O.ST_LOW_ORDER] > 0        # the repair path ran on both sides
+
+
+def test_sod_odd_grid_many_tiles():
+    prob, avg, lm, lp = I.sod(1001)
+    check_parity(prob, avg, lm, lp, 120, DISC_TOL)
+
+
+def test_batched_subset_100_steps():
+    ids = np.arange(0, 65536, 173)[:300]
+    prob, avg, lm, lp = I.batched(domains=ids)
+    S, G, rd = check_parity(prob, avg, lm, lp, 100, DISC_TOL)
+
+
+def test_batched_stats_agree():
+    ids = np.arange(0, 65536, 997)[:60]
+    prob, avg, lm, lp = I.batched(domains=ids)
+    S, (a, g, t, stats, status), rd = check_parity(prob, avg, lm, lp, 60, DISC_TOL)
+    ok = S.status == 0
+    for k in (O.ST_RS_CALLS, O.ST_RECON_FB, O.ST_LOW_ORDER, O.ST_FLUX_FB):
+        assert np.array_equal(stats[ok, k].astype(np.int64), S.stats[ok, k]), k
+
+
+def test_single_cell_domains_and_tiny_domains():
+    """Degenerate grids: one cell (periodic and transmissive), two and three cells."""
+    for N in (1, 2, 3):
+        prob, avg, lm, lp = I.advection_sine(N, M=2)
+        check_parity(prob, avg, lm, lp, 5, SMOOTH_TOL)
+        prob, avg, lm, lp = I.sod(N, M=2)
+        check_parity(prob, avg, lm, lp, 5, DISC_TOL)
+
+
+def test_zero_steps_and_finished_domains_do_not_move():
+    prob, avg, lm, lp = I.euler_wave(40, 2)
+    from paper_2602_21911_gb300 import grprec
+    s = grprec.Solver(prob)
+    s.set_initial(avg, lm, lp)
+    s.step(0)
+    a, g, t = s.get_state()
+    assert np.array_equal(a, avg) and t[0] == 0.0
+    s.step(1000, 0.01)
+    a1, g1, t1 = s.get_state()
+    assert t1[0] == 0.01
+    s.step(5, 0.01)                            # already at t_end: nothing moves
+    a2, g2, t2 = s.get_state()
+    assert np.array_equal(a1, a2) and np.array_equal(g1, g2)
+
+
+def test_dt_hold():
+    prob, avg, lm, lp = I.sod(300)
+    prob = dict(prob, dt_hold=4)
+    check_parity(prob, avg, lm, lp, 40, DISC_TOL)
+
+
+def test_advance_to_and_norms():
+    prob, avg, lm, lp = I.euler_wave(128, 3)
+    from paper_2602_21911_gb300 import grprec
+    s = grprec.Solver(prob)
+    s.set_initial(avg, lm, lp)
+    s.advance_to(1.0)
+    a, g, t = s.get_state()
+    S = oracle_run(prob, avg, lm, lp, 10 ** 6, 1.0)
+    assert t[0] == 1.0 and rel_diff(a, S.avg, prob).max() < SMOOTH_TOL
+    ex = I.euler_wave_exact(128, 1.0)
+    l1, l2, li = s.error_norms(np.ascontiguousarray(ex[0]))
+    e = np.abs(S.avg[0] - ex[0])
+    assert l1[0] == pytest.approx(e.sum() / 128, rel=1e-6)
+    assert li[0] == pytest.approx(e.max(), rel=1e-6)
+
+
+def test_device_pointers_through_torch():
+    torch = pytest.importorskip("torch")
+    prob, avg, lm, lp = I.euler_wave(64, 2)
+    from paper_2602_21911_gb300 import grprec
+    st = torch.cuda.Stream()
+    s = grprec.Solver(prob, stream=st.cuda_stream)
+    with torch.cuda.stream(st):
+        da = torch.tensor(avg, device="cuda").contiguous()
+        dm = torch.tensor(lm, device="cuda").contiguous()
+        s.set_initial(da, dm, dm)
+        s.step(50)
+        out = torch.empty_like(da)
+        s.get_state(avg=out)
+    S = oracle_run(prob, avg, lm, lp, 50)
+    assert rel_diff(out.cpu().numpy(), S.avg, prob).max() < SMOOTH_TOL
