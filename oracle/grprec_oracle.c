@@ -20,39 +20,48 @@
 
 #ifndef OR_REAL_DEFINED
 typedef double real;
+#define OR_DATA(x) (x)        /* marks a value read from the state (op counting) */
 #endif
 
 #define MAXM 4
 #define MAXC 3
+/* READING: signs decided in the Riemann solvers (the contact side, the upwind
+ * side of a derivative Riemann problem) treat |speed| <= OR_TIE x (wave-speed
+ * scale) as zero, so a stationary contact is not decided by rounding noise. */
+#define OR_TIE 1e-10
+#ifndef OR_DMP_REL
+#define OR_DMP_REL 1e-2
+#endif
 #ifndef OR_MAX_REPAIR
 #define OR_MAX_REPAIR 4
 #endif
 
 /* ------------------------------------------------------------------------- */
 /* Small dense linear algebra: Gaussian elimination with partial pivoting.   */
+/* (data-independent systems only, so plain double)                          */
 /* ------------------------------------------------------------------------- */
-static int solve_dense(int n, real *A /* n*n row-major, destroyed */, real *x /* rhs in, sol out */)
+static int solve_dense_d(int n, double *A /* n*n row-major, destroyed */, double *x /* rhs in, sol out */)
 {
   for (int k = 0; k < n; ++k) {
     int piv = k;
-    real best = fabs(A[k * n + k]);
+    double best = fabs(A[k * n + k]);
     for (int r = k + 1; r < n; ++r) {
-      real v = fabs(A[r * n + k]);
+      double v = fabs(A[r * n + k]);
       if (v > best) { best = v; piv = r; }
     }
     if (!(best > 0)) return -1;
     if (piv != k) {
-      for (int c = 0; c < n; ++c) { real tmp = A[k * n + c]; A[k * n + c] = A[piv * n + c]; A[piv * n + c] = tmp; }
-      real tmp = x[k]; x[k] = x[piv]; x[piv] = tmp;
+      for (int c = 0; c < n; ++c) { double tmp = A[k * n + c]; A[k * n + c] = A[piv * n + c]; A[piv * n + c] = tmp; }
+      double tmp = x[k]; x[k] = x[piv]; x[piv] = tmp;
     }
     for (int r = k + 1; r < n; ++r) {
-      real f = A[r * n + k] / A[k * n + k];
+      double f = A[r * n + k] / A[k * n + k];
       for (int c = k; c < n; ++c) A[r * n + c] = A[r * n + c] - f * A[k * n + c];
       x[r] = x[r] - f * x[k];
     }
   }
   for (int k = n - 1; k >= 0; --k) {
-    real s = x[k];
+    double s = x[k];
     for (int c = k + 1; c < n; ++c) s = s - A[k * n + c] * x[c];
     x[k] = s / A[k * n + k];
   }
@@ -65,15 +74,15 @@ static int solve_dense(int n, real *A /* n*n row-major, destroyed */, real *x /*
 /*   point value  p(xi0)                    -> [xi0^k]                        */
 /*   cell average (1/dx) int p dx over [a,b] -> [(b^{k+1}-a^{k+1})/(k+1)]      */
 /* ------------------------------------------------------------------------- */
-static void row_point(int M, real xi0, real *row)
+static void row_point_d(int M, double xi0, double *row)
 {
-  real v = 1;
+  double v = 1;
   for (int k = 0; k <= M; ++k) { row[k] = v; v = v * xi0; }
 }
 
-static void row_average(int M, real a, real b, real *row)
+static void row_average_d(int M, double a, double b, double *row)
 {
-  real pa = a, pb = b;
+  double pa = a, pb = b;
   for (int k = 0; k <= M; ++k) { row[k] = (pb - pa) / (k + 1); pa = pa * a; pb = pb * b; }
 }
 
@@ -88,43 +97,43 @@ static void row_average(int M, real a, real b, real *row)
  * are printed.  The minimiser of |A c - b|^2 subject to C c = d solves the
  * KKT system [2 A^T A, -C^T; C, 0] [c; mu] = [2 A^T b; d].
  */
-int or_recon(int M, const double *qbar, const double *g, double *coef)
+static int recon_kkt(int M, const double *qbar, const double *g, double *coef)
 {
-  real Arows[4][MAXM + 1], b[4];
-  real Crows[5][MAXM + 1], d[5];
+  double Arows[4][MAXM + 1], b[4];
+  double Crows[5][MAXM + 1], d[5];
   int nA = 0, nC = 0;
-  const real half = 0.5, three_half = 1.5;
+  const double half = 0.5, three_half = 1.5;
   if (M < 1 || M > MAXM) return -1;
 
   if (M == 1 || M == 3) {
-    row_point(M, -half, Arows[nA]); b[nA++] = g[0];
-    row_point(M, half, Arows[nA]); b[nA++] = g[1];
+    row_point_d(M, -half, Arows[nA]); b[nA++] = g[0];
+    row_point_d(M, half, Arows[nA]); b[nA++] = g[1];
     if (M == 3) {
-      row_average(M, half, three_half, Arows[nA]); b[nA++] = qbar[2];
-      row_average(M, -three_half, -half, Arows[nA]); b[nA++] = qbar[0];
+      row_average_d(M, half, three_half, Arows[nA]); b[nA++] = qbar[2];
+      row_average_d(M, -three_half, -half, Arows[nA]); b[nA++] = qbar[0];
     }
-    row_average(M, -half, half, Crows[nC]); d[nC++] = qbar[1];
+    row_average_d(M, -half, half, Crows[nC]); d[nC++] = qbar[1];
   } else {
-    row_point(M, -half, Crows[nC]); d[nC++] = g[0];
-    row_point(M, half, Crows[nC]); d[nC++] = g[1];
-    row_average(M, -half, half, Crows[nC]); d[nC++] = qbar[1];
+    row_point_d(M, -half, Crows[nC]); d[nC++] = g[0];
+    row_point_d(M, half, Crows[nC]); d[nC++] = g[1];
+    row_average_d(M, -half, half, Crows[nC]); d[nC++] = qbar[1];
     if (M == 4) {
-      row_average(M, -three_half, -half, Crows[nC]); d[nC++] = qbar[0];
-      row_average(M, half, three_half, Crows[nC]); d[nC++] = qbar[2];
+      row_average_d(M, -three_half, -half, Crows[nC]); d[nC++] = qbar[0];
+      row_average_d(M, half, three_half, Crows[nC]); d[nC++] = qbar[2];
     }
   }
 
   int nu = M + 1, n = nu + nC;
-  real K[(MAXM + 1 + 5) * (MAXM + 1 + 5)], rhs[MAXM + 1 + 5];
+  double K[(MAXM + 1 + 5) * (MAXM + 1 + 5)], rhs[MAXM + 1 + 5];
   for (int i = 0; i < n * n; ++i) K[i] = 0;
   for (int i = 0; i < n; ++i) rhs[i] = 0;
   for (int r = 0; r < nu; ++r) {
     for (int c = 0; c < nu; ++c) {
-      real s = 0;
+      double s = 0;
       for (int k = 0; k < nA; ++k) s = s + Arows[k][r] * Arows[k][c];
       K[r * n + c] = 2 * s;
     }
-    real s = 0;
+    double s = 0;
     for (int k = 0; k < nA; ++k) s = s + Arows[k][r] * b[k];
     rhs[r] = 2 * s;
     for (int j = 0; j < nC; ++j) K[r * n + nu + j] = -Crows[j][r];
@@ -133,9 +142,50 @@ int or_recon(int M, const double *qbar, const double *g, double *coef)
     for (int c = 0; c < nu; ++c) K[(nu + j) * n + c] = Crows[j][c];
     rhs[nu + j] = d[j];
   }
-  if (solve_dense(n, K, rhs) != 0) return -1;
+  if (solve_dense_d(n, K, rhs) != 0) return -1;
   for (int k = 0; k <= M; ++k) coef[k] = rhs[k];
   for (int k = M + 1; k <= MAXM; ++k) coef[k] = 0;
+  return 0;
+}
+
+/* The minimiser is linear in the data (q_{i-1}, q_i, q_{i+1}, g_{i-1/2},
+ * g_{i+1/2}); column j of the operator is the KKT solution for unit datum j.
+ * The operator depends on M only and is built once. */
+static double recon_op[MAXM + 1][MAXM + 1][5];
+static int recon_op_ready[MAXM + 1];
+
+static const double (*recon_operator(int M))[5]
+{
+  if (!recon_op_ready[M]) {
+    for (int j = 0; j < 5; ++j) {
+      double unit[5] = { 0, 0, 0, 0, 0 }, cf[MAXM + 1];
+      unit[j] = 1;
+      recon_kkt(M, unit, unit + 3, cf);
+      for (int k = 0; k <= MAXM; ++k) recon_op[M][k][j] = cf[k];
+    }
+    recon_op_ready[M] = 1;
+  }
+  return (const double (*)[5])recon_op[M];
+}
+
+/* coefficients of cell i from data = {q_{i-1}, q_i, q_{i+1}, g_{i-1/2}, g_{i+1/2}} */
+static void recon_apply(int M, const real *data, real *coef)
+{
+  const double (*op)[5] = recon_operator(M);
+  for (int k = 0; k <= MAXM; ++k) {
+    real s = 0;
+    for (int j = 0; j < 5; ++j)
+      if (op[k][j] != 0) s = s + op[k][j] * data[j];
+    coef[k] = k <= M ? s : (real)0;
+  }
+}
+
+int or_recon(int M, const double *qbar, const double *g, double *coef)
+{
+  if (M < 1 || M > MAXM) return -1;
+  real data[5] = { qbar[0], qbar[1], qbar[2], g[0], g[1] }, cf[MAXM + 1];
+  recon_apply(M, data, cf);
+  for (int k = 0; k <= MAXM; ++k) coef[k] = (double)cf[k];
   return 0;
 }
 
@@ -263,11 +313,13 @@ static int star_pressure(real gamma, const real *WL, const real *WR, int guess_k
   return OR_OK;
 }
 
-/* Self-similar solution sampled at x/t = 0.  READING: u* = 0 takes the left side. */
+/* Self-similar solution sampled at x/t = 0.  READING: a contact speed u* with
+ * |u*| <= OR_TIE (c_L + c_R) counts as stationary and takes the left side. */
 static void sample_at_zero(real gamma, const real *WL, const real *WR, real pstar, real ustar, real *W)
 {
   real g1 = (gamma - 1) / (2 * gamma), g6 = (gamma - 1) / (gamma + 1);
-  if (ustar >= 0) {
+  real tie = OR_TIE * (sqrt(gamma * WL[2] / WL[0]) + sqrt(gamma * WR[2] / WR[0]));
+  if (ustar >= -tie) {
     real c = sqrt(gamma * WL[2] / WL[0]);
     real ratio = pstar / WL[2];
     if (pstar > WL[2]) {
@@ -366,20 +418,18 @@ static void deriv_rp(real gamma, const real *Q0, const real *DL, const real *DR,
                 u - c, u, u + c,
                 H - u * c, 0.5 * u * u, H + u * c };
   real lam[3] = { u - c, u, u + c };
-  /* left eigenvectors: rows of R^{-1}, by elimination on R e_j */
-  real Linv[9];
-  for (int j = 0; j < 3; ++j) {
-    real A[9], e[3] = { 0, 0, 0 };
-    for (int i = 0; i < 9; ++i) A[i] = R[i];
-    e[j] = 1;
-    solve_dense(3, A, e);           /* column j of R^{-1} */
-    for (int i = 0; i < 3; ++i) Linv[i * 3 + j] = e[i];
-  }
+  real tie = OR_TIE * (fabs(u) + c);   /* READING: |lambda| within this counts as zero */
+  /* left eigenvectors (rows of R^{-1}, textbook closed form), with
+   * b1 = (gamma-1)/c^2 and b2 = b1 u^2 / 2 */
+  real b1 = (gamma - 1) / (c * c), b2 = 0.5 * b1 * u * u;
+  real Linv[9] = { 0.5 * (b2 + u / c), -0.5 * (b1 * u + 1 / c), 0.5 * b1,
+                   1 - b2, b1 * u, -b1,
+                   0.5 * (b2 - u / c), -0.5 * (b1 * u - 1 / c), 0.5 * b1 };
   for (int c0 = 0; c0 < 3; ++c0) D[c0] = 0;
   for (int j = 0; j < 3; ++j) {
     real wl = 0, wr = 0;
     for (int k = 0; k < 3; ++k) { wl = wl + Linv[j * 3 + k] * DL[k]; wr = wr + Linv[j * 3 + k] * DR[k]; }
-    real w = lam[j] > 0 ? wl : (lam[j] < 0 ? wr : 0.5 * (wl + wr));
+    real w = lam[j] > tie ? wl : (lam[j] < -tie ? wr : 0.5 * (wl + wr));
     for (int k = 0; k < 3; ++k) D[k] = D[k] + R[k * 3 + j] * w;
   }
 }
@@ -623,6 +673,33 @@ static real domain_smax(const params *P, int N, const real *avg, long stride)
   return smax;
 }
 
+/* Relaxed discrete maximum principle on density and pressure: the candidate
+ * must lie within [min - d, max + d] of the old averages of cells i-1, i,
+ * i+1 (boundary rule for the neighbours), d = OR_DMP_REL * max(|min|, |max|). */
+static int dmp_ok(real gamma, int N, int bc, int i, const real *avg, long cstride, const real *Qc)
+{
+  int nb[3] = { i - 1, i, i + 1 };
+  if (bc == OR_BC_PERIODIC) { nb[0] = (i - 1 + N) % N; nb[2] = (i + 1) % N; }
+  else { if (nb[0] < 0) nb[0] = 0; if (nb[2] > N - 1) nb[2] = N - 1; }
+  real W[3], lo[2], hi[2];
+  for (int k = 0; k < 3; ++k) {
+    real Q[3] = { avg[nb[k]], avg[cstride + nb[k]], avg[2 * cstride + nb[k]] };
+    cons_to_prim(gamma, Q, W);
+    if (k == 0 || W[0] < lo[0]) lo[0] = W[0];
+    if (k == 0 || W[0] > hi[0]) hi[0] = W[0];
+    if (k == 0 || W[2] < lo[1]) lo[1] = W[2];
+    if (k == 0 || W[2] > hi[1]) hi[1] = W[2];
+  }
+  real Wc[3];
+  cons_to_prim(gamma, Qc, Wc);
+  real v[2] = { Wc[0], Wc[2] };
+  for (int q = 0; q < 2; ++q) {
+    real d = OR_DMP_REL * (fabs(lo[q]) > fabs(hi[q]) ? fabs(lo[q]) : fabs(hi[q]));
+    if (!(v[q] >= lo[q] - d && v[q] <= hi[q] + d)) return 0;
+  }
+  return 1;
+}
+
 /* First-order Godunov flux at interface j: exact Riemann problem of the two
  * adjacent cell averages (a transmissive end uses the boundary cell twice). */
 static int first_order_interface(const params *P, int N, int bc, int j, const real *avg, long cstride,
@@ -668,11 +745,9 @@ static int step_domain(const params *P, int N, int bc, real dx, real dt, real *a
     else { if (im < 0) im = 0; if (ip > N - 1) ip = N - 1; }  /* ghost = copy */
     int jl = i, jr = (bc == OR_BC_PERIODIC) ? (i + 1) % N : i + 1;
     for (int c = 0; c < C; ++c) {
-      double qb[3] = { (double)avg[c * cstride + im], (double)avg[c * cstride + i], (double)avg[c * cstride + ip] };
-      double g[2] = { (double)iface[c * istride + jl], (double)iface[c * istride + jr] };
-      double cf[MAXM + 1];
-      or_recon(M, qb, g, cf);
-      for (int k = 0; k <= MAXM; ++k) coef[(i * C + c) * (MAXM + 1) + k] = cf[k];
+      real data[5] = { avg[c * cstride + im], avg[c * cstride + i], avg[c * cstride + ip],
+                       iface[c * istride + jl], iface[c * istride + jr] };
+      recon_apply(M, data, coef + (i * C + c) * (MAXM + 1));
     }
     if (P->system == OR_EULER) {   /* READING: inadmissible trace -> degree 0 */
       int ok = 1;
@@ -685,7 +760,7 @@ static int step_domain(const params *P, int N, int bc, real dx, real dt, real *a
       if (!ok) {
         for (int c = 0; c < 3; ++c)
           for (int k = 0; k <= MAXM; ++k)
-            coef[(i * C + c) * (MAXM + 1) + k] = k == 0 ? avg[c * cstride + i] : 0;
+            coef[(i * C + c) * (MAXM + 1) + k] = k == 0 ? avg[c * cstride + i] : (real)0;
         st[OR_ST_RECON_FB] += 1;
       }
     }
@@ -701,9 +776,9 @@ static int step_domain(const params *P, int N, int bc, real dx, real dt, real *a
     real scale = 1;
     for (int k = 0; k <= M; ++k) {
       for (int c = 0; c < C; ++c) {
-        if (cl < 0) trL[k * C + c] = k == 0 ? avg[c * cstride + 0] : 0;
+        if (cl < 0) trL[k * C + c] = k == 0 ? avg[c * cstride + 0] : (real)0;
         else trL[k * C + c] = poly_deriv(M, coef + (cl * C + c) * (MAXM + 1), k, (real)0.5) / scale;
-        if (cr > N - 1) trR[k * C + c] = k == 0 ? avg[c * cstride + N - 1] : 0;
+        if (cr > N - 1) trR[k * C + c] = k == 0 ? avg[c * cstride + N - 1] : (real)0;
         else trR[k * C + c] = poly_deriv(M, coef + (cr * C + c) * (MAXM + 1), k, (real)-0.5) / scale;
       }
       scale = scale * dx;
@@ -737,14 +812,18 @@ static int step_domain(const params *P, int N, int bc, real dx, real dt, real *a
           cand[c * N + i] = avg[c * cstride + i] - dt / dx * (flux[jr * C + c] - flux[jl * C + c]);
       }
       if (P->system != OR_EULER) break;
-      /* READING (a posteriori, MOOD-like): an inadmissible candidate average
-       * marks its cell troubled; both of its interfaces are recomputed with the
-       * first-order Godunov flux of the cell averages, in at most OR_MAX_REPAIR
-       * rounds; a cell still inadmissible after that freezes the domain. */
+      /* READING (a posteriori, MOOD-like): a candidate average that is
+       * inadmissible, or whose density or pressure leaves the range of the
+       * old averages of cells i-1, i, i+1 by more than OR_DMP_REL of the
+       * range's magnitude, marks its cell troubled; both of its interfaces
+       * are recomputed with the first-order Godunov flux of the cell
+       * averages, in at most OR_MAX_REPAIR rounds.  A cell still
+       * inadmissible at the end freezes the domain. */
       for (int i = 0; i < N && status == OR_OK; ++i) {
         real Q[3] = { cand[i], cand[N + i], cand[2 * N + i] };
-        if (euler_admissible(P->gamma, Q)) continue;
-        bad = 1;
+        int adm = euler_admissible(P->gamma, Q);
+        if (adm && dmp_ok(P->gamma, N, bc, i, avg, cstride, Q)) continue;
+        if (!adm) bad = 1;
         if (pass >= OR_MAX_REPAIR) continue;
         int js[2] = { i, (bc == OR_BC_PERIODIC) ? (i + 1) % N : i + 1 };
         for (int e = 0; e < 2; ++e) {
@@ -756,8 +835,8 @@ static int step_domain(const params *P, int N, int bc, real dx, real dt, real *a
           changed = 1;
         }
       }
-      if (!bad || status != OR_OK) break;
-      if (!changed) { status = OR_NONPHYSICAL; break; }
+      if (status != OR_OK) break;
+      if (!changed) { if (bad) status = OR_NONPHYSICAL; break; }
     }
   }
   if (status == OR_OK || status == OR_NONPHYSICAL) {
@@ -804,8 +883,8 @@ int or_run(int system, double lambda, double gamma, int M, double cfl,
     real *g = (real *)malloc(sizeof(real) * (N + 1) * C);
     const int nif = (int)(ioff[d + 1] - ioff[d]);
     for (int c = 0; c < C; ++c) {
-      for (int i = 0; i < N; ++i) a[c * N + i] = avg[c * ctot + coff[d] + i];
-      for (int j = 0; j < nif; ++j) g[c * nif + j] = iface[c * itot + ioff[d] + j];
+      for (int i = 0; i < N; ++i) a[c * N + i] = OR_DATA(avg[c * ctot + coff[d] + i]);
+      for (int j = 0; j < nif; ++j) g[c * nif + j] = OR_DATA(iface[c * itot + ioff[d] + j]);
     }
     long long *st = stats + (long)d * OR_NSTATS;
     for (int s = 0; s < n_steps; ++s) {
@@ -821,7 +900,7 @@ int or_run(int system, double lambda, double gamma, int M, double cfl,
       if (td + dt >= t_end) { dt = t_end - td; last = 1; }
       int rc = step_domain(&P, N, bc[d], dx, dt, a, N, g, nif, st);
       if (rc != OR_OK && rc != OR_NONPHYSICAL) { status[d] = rc; break; }
-      t[d] = last ? t_end : td + dt;
+      t[d] = last ? t_end : (double)(td + dt);
       nstep[d] += 1;
       dt_prev[d] = dt_cfl;
       st[OR_ST_STEPS] += 1;

@@ -1,0 +1,66 @@
+// Op-counting build of the oracle (measurement infrastructure, never on the
+// product path).  The oracle source is compiled as C++ with `real` a double
+// that counts every FP64 operation with at least one operand derived from the
+// state; operations on constants only (folded by any compiler) are not
+// counted.  Each of + - * / sqrt pow counts one algorithmic flop; negation,
+// fabs and comparisons count none.
+#include <cmath>
+
+namespace opc {
+long long add = 0, mul = 0, dvd = 0, sqr = 0, pw = 0;
+}
+
+struct real {
+  double v;
+  bool k;   // known constant (not derived from the state)
+  real() : v(0.0), k(true) {}
+  real(double x) : v(x), k(true) {}
+  operator double() const { return v; }
+};
+
+static inline real mk(double v, bool k) { real r(v); r.k = k; return r; }
+static inline real or_data(double x) { return mk(x, false); }
+
+#define OR_REAL_DEFINED
+#define OR_DATA(x) or_data(x)
+
+#define BINOP(OP, CTR)                                                                               \
+  static inline real operator OP(real a, real b) { if (!(a.k && b.k)) ++opc::CTR; return mk(a.v OP b.v, a.k && b.k); } \
+  static inline real operator OP(real a, double b) { return a OP real(b); }                         \
+  static inline real operator OP(double a, real b) { return real(a) OP b; }                         \
+  static inline real operator OP(real a, int b) { return a OP real((double)b); }                    \
+  static inline real operator OP(int a, real b) { return real((double)a) OP b; }
+BINOP(+, add)
+BINOP(-, add)
+BINOP(*, mul)
+BINOP(/, dvd)
+#define CMPOP(OP)                                                                  \
+  static inline bool operator OP(real a, real b) { return a.v OP b.v; }            \
+  static inline bool operator OP(real a, double b) { return a.v OP b; }            \
+  static inline bool operator OP(double a, real b) { return a OP b.v; }            \
+  static inline bool operator OP(real a, int b) { return a.v OP (double)b; }       \
+  static inline bool operator OP(int a, real b) { return (double)a OP b.v; }
+CMPOP(<)
+CMPOP(>)
+CMPOP(<=)
+CMPOP(>=)
+CMPOP(==)
+CMPOP(!=)
+static inline real operator-(real a) { return mk(-a.v, a.k); }
+static inline bool operator!(real a) { return !a.v; }
+static inline real sqrt(real a) { if (!a.k) ++opc::sqr; return mk(std::sqrt(a.v), a.k); }
+static inline real fabs(real a) { return mk(std::fabs(a.v), a.k); }
+static inline real pow(real a, real b) { if (!(a.k && b.k)) ++opc::pw; return mk(std::pow(a.v, b.v), a.k && b.k); }
+static inline real pow(real a, double b) { return pow(a, real(b)); }
+
+#include "grprec_oracle.c"
+
+extern "C" void or_opcount(long long *out)
+{
+  out[0] = opc::add; out[1] = opc::mul; out[2] = opc::dvd; out[3] = opc::sqr; out[4] = opc::pw;
+}
+
+extern "C" void or_opcount_reset(void)
+{
+  opc::add = opc::mul = opc::dvd = opc::sqr = opc::pw = 0;
+}

@@ -10,10 +10,19 @@
 #include <math.h>
 #include <stdint.h>
 
+#ifndef GRP_HD
+#define GRP_HD __host__ __device__
+#endif
+
 namespace grp {
 
 enum { SYS_ADV = 0, SYS_EULER = 1 };
 enum { ST_OK = 0, ST_NO_CONV = 1, ST_VACUUM = 2, ST_NONPHYS = 3 };
+
+// Speeds within TIE x (wave-speed scale) of zero count as zero when a sign
+// picks a side (contact sampling, upwinding of derivative Riemann problems):
+// a stationary contact must not be decided by rounding noise.
+constexpr double TIE = 1e-10;
 
 struct Phys {
   double lambda, gamma;
@@ -32,7 +41,7 @@ struct Phys {
 // t_a = p^{(a)}(xi0)/a!.
 // ---------------------------------------------------------------------------
 template <int M>
-__device__ __forceinline__ void grprec_coeffs(double qm, double q0, double qp, double gL, double gR,
+GRP_HD __forceinline__ void grprec_coeffs(double qm, double q0, double qp, double gL, double gR,
                                               double b[5])
 {
   b[0] = q0; b[1] = b[2] = b[3] = b[4] = 0.0;
@@ -53,7 +62,7 @@ __device__ __forceinline__ void grprec_coeffs(double qm, double q0, double qp, d
 
 // Taylor coefficients at the right edge (side = +1) or left edge (side = -1).
 template <int M>
-__device__ __forceinline__ void edge_taylor(const double b[5], double side, double t[M + 1])
+GRP_HD __forceinline__ void edge_taylor(const double b[5], double side, double t[M + 1])
 {
   // p(xi) = b0 + b1 xi + b2 (xi^2 - 1/12) + b3 xi^3 + b4 (xi^4 - 1/80)
   t[0] = b[0] + side * 0.5 * b[1] + b[2] * (1.0 / 6.0) + side * 0.125 * b[3] + b[4] * 0.05;
@@ -68,7 +77,7 @@ __device__ __forceinline__ void edge_taylor(const double b[5], double side, doub
 // ---------------------------------------------------------------------------
 struct Prim { double r, u, p; };
 
-__device__ __forceinline__ Prim to_prim(double g, double r, double m, double E)
+GRP_HD __forceinline__ Prim to_prim(double g, double r, double m, double E)
 {
   Prim w;
   w.r = r;
@@ -77,21 +86,21 @@ __device__ __forceinline__ Prim to_prim(double g, double r, double m, double E)
   return w;
 }
 
-__device__ __forceinline__ void to_cons(double g, Prim w, double Q[3])
+GRP_HD __forceinline__ void to_cons(double g, Prim w, double Q[3])
 {
   Q[0] = w.r;
   Q[1] = w.r * w.u;
   Q[2] = w.p / (g - 1.0) + 0.5 * w.r * w.u * w.u;
 }
 
-__device__ __forceinline__ bool admissible(double g, double r, double m, double E)
+GRP_HD __forceinline__ bool admissible(double g, double r, double m, double E)
 {
   if (!(r > 0.0)) return false;
   const double p = (g - 1.0) * (E - 0.5 * m * (m / r));
   return p > 0.0;
 }
 
-__device__ __forceinline__ void euler_flux(double g, double r, double m, double E, double F[3])
+GRP_HD __forceinline__ void euler_flux(double g, double r, double m, double E, double F[3])
 {
   const double u = m / r;
   const double p = (g - 1.0) * (E - 0.5 * m * u);
@@ -103,7 +112,7 @@ __device__ __forceinline__ void euler_flux(double g, double r, double m, double 
 // ---------------------------------------------------------------------------
 // Exact Riemann solver of the ideal gas: Newton on the star pressure.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void pressure_fn(double g, double p, Prim K, double c, double& f, double& df)
+GRP_HD __forceinline__ void pressure_fn(double g, double p, Prim K, double c, double& f, double& df)
 {
   if (p > K.p) {
     const double A = 2.0 / ((g + 1.0) * K.r);
@@ -120,7 +129,7 @@ __device__ __forceinline__ void pressure_fn(double g, double p, Prim K, double c
 
 // Returns ST_OK / ST_NO_CONV / ST_VACUUM.  p0 > 0 is used as the start when
 // given (learned guess), otherwise PVRS or TRRS per ph.guess.
-static __device__ int star_pressure(const Phys& ph, Prim L, Prim R, double cL, double cR, double p0,
+static GRP_HD int star_pressure(const Phys& ph, Prim L, Prim R, double cL, double cR, double p0,
                              double& ps, double& us, int& iters)
 {
   const double g = ph.gamma;
@@ -166,11 +175,12 @@ static __device__ int star_pressure(const Phys& ph, Prim L, Prim R, double cL, d
   return ST_OK;
 }
 
-// Left of the contact when u* >= 0 (ties go left), sampled on the ray x/t = 0.
-static __device__ Prim sample_zero(double g, Prim L, Prim R, double cL, double cR, double ps, double us)
+// Left of the contact when u* >= 0, sampled on the ray x/t = 0.  A contact
+// speed within TIE of the sound-speed scale is stationary and goes left.
+static GRP_HD Prim sample_zero(double g, Prim L, Prim R, double cL, double cR, double ps, double us)
 {
   const double g1 = (g - 1.0) / (2.0 * g), g6 = (g - 1.0) / (g + 1.0);
-  if (us >= 0.0) {
+  if (us >= -TIE * (cL + cR)) {
     const double ratio = ps / L.p;
     if (ps > L.p) {
       const double S = L.u - cL * sqrt((g + 1.0) / (2.0 * g) * ratio + g1);
@@ -197,7 +207,7 @@ static __device__ Prim sample_zero(double g, Prim L, Prim R, double cL, double c
 }
 
 // Vacuum-generating data: two rarefactions around a vacuum, sampled at x/t = 0.
-static __device__ Prim sample_vacuum_zero(double g, Prim L, Prim R, double cL, double cR)
+static GRP_HD Prim sample_vacuum_zero(double g, Prim L, Prim R, double cL, double cR)
 {
   if (L.u - cL >= 0.0) return L;
   if (L.u + 2.0 * cL / (g - 1.0) > 0.0) {
@@ -214,7 +224,7 @@ static __device__ Prim sample_vacuum_zero(double g, Prim L, Prim R, double cL, d
 
 // Conserved Godunov state at x/t = 0 of conserved data QL | QR.
 // allow_vacuum: vacuum data are sampled and ST_VACUUM returned with Q valid.
-static __device__ int riemann_state(const Phys& ph, const double QL[3], const double QR[3], double p0,
+static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double QR[3], double p0,
                              bool allow_vacuum, double Q[3], int& iters)
 {
   const double g = ph.gamma;
@@ -235,16 +245,17 @@ static __device__ int riemann_state(const Phys& ph, const double QL[3], const do
 // ---------------------------------------------------------------------------
 // Derivative Riemann problem (Toro-Titarev, Section 2): the linear system
 // d_t D + A(Q0) d_x D = 0 with data DL | DR; Godunov value at x/t = 0 by
-// upwinding in the eigenbasis of A(Q0) (a zero eigenvalue averages).
+// upwinding in the eigenbasis of A(Q0) (an eigenvalue within TIE of zero
+// averages the two sides).
 // Eigenvectors of the ideal-gas Jacobian in conserved variables, with
 // H = (E + p)/rho, b1 = (g-1)/c^2, b2 = b1 u^2/2.
 // ---------------------------------------------------------------------------
 struct Eig {
-  double u, c, H, b1, b2, ic;
+  double u, c, H, b1, b2, ic, tie;
   double lam[3];
 };
 
-__device__ __forceinline__ Eig make_eig(double g, const double Q0[3])
+GRP_HD __forceinline__ Eig make_eig(double g, const double Q0[3])
 {
   Eig e;
   const Prim w = to_prim(g, Q0[0], Q0[1], Q0[2]);
@@ -255,10 +266,11 @@ __device__ __forceinline__ Eig make_eig(double g, const double Q0[3])
   e.b1 = (g - 1.0) * e.ic * e.ic;
   e.b2 = 0.5 * e.u * e.u * e.b1;
   e.lam[0] = e.u - e.c; e.lam[1] = e.u; e.lam[2] = e.u + e.c;
+  e.tie = TIE * (fabs(e.u) + e.c);
   return e;
 }
 
-__device__ __forceinline__ void char_proj(const Eig& e, const double D[3], double w[3])
+GRP_HD __forceinline__ void char_proj(const Eig& e, const double D[3], double w[3])
 {
   // rows of R^{-1}
   const double uc = e.u * e.ic;
@@ -267,14 +279,14 @@ __device__ __forceinline__ void char_proj(const Eig& e, const double D[3], doubl
   w[2] = 0.5 * ((e.b2 - uc) * D[0] - (e.b1 * e.u - e.ic) * D[1] + e.b1 * D[2]);
 }
 
-__device__ __forceinline__ void deriv_rp(const Eig& e, const double DL[3], const double DR[3], double D[3])
+GRP_HD __forceinline__ void deriv_rp(const Eig& e, const double DL[3], const double DR[3], double D[3])
 {
   double wl[3], wr[3], w[3];
   char_proj(e, DL, wl);
   char_proj(e, DR, wr);
 #pragma unroll
   for (int j = 0; j < 3; ++j)
-    w[j] = e.lam[j] > 0.0 ? wl[j] : (e.lam[j] < 0.0 ? wr[j] : 0.5 * (wl[j] + wr[j]));
+    w[j] = e.lam[j] > e.tie ? wl[j] : (e.lam[j] < -e.tie ? wr[j] : 0.5 * (wl[j] + wr[j]));
   D[0] = w[0] + w[1] + w[2];
   D[1] = (e.u - e.c) * w[0] + e.u * w[1] + (e.u + e.c) * w[2];
   D[2] = (e.H - e.u * e.c) * w[0] + 0.5 * e.u * e.u * w[1] + (e.H + e.u * e.c) * w[2];
@@ -294,7 +306,7 @@ struct Tri {
 
 // In: q0[c][idx(a,0)] filled for a = 0..M (others ignored).  Out: s[c][b] = q[0][b].
 template <int M>
-__device__ __forceinline__ void ck_euler(double g, double rho[Tri<M>::N], double m[Tri<M>::N],
+GRP_HD __forceinline__ void ck_euler(double g, double rho[Tri<M>::N], double m[Tri<M>::N],
                                          double E[Tri<M>::N], double s[3][M + 1])
 {
   using T = Tri<M>;
@@ -351,18 +363,114 @@ __device__ __forceinline__ void ck_euler(double g, double rho[Tri<M>::N], double
 template <int M>
 struct Gauss {
   static constexpr int G = (M + 2) / 2;
-  __device__ static __forceinline__ double node(int a)
+  GRP_HD static __forceinline__ double node(int a)
   {
     if (G == 1) return 0.5;
     if (G == 2) return a == 0 ? 0.5 - 0.28867513459481288225 : 0.5 + 0.28867513459481288225;
     return a == 0 ? 0.5 - 0.38729833462074168852 : (a == 1 ? 0.5 : 0.5 + 0.38729833462074168852);
   }
-  __device__ static __forceinline__ double weight(int a)
+  GRP_HD static __forceinline__ double weight(int a)
   {
     if (G == 1) return 1.0;
     if (G == 2) return 0.5;
     return a == 1 ? 8.0 / 18.0 : 5.0 / 18.0;
   }
 };
+
+// ---------------------------------------------------------------------------
+// One GRP_M at an interface (Toro-Titarev structure, Section 2) and its flux
+// time integral over [0, dt] (numerical flux, Section 2), in scaled
+// variables: t[c][k] are the Taylor coefficients p^{(k)}/k! of the
+// reconstructions at the interface, nu = dt/dx.  The interface datum for the
+// next step is the series at tau = dt.
+// ---------------------------------------------------------------------------
+template <int M>
+GRP_HD __forceinline__ void grp_adv(double lam, double nu, const double tL[M + 1], const double tR[M + 1],
+                                    double& F, double& gnew)
+{
+  double s[M + 1];
+#pragma unroll
+  for (int k = 0; k <= M; ++k) s[k] = lam > 0.0 ? tL[k] : (lam < 0.0 ? tR[k] : 0.5 * (tL[k] + tR[k]));
+  // CK for q_t + lam q_x = 0: q[0][b] = (-lam)^b q[b][0]
+  double sc = 1.0;
+#pragma unroll
+  for (int k = 0; k <= M; ++k) { s[k] *= sc; sc *= -lam; }
+  double acc = 0.0;
+#pragma unroll
+  for (int al = 0; al < Gauss<M>::G; ++al) {
+    const double T = nu * Gauss<M>::node(al);
+    double v = s[M];
+#pragma unroll
+    for (int k = M - 1; k >= 0; --k) v = v * T + s[k];
+    acc += Gauss<M>::weight(al) * v;
+  }
+  F = lam * acc;
+  double v = s[M];
+#pragma unroll
+  for (int k = M - 1; k >= 0; --k) v = v * nu + s[k];
+  gnew = v;
+}
+
+// Returns ST_OK, or the failure of the leading Riemann problem (the caller
+// then takes the first-order flux).  truncated: a state of the series at a
+// Gauss node or at dt was inadmissible, so the series was cut to its
+// leading term.
+template <int M>
+GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[3][M + 1],
+                                     const double tR[3][M + 1], double F[3], double gnew[3], int& iters,
+                                     bool& truncated)
+{
+  const double g = ph.gamma;
+  const double QL[3] = {tL[0][0], tL[1][0], tL[2][0]}, QR[3] = {tR[0][0], tR[1][0], tR[2][0]};
+  double Q0[3];
+  truncated = false;
+  const int st = riemann_state(ph, QL, QR, 0.0, false, Q0, iters);
+  if (st != ST_OK) return st;
+  using T = Tri<M>;
+  double rho[T::N], m[T::N], E[T::N];
+  rho[0] = Q0[0]; m[0] = Q0[1]; E[0] = Q0[2];
+  {
+    const Eig e = make_eig(g, Q0);
+#pragma unroll
+    for (int k = 1; k <= M; ++k) {
+      const double DL[3] = {tL[0][k], tL[1][k], tL[2][k]}, DR[3] = {tR[0][k], tR[1][k], tR[2][k]};
+      double D[3];
+      deriv_rp(e, DL, DR, D);
+      rho[T::idx(k, 0)] = D[0]; m[T::idx(k, 0)] = D[1]; E[T::idx(k, 0)] = D[2];
+    }
+  }
+  double s[3][M + 1];
+  ck_euler<M>(g, rho, m, E, s);
+  // states at the Gauss nodes and at tau = dt
+  double Qg[Gauss<M>::G + 1][3];
+  bool ok = true;
+#pragma unroll
+  for (int al = 0; al <= Gauss<M>::G; ++al) {
+    const double Tn = al < Gauss<M>::G ? nu * Gauss<M>::node(al) : nu;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double v = s[c][M];
+#pragma unroll
+      for (int k = M - 1; k >= 0; --k) v = v * Tn + s[c][k];
+      Qg[al][c] = v;
+    }
+    ok = ok && admissible(g, Qg[al][0], Qg[al][1], Qg[al][2]);
+  }
+  if (!ok) {
+    truncated = true;
+#pragma unroll
+    for (int al = 0; al <= Gauss<M>::G; ++al) { Qg[al][0] = Q0[0]; Qg[al][1] = Q0[1]; Qg[al][2] = Q0[2]; }
+  }
+  F[0] = F[1] = F[2] = 0.0;
+#pragma unroll
+  for (int al = 0; al < Gauss<M>::G; ++al) {
+    double Fa[3];
+    euler_flux(g, Qg[al][0], Qg[al][1], Qg[al][2], Fa);
+    const double w = Gauss<M>::weight(al);
+    F[0] += w * Fa[0]; F[1] += w * Fa[1]; F[2] += w * Fa[2];
+  }
+  gnew[0] = Qg[Gauss<M>::G][0]; gnew[1] = Qg[Gauss<M>::G][1]; gnew[2] = Qg[Gauss<M>::G][2];
+  return ST_OK;
+}
 
 }  // namespace grp

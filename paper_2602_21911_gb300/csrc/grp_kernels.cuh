@@ -18,6 +18,7 @@ constexpr int NSTATS = 9;
 enum { S_STEPS = 0, S_NEWTON_SUM, S_NEWTON_MAX, S_RECON_FB, S_FLUX_FB, S_RS_CALLS, S_LOW, S_GUESS_USED,
        S_GUESS_REJ };
 constexpr int MAX_REPAIR = 4;   // rounds of the a-posteriori first-order repair
+constexpr double DMP_REL = 1e-2; // relaxation of the discrete maximum principle
 
 struct StepArgs {
   int sys, M, C;
@@ -46,7 +47,8 @@ struct StepArgs {
   int* nstep;                        // [D]
   int* status;                       // [D]
   unsigned long long* smax_bits;     // [D] S_max as the bits of a non-negative double
-  int* bad;                          // [(MAX_REPAIR+1) * D] troubled cells after pass p
+  int* bad;                          // [(MAX_REPAIR+1) * D] troubled cells (repair wanted) after pass p
+  int* inad;                         // [(MAX_REPAIR+1) * D] inadmissible cells after pass p
   int* changed;                      // [MAX_REPAIR * D] interfaces repaired in pass p
   int* fail;                         // [D] non-zero: solver failure code this step
   int* any_bad;                      // [MAX_REPAIR+1] any domain troubled after pass p
@@ -112,7 +114,7 @@ static __global__ void k_smax(StepArgs a)
   if (gi >= a.ncell) return;
   const int d = a.cell_dom[gi];
   if (gi == a.cell_off[d]) {                // one thread per domain resets the step words
-    for (int p = 0; p <= MAX_REPAIR; ++p) a.bad[p * a.n_domains + d] = 0;
+    for (int p = 0; p <= MAX_REPAIR; ++p) a.bad[p * a.n_domains + d] = a.inad[p * a.n_domains + d] = 0;
     for (int p = 0; p < MAX_REPAIR; ++p) a.changed[p * a.n_domains + d] = 0;
     a.fail[d] = 0;
   }
@@ -248,34 +250,13 @@ __device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d,
 
   double F[3] = {0.0, 0.0, 0.0}, gnew[3] = {0.0, 0.0, 0.0};
   if (SYS == SYS_ADV) {
-    const double lam = a.ph.lambda;
-    double s[M + 1];
-#pragma unroll
-    for (int k = 0; k <= M; ++k) s[k] = lam > 0.0 ? tL[0][k] : (lam < 0.0 ? tR[0][k] : 0.5 * (tL[0][k] + tR[0][k]));
-    // CK for q_t + lam q_x = 0: q[0][b] = (-lam)^b q[b][0], in scaled variables
-    double sc = 1.0;
-#pragma unroll
-    for (int k = 0; k <= M; ++k) { s[k] *= sc; sc *= -lam; }
-    double acc = 0.0;
-#pragma unroll
-    for (int al = 0; al < Gauss<M>::G; ++al) {
-      const double T = nu * Gauss<M>::node(al);
-      double v = s[M];
-#pragma unroll
-      for (int k = M - 1; k >= 0; --k) v = v * T + s[k];
-      acc += Gauss<M>::weight(al) * v;
-    }
-    F[0] = lam * acc;
-    double v = s[M];
-#pragma unroll
-    for (int k = M - 1; k >= 0; --k) v = v * nu + s[k];
-    gnew[0] = v;
+    grp_adv<M>(a.ph.lambda, nu, tL[0], tR[0], F[0], gnew[0]);
   } else {
-    const double g = a.ph.gamma;
-    double QL[3] = {tL[0][0], tL[1][0], tL[2][0]}, QR[3] = {tR[0][0], tR[1][0], tR[2][0]}, Q0[3];
     int iters = 0;
-    int rs_st = riemann_state(a.ph, QL, QR, 0.0, false, Q0, iters);
+    bool trunc = false;
+    int rs_st = grp_euler<M>(a.ph, nu, tL, tR, F, gnew, iters, trunc);
     st[2] = 1;
+    st[3] = trunc ? 1u : 0u;
     if (rs_st != ST_OK) {
       // no solution of the traces' Riemann problem: first-order flux here
       int it2 = 0;
@@ -285,50 +266,6 @@ __device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d,
       st[4] = 1;
       a.low[gj] = 1;
       if (rs_st != ST_OK) atomicExch(a.fail + d, rs_st);
-    } else {
-      using T = Tri<M>;
-      double rho[T::N], m[T::N], E[T::N];
-      rho[0] = Q0[0]; m[0] = Q0[1]; E[0] = Q0[2];
-      {
-        const Eig e = make_eig(g, Q0);
-#pragma unroll
-        for (int k = 1; k <= M; ++k) {
-          const double DL[3] = {tL[0][k], tL[1][k], tL[2][k]}, DR[3] = {tR[0][k], tR[1][k], tR[2][k]};
-          double D[3];
-          deriv_rp(e, DL, DR, D);
-          rho[T::idx(k, 0)] = D[0]; m[T::idx(k, 0)] = D[1]; E[T::idx(k, 0)] = D[2];
-        }
-      }
-      double s[3][M + 1];
-      ck_euler<M>(g, rho, m, E, s);
-      // states at the Gauss nodes and at tau = dt
-      double Qg[Gauss<M>::G + 1][3];
-      bool ok = true;
-#pragma unroll
-      for (int al = 0; al <= Gauss<M>::G; ++al) {
-        const double T = al < Gauss<M>::G ? nu * Gauss<M>::node(al) : nu;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          double v = s[c][M];
-#pragma unroll
-          for (int k = M - 1; k >= 0; --k) v = v * T + s[c][k];
-          Qg[al][c] = v;
-        }
-        ok = ok && admissible(g, Qg[al][0], Qg[al][1], Qg[al][2]);
-      }
-      if (!ok) {
-        st[3] = 1;
-#pragma unroll
-        for (int al = 0; al <= Gauss<M>::G; ++al) { Qg[al][0] = Q0[0]; Qg[al][1] = Q0[1]; Qg[al][2] = Q0[2]; }
-      }
-#pragma unroll
-      for (int al = 0; al < Gauss<M>::G; ++al) {
-        double Fa[3];
-        euler_flux(g, Qg[al][0], Qg[al][1], Qg[al][2], Fa);
-        const double w = Gauss<M>::weight(al);
-        F[0] += w * Fa[0]; F[1] += w * Fa[1]; F[2] += w * Fa[2];
-      }
-      gnew[0] = Qg[Gauss<M>::G][0]; gnew[1] = Qg[Gauss<M>::G][1]; gnew[2] = Qg[Gauss<M>::G][2];
     }
     st[0] = (unsigned)iters;
     st[1] = (unsigned)iters;
@@ -400,18 +337,40 @@ __global__ void k_update(StepArgs a, int pass)
     a.avg_new[c * a.ncell + gi] = Q[c];
   }
   if (SYS == SYS_EULER) {
-    const bool ok = admissible(a.ph.gamma, Q[0], Q[1], Q[2]);
+    const double g = a.ph.gamma;
+    const bool adm = admissible(g, Q[0], Q[1], Q[2]);
+    bool ok = adm;
+    if (adm) {
+      // relaxed discrete maximum principle on density and pressure against the
+      // old averages of cells i-1, i, i+1 (boundary rule for the neighbours)
+      int im, ip;
+      nbr(i, N, a.bc[d], im, ip);
+      const int nb[3] = {im, i, ip};
+      double lo0 = 0.0, hi0 = 0.0, lo1 = 0.0, hi1 = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const long long q = c0 + nb[k];
+        const Prim w = to_prim(g, a.avg[q], a.avg[a.ncell + q], a.avg[2 * a.ncell + q]);
+        lo0 = k == 0 ? w.r : fmin(lo0, w.r); hi0 = k == 0 ? w.r : fmax(hi0, w.r);
+        lo1 = k == 0 ? w.p : fmin(lo1, w.p); hi1 = k == 0 ? w.p : fmax(hi1, w.p);
+      }
+      const Prim wc = to_prim(g, Q[0], Q[1], Q[2]);
+      const double d0 = DMP_REL * fmax(fabs(lo0), fabs(hi0)), d1 = DMP_REL * fmax(fabs(lo1), fabs(hi1));
+      ok = wc.r >= lo0 - d0 && wc.r <= hi0 + d0 && wc.p >= lo1 - d1 && wc.p <= hi1 + d1;
+    }
     a.troubled[gi] = ok ? 0 : 1;
-    if (!ok) {
-      const int np = pass + 1;
+    const int np = pass + 1;
+    if (!ok && np < MAX_REPAIR + 1) {
       a.bad[np * a.n_domains + d] = 1;
       a.any_bad[np] = 1;
     }
+    if (!adm) a.inad[np * a.n_domains + d] = 1;
   }
 }
 
 // ------------------------------------------------------------------ repair
-// Interfaces of troubled cells take the first-order Godunov flux (a-posteriori,
+// Interfaces of troubled cells (inadmissible, or outside the relaxed discrete
+// maximum principle) take the first-order Godunov flux (a-posteriori,
 // MOOD-like, bounded to MAX_REPAIR rounds).
 static __device__ __forceinline__ void repair_one(const StepArgs& a, int pass, long long gj, int d, unsigned st[3])
 {
@@ -477,9 +436,10 @@ static __global__ void k_finish(StepArgs a)
   a.dt_prev[d] = dt_cfl;
   a.stats[(long long)d * NSTATS + S_STEPS] += 1;
   if (a.sys == SYS_EULER) {
+    // the committed candidate is the one of the last pass that changed something
     int p = 0;
     while (p < MAX_REPAIR && a.bad[p * a.n_domains + d] && a.changed[p * a.n_domains + d]) ++p;
-    if (a.bad[p * a.n_domains + d]) a.status[d] = ST_NONPHYS;
+    if (a.inad[p * a.n_domains + d]) a.status[d] = ST_NONPHYS;
   }
 }
 

@@ -259,3 +259,25 @@ def test_grp_euler_flux_tends_to_godunov_flux():
         st, F, g, it, tr = O.grp_interface(O.EULER, 0.0, G, M, dt, trL, trR)
         errs.append(np.abs(F - flux(Q0)).max())
     assert errs[0] / errs[1] == pytest.approx(2.0, rel=0.05)
+
+
+# --------------------------------------------------------------------------- tie reading
+def test_stationary_contact_is_not_decided_by_rounding():
+    """A contact speed within 1e-10 of the sound-speed scale counts as zero:
+    the sampled state is the same for u* = 0 and u* = +-1e-14."""
+    WL, WR = (1.0, 0.0, 1.0), (0.5, 0.0, 1.0)           # stationary contact
+    s0 = sample(WL, WR, 0.0)
+    for eps in (1e-14, -1e-14):
+        s1 = sample((1.0, eps, 1.0), (0.5, eps, 1.0), 0.0)
+        assert np.allclose(s1, s0, rtol=1e-12, atol=1e-12)
+    assert s0[0] == pytest.approx(1.0)                 # ties take the left side
+
+
+def test_derivative_rp_tie_averages_and_is_continuous_there():
+    DL, DR = RNG.normal(size=3), RNG.normal(size=3)
+    base = O.deriv_rp(G, cons((1.0, 0.0, 1.0)), DL, DR)
+    for eps in (1e-13, -1e-13):
+        assert np.allclose(O.deriv_rp(G, cons((1.0, eps, 1.0)), DL, DR), base, rtol=1e-10, atol=1e-10)
+    # away from the tie the contact component is upwinded
+    up = O.deriv_rp(G, cons((1.0, 1e-3, 1.0)), DL, DR)
+    assert not np.allclose(up, base, rtol=1e-6)

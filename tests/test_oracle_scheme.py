@@ -192,3 +192,39 @@ def test_initial_interface_data_of_smooth_data_are_point_values():
 def test_step_clips_to_t_end():
     prob, S = run_adv(30, 2, 0.05)
     assert S.t[0] == 0.05
+
+
+def _exact_sod_averages(N, t, nsub=16):
+    """Cell averages of the exact shock-tube solution (x_c = 0.5), by Gauss
+    quadrature of the self-similar solution sampled through Galilean shifts."""
+    xs, ws = np.polynomial.legendre.leggauss(nsub)
+    dx = 1.0 / N
+    out = np.zeros(N)
+    g = 1.4
+    for i in range(N):
+        acc = 0.0
+        for x, w in zip(xs, ws):
+            xi = ((i + 0.5 + 0.5 * x) * dx - 0.5) / t
+            WL = np.array([1.0, -xi, 1.0]); WR = np.array([0.125, -xi, 0.1])
+            QL = np.array([WL[0], WL[0] * WL[1], WL[2] / (g - 1) + 0.5 * WL[0] * WL[1] ** 2])
+            QR = np.array([WR[0], WR[0] * WR[1], WR[2] / (g - 1) + 0.5 * WR[0] * WR[1] ** 2])
+            st, Q, _ = O.riemann_state(g, QL, QR)
+            acc += 0.5 * w * Q[0]
+        out[i] = acc
+    return out
+
+
+def test_sod_converges_to_the_exact_solution():
+    """With the a-posteriori repair (admissibility and a relaxed discrete
+    maximum principle) the degree-2 scheme converges to the exact shock-tube
+    solution: first order in L1, as for any captured discontinuity."""
+    e = []
+    for N in (100, 200, 400):
+        prob, avg, lm, lp = I.sod(N)
+        st, g = O.init_iface(O.EULER, 1.0, 1.4, lm, lp)
+        S = O.State(prob, avg, g)
+        O.run(prob, S, 10 ** 6, t_end=0.2)
+        assert S.status[0] == O.OK
+        e.append(np.abs(S.avg[0] - _exact_sod_averages(N, 0.2)).sum() / N)
+    assert e[0] > 1.5 * e[1] > 2.25 * e[2]
+    assert e[2] < 5e-3
