@@ -124,7 +124,9 @@ int grp_set_initial(grp_ctx *ctx, const double *averages, const double *lim_minu
 /*
  * Advance every active domain by n_steps steps (n_steps >= 0).  A domain stops
  * early when it reaches t_end (the last step is clipped to land on t_end; pass
- * INFINITY for no end) or when its status becomes non-zero.  Asynchronous.
+ * INFINITY for no end) or when its status becomes non-zero.  Asynchronous when
+ * t_end is infinite or n_steps <= 64; with a finite t_end a longer request
+ * synchronises every 64 steps and returns once every domain is done.
  */
 int grp_step(grp_ctx *ctx, int n_steps, double t_end);
 

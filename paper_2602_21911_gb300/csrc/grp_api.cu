@@ -183,6 +183,20 @@ int enqueue_step(grp_ctx* c, double t_end)
   return GRP_OK;
 }
 
+// true when every domain has reached t_end or is frozen (synchronises the stream)
+int all_done(grp_ctx* c, double t_end, bool& done)
+{
+  std::vector<double> ht(c->D);
+  std::vector<int> hs(c->D);
+  CK(cudaMemcpyAsync(ht.data(), c->t, sizeof(double) * c->D, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(hs.data(), c->status, sizeof(int) * c->D, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  done = true;
+  for (int d = 0; d < c->D; ++d)
+    if (hs[d] == GRP_ST_OK && ht[d] < t_end) { done = false; break; }
+  return GRP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -328,7 +342,16 @@ int grp_step(grp_ctx* c, int n_steps, double t_end)
   if (!c->initialized) return GRP_E_NOT_INITIALIZED;
   if (c->p.guess == GRP_GUESS_MLP && !c->mlp) return GRP_E_NO_MODEL;
   CK(cudaSetDevice(c->p.device));
+  // With a finite t_end, long requests test completion every DONE_CHECK steps
+  // so that the steps left after every domain has arrived are not enqueued.
+  const int DONE_CHECK = 64;
   for (int i = 0; i < n_steps; ++i) {
+    if (isfinite(t_end) && i > 0 && i % DONE_CHECK == 0) {
+      bool done = false;
+      const int rc = all_done(c, t_end, done);
+      if (rc) return rc;
+      if (done) break;
+    }
     const int rc = enqueue_step(c, t_end);
     if (rc) return rc;
   }
@@ -339,22 +362,20 @@ int grp_advance_to(grp_ctx* c, double t_end, int max_steps)
 {
   if (!c || !isfinite(t_end) || max_steps < 0) return GRP_E_INVALID_ARG;
   if (!c->initialized) return GRP_E_NOT_INITIALIZED;
-  std::vector<double> ht(c->D);
-  std::vector<int> hs(c->D);
+  CK(cudaSetDevice(c->p.device));
   int done_steps = 0;
   const int block = 32;
   while (true) {
-    CK(cudaMemcpyAsync(ht.data(), c->t, sizeof(double) * c->D, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(hs.data(), c->status, sizeof(int) * c->D, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    bool all = true;
-    for (int d = 0; d < c->D; ++d)
-      if (hs[d] == GRP_ST_OK && ht[d] < t_end) { all = false; break; }
+    bool all = false;
+    const int rc0 = all_done(c, t_end, all);
+    if (rc0) return rc0;
     if (all) return GRP_OK;
     if (done_steps >= max_steps) return GRP_E_MAX_STEPS;
     const int n = max_steps - done_steps < block ? max_steps - done_steps : block;
-    const int rc = grp_step(c, n, t_end);
-    if (rc) return rc;
+    for (int i = 0; i < n; ++i) {
+      const int rc = enqueue_step(c, t_end);
+      if (rc) return rc;
+    }
     done_steps += n;
   }
 }

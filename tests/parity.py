@@ -25,24 +25,31 @@ def gpu_run(prob, avg, lm, lp, n_steps, t_end=np.inf, solver=None, **kw):
     return s, a, g, t, stats, status
 
 
+def _rel(sa, sb):
+    """max_i |a_i - b_i| / max_i |b_i| per component (normwise).  The
+    denominator is floored at 1e-6 of the largest component magnitude of the
+    domain, so that a component that is zero up to round-off (the momentum of
+    a fluid at rest) is compared on the scale of the state."""
+    mag = np.abs(sb).max(axis=1)
+    den = np.maximum(mag, max(1e-6 * mag.max(), 1e-300))
+    return np.abs(sa - sb).max(axis=1) / den
+
+
 def rel_diff(a, b, prob):
-    """Per domain and component: max_i |a_i - b_i| / max_i |b_i| (normwise)."""
+    """Per domain and component, over the cell averages."""
     co = I.cell_offsets(prob)
     out = np.zeros((len(co) - 1, a.shape[0]))
     for d in range(len(co) - 1):
-        sa, sb = a[:, co[d]:co[d + 1]], b[:, co[d]:co[d + 1]]
-        den = np.maximum(np.abs(sb).max(axis=1), 1e-300)
-        out[d] = np.abs(sa - sb).max(axis=1) / den
+        out[d] = _rel(a[:, co[d]:co[d + 1]], b[:, co[d]:co[d + 1]])
     return out
 
 
 def rel_diff_iface(a, b, prob):
+    """Per domain and component, over the interface data."""
     io = I.iface_offsets(prob)
     out = np.zeros((len(io) - 1, a.shape[0]))
     for d in range(len(io) - 1):
-        sa, sb = a[:, io[d]:io[d + 1]], b[:, io[d]:io[d + 1]]
-        den = np.maximum(np.abs(sb).max(axis=1), 1e-300)
-        out[d] = np.abs(sa - sb).max(axis=1) / den
+        out[d] = _rel(a[:, io[d]:io[d + 1]], b[:, io[d]:io[d + 1]])
     return out
 
 
