@@ -30,6 +30,14 @@ sys.path.insert(0, ROOT)
 METRIC = "FP64 cell-updates/s at fixed L1 error, plain vs batched+learned p* guess, 1 GB300"
 UNIT = "cell-updates/s"
 
+# Algorithmic FP64 flops per cell-update of the reconstruction + GRP phase (the
+# work of the flux kernel), counted by the op-counting build of the CPU oracle
+# (oracle/opcount.py) on a sample of each workload: every +, -, *, /, sqrt and
+# pow touching the state counts one.
+FLUX_FLOPS_PER_UPDATE = {("batched", 1): 441.5, ("batched", 2): 766.5, ("batched", 3): 1178.8,
+                         ("batched", 4): 1727.2}
+PROFILE = os.path.join(ROOT, "profiles", "k_flux_batched_m2.txt")
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -88,13 +96,39 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def source_digest():
+    import hashlib
+    d = os.path.join(ROOT, "paper_2602_21911_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(cells):
+    """DRAM bytes per flux launch from the committed ncu summary, scaled from
+    its workload to this one by cell count; None when the kernel source has
+    changed since the capture."""
+    if not os.path.exists(PROFILE):
+        return None
+    kv = {}
+    for line in open(PROFILE):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_digest") != source_digest():
+        return None
+    return float(kv["dram_bytes_per_launch"]) * cells / float(kv["cells_per_launch"])
+
+
 def workload(args, rank):
     from paper_2602_21911_gb300 import inputs as I
     prob, avg, lm, lp = I.batched(args.domains, seed=2602 + rank, M=args.M)
     return prob, avg, lm, lp
 
 
-def cpu_baseline(args, steps=100, stride=16):
+def cpu_baseline(args, steps=100, stride=4):
     """The oracle as it stands, OpenMP over domains, on a bounded sample."""
     import oracle as O
     from paper_2602_21911_gb300 import inputs as I
@@ -157,6 +191,7 @@ def main():
     torch.cuda.set_device(local)
     from paper_2602_21911_gb300 import grprec
     prob, avg, lm, lp = workload(args, rank)
+    peak = grprec.grp_probe_fp64_peak(local)
     stream = torch.cuda.Stream()
     s = grprec.Solver(prob, device=local, stream=stream.cuda_stream)
     s.set_initial(avg, lm, lp)
@@ -222,6 +257,14 @@ def main():
             "flux_kernel": {"ms_total": flux_ms, "launches": flux_n,
                             "share_of_step": flux_ms / ms if ms > 0 else None},
             "frozen_domains": int((status != 0).sum())}
+    flops = FLUX_FLOPS_PER_UPDATE.get(("batched", args.M))
+    if flops and flux_n:
+        ach = flops * (upd / world) / args.steps / (flux_ms / flux_n * 1e-3)
+        line["roofline"] = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                            "frac": ach / peak, "traffic": profiled_traffic(int(prob["n_cells"].sum())),
+                            "kernel": "k_flux<Euler,M=%d>" % args.M,
+                            "peak_source": "measured FP64 FMA-chain probe (grp_probe_fp64_peak), this GPU",
+                            "flops_per_cell_update": flops}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line))

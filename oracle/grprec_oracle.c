@@ -22,6 +22,9 @@
 typedef double real;
 #define OR_DATA(x) (x)        /* marks a value read from the state (op counting) */
 #endif
+#ifndef OR_PHASE
+#define OR_PHASE(k)           /* op counting: 0 CFL, 1 reconstruction + GRP, 2 update + repair */
+#endif
 
 #define MAXM 4
 #define MAXC 3
@@ -737,6 +740,7 @@ static int step_domain(const params *P, int N, int bc, real dx, real dt, real *a
   char *low = (char *)calloc(nif, 1);
   int status = OR_OK;
 
+  OR_PHASE(1);
   /* reconstruction, cell by cell, component by component (READING: conserved
    * variables; linear GRPrec commutes with a per-cell characteristic projection) */
   for (int i = 0; i < N; ++i) {
@@ -801,6 +805,7 @@ static int step_domain(const params *P, int N, int bc, real dx, real dt, real *a
     if (s != OR_OK) status = s;
   }
 
+  OR_PHASE(2);
   real *cand = (real *)malloc(sizeof(real) * N * C);
   if (status == OR_OK) {
     /* conservative update, eq. eq_finite_volume with S = 0 */
@@ -893,7 +898,10 @@ int or_run(int system, double lambda, double gamma, int M, double cfl,
       if (!(td < t_end)) break;
       real dt_cfl;
       if (dt_fixed) dt_cfl = dt_fixed[s];
-      else if (nstep[d] % P.dt_hold == 0 || !(dt_prev[d] > 0)) dt_cfl = P.cfl * dx / domain_smax(&P, N, a, N);
+      else if (nstep[d] % P.dt_hold == 0 || !(dt_prev[d] > 0)) {
+        OR_PHASE(0);
+        dt_cfl = P.cfl * dx / domain_smax(&P, N, a, N);
+      }
       else dt_cfl = dt_prev[d];
       real dt = dt_cfl;
       int last = 0;

@@ -8,6 +8,8 @@
 
 namespace opc {
 long long add = 0, mul = 0, dvd = 0, sqr = 0, pw = 0;
+int phase = 0;
+long long by_phase[3][5];
 }
 
 struct real {
@@ -19,10 +21,18 @@ struct real {
 };
 
 static inline real mk(double v, bool k) { real r(v); r.k = k; return r; }
+static inline void set_phase(int k)
+{
+  long long now[5] = {opc::add, opc::mul, opc::dvd, opc::sqr, opc::pw};
+  static long long last[5];
+  for (int i = 0; i < 5; ++i) { opc::by_phase[opc::phase][i] += now[i] - last[i]; last[i] = now[i]; }
+  opc::phase = k;
+}
 static inline real or_data(double x) { return mk(x, false); }
 
 #define OR_REAL_DEFINED
 #define OR_DATA(x) or_data(x)
+#define OR_PHASE(k) set_phase(k)
 
 #define BINOP(OP, CTR)                                                                               \
   static inline real operator OP(real a, real b) { if (!(a.k && b.k)) ++opc::CTR; return mk(a.v OP b.v, a.k && b.k); } \
@@ -55,12 +65,18 @@ static inline real pow(real a, double b) { return pow(a, real(b)); }
 
 #include "grprec_oracle.c"
 
+// out[phase * 5 + kind]: phases CFL, reconstruction + GRP, update + repair;
+// kinds add, mul, div, sqrt, pow (a single-threaded run is assumed)
 extern "C" void or_opcount(long long *out)
 {
-  out[0] = opc::add; out[1] = opc::mul; out[2] = opc::dvd; out[3] = opc::sqr; out[4] = opc::pw;
+  set_phase(opc::phase);
+  for (int p = 0; p < 3; ++p)
+    for (int i = 0; i < 5; ++i) out[p * 5 + i] = opc::by_phase[p][i];
 }
 
 extern "C" void or_opcount_reset(void)
 {
-  opc::add = opc::mul = opc::dvd = opc::sqr = opc::pw = 0;
+  set_phase(0);
+  for (int p = 0; p < 3; ++p)
+    for (int i = 0; i < 5; ++i) opc::by_phase[p][i] = 0;
 }
