@@ -168,7 +168,8 @@ int enqueue_step(grp_ctx* c, double t_end)
     k_update<SYS_EULER><<<blocks(c->ncell, 256), 256, 0, s>>>(a, -1);
     c->launches++;
     for (int r = 0; r < MAX_REPAIR; ++r) {
-      k_repair_flux<<<blocks(c->nif, 128), 128, 0, s>>>(a, r);
+      if (c->p.gamma == 1.4) k_repair_flux<true><<<blocks(c->nif, 128), 128, 0, s>>>(a, r);
+      else k_repair_flux<false><<<blocks(c->nif, 128), 128, 0, s>>>(a, r);
       k_update<SYS_EULER><<<blocks(c->ncell, 256), 256, 0, s>>>(a, r);
       c->launches += 2;
     }

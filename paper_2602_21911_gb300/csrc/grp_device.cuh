@@ -110,43 +110,126 @@ GRP_HD __forceinline__ void euler_flux(double g, double r, double m, double E, d
 }
 
 // ---------------------------------------------------------------------------
-// Exact Riemann solver of the ideal gas: Newton on the star pressure.
+// Arithmetic helpers.  FP64 is the scarce pipe on this GPU; seeds come from
+// the FP32 special-function unit and are refined by FP64 Newton steps.
 // ---------------------------------------------------------------------------
-GRP_HD __forceinline__ void pressure_fn(double g, double p, Prim K, double c, double& f, double& df)
+GRP_HD __forceinline__ float f32_log2(float x)
+{
+#ifdef __CUDA_ARCH__
+  return __log2f(x);
+#else
+  return log2f(x);
+#endif
+}
+
+GRP_HD __forceinline__ float f32_exp2(float x)
+{
+#ifdef __CUDA_ARCH__
+  return exp2f(x);
+#else
+  return exp2f(x);
+#endif
+}
+
+// 1/y to ~1e-14 relative: FP32 reciprocal seed, one FP64 Newton step.  Used
+// only for the Newton update of the star pressure, whose next iterate corrects
+// any residual of the step.
+GRP_HD __forceinline__ double rcp_newton_step(double y)
+{
+  const float yf = (float)y;
+  const float af = fabsf(yf);
+  if (!(af > 1e-30f && af < 1e30f)) return 1.0 / y;
+  double r = (double)(1.0f / yf);
+  const double e = fma(-y, r, 1.0);
+  return fma(r, e, r);
+}
+
+// x^(-1/7) for x > 0: FP32 seed 2^(-log2(x)/7), then two FP64 Newton steps on
+// w^-7 = x, w <- w (8 - x w^7)/7, each squaring the relative error
+// (2^-21 -> 2^-40 -> rounding).  Outside the FP32 normal range: pow.
+GRP_HD __forceinline__ double inv_root7(double x)
+{
+  const float xf = (float)x;
+  if (!(xf > 1e-36f && xf < 1e36f)) return pow(x, -1.0 / 7.0);
+  double w = (double)f32_exp2(-f32_log2(xf) * (1.0f / 7.0f));
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const double w2 = w * w, w4 = w2 * w2;
+    const double w7 = w4 * w2 * w;
+    w = w * fma(-x, w7, 8.0) * (1.0 / 7.0);
+  }
+  return w;
+}
+
+// ---------------------------------------------------------------------------
+// Exact Riemann solver of the ideal gas: Newton on the star pressure.
+// G75 selects gamma = 7/5, where every power of the solver has exponent
+// k/7 or an integer and comes from one x^(-1/7); otherwise pow() is used.
+// ---------------------------------------------------------------------------
+struct Side {
+  double r, u, p, c;     // primitive state and sound speed
+  double A, B;           // shock branch: A = 2/((g+1) rho), B = (g-1)/(g+1) p
+  double ip;             // 1/p
+  double k;              // rarefaction branch: 2 c/(g-1)
+  double d;              // rarefaction branch: 1/(rho c)
+};
+
+GRP_HD __forceinline__ Side make_side(double g, Prim W)
+{
+  Side s;
+  s.r = W.r; s.u = W.u; s.p = W.p;
+  s.c = sqrt(g * W.p / W.r);
+  s.A = 2.0 / ((g + 1.0) * W.r);
+  s.B = (g - 1.0) / (g + 1.0) * W.p;
+  s.ip = 1.0 / W.p;
+  s.k = 2.0 * s.c / (g - 1.0);
+  s.d = 1.0 / (W.r * s.c);
+  return s;
+}
+
+// pressure function f_K(p) and its derivative
+template <bool G75>
+GRP_HD __forceinline__ void pressure_fn(double g, double p, const Side& K, double& f, double& df)
 {
   if (p > K.p) {
-    const double A = 2.0 / ((g + 1.0) * K.r);
-    const double B = (g - 1.0) / (g + 1.0) * K.p;
-    const double s = sqrt(A / (p + B));
+    const double q = p + K.B;
+    const double s = sqrt(K.A / q);
     f = (p - K.p) * s;
-    df = s * (1.0 - (p - K.p) / (2.0 * (B + p)));
+    df = s * (1.0 - (p - K.p) / (2.0 * q));
+  } else if (G75) {
+    const double x = p * K.ip;
+    const double w = inv_root7(x);
+    const double w2 = w * w, w6 = w2 * w2 * w2;
+    f = K.k * fma(x, w6, -1.0);          // (p/pK)^(1/7) = x * x^(-6/7)
+    df = K.d * w6;                        // (p/pK)^(-6/7)
   } else {
-    const double ratio = p / K.p;
-    f = 2.0 * c / (g - 1.0) * (pow(ratio, (g - 1.0) / (2.0 * g)) - 1.0);
-    df = 1.0 / (K.r * c) * pow(ratio, -(g + 1.0) / (2.0 * g));
+    const double x = p * K.ip;
+    f = K.k * (pow(x, (g - 1.0) / (2.0 * g)) - 1.0);
+    df = K.d * pow(x, -(g + 1.0) / (2.0 * g));
   }
 }
 
 // Returns ST_OK / ST_NO_CONV / ST_VACUUM.  p0 > 0 is used as the start when
 // given (learned guess), otherwise PVRS or TRRS per ph.guess.
-static GRP_HD int star_pressure(const Phys& ph, Prim L, Prim R, double cL, double cR, double p0,
-                             double& ps, double& us, int& iters)
+template <bool G75>
+static GRP_HD int star_pressure(const Phys& ph, const Side& L, const Side& R, double p0, double& ps, double& us,
+                                int& iters)
 {
   const double g = ph.gamma;
   const double du = R.u - L.u;
   iters = 0;
-  if (2.0 * (cL + cR) / (g - 1.0) <= du) return ST_VACUUM;
+  if (2.0 * (L.c + R.c) / (g - 1.0) <= du) return ST_VACUUM;
   const double pfloor = 1e-14 * fmax(L.p, R.p);
   double p;
   if (p0 > 0.0 && isfinite(p0)) {
     p = p0;
   } else if (ph.guess == 1) {
     const double z = (g - 1.0) / (2.0 * g);
-    const double num = cL + cR - 0.5 * (g - 1.0) * du;
-    const double den = cL * pow(L.p, -z) + cR * pow(R.p, -z);
+    const double num = L.c + R.c - 0.5 * (g - 1.0) * du;
+    const double den = L.c * pow(L.p, -z) + R.c * pow(R.p, -z);
     p = pow(num / den, 1.0 / z);
   } else {
-    const double ppv = 0.5 * (L.p + R.p) - 0.125 * du * (L.r + R.r) * (cL + cR);
+    const double ppv = 0.5 * (L.p + R.p) - 0.125 * du * (L.r + R.r) * (L.c + R.c);
     p = fmax(ppv, pfloor);
   }
   if (!(p > pfloor)) p = pfloor;
@@ -154,91 +237,126 @@ static GRP_HD int star_pressure(const Phys& ph, Prim L, Prim R, double cL, doubl
   int it = 0;
   while (it < ph.max_iter) {
     double fL, dfL, fR, dfR;
-    pressure_fn(g, p, L, cL, fL, dfL);
-    pressure_fn(g, p, R, cR, fR, dfR);
-    double step = -(fL + fR + du) / (dfL + dfR);
+    pressure_fn<G75>(g, p, L, fL, dfL);
+    pressure_fn<G75>(g, p, R, fR, dfR);
+    double step = -(fL + fR + du) * rcp_newton_step(dfL + dfR);
     double pn = p + step;
     for (int h = 0; h < 64 && !(pn > 0.0); ++h) { step *= 0.5; pn = p + step; }
     ++it;
-    const double change = 2.0 * fabs(pn - p) / (pn + p);
+    const bool small = 2.0 * fabs(pn - p) < ph.rtol * (pn + p);   // relative change < rtol
     p = pn;
     if (conv) break;
-    if (change < ph.rtol) conv = true;
+    if (small) conv = true;
   }
   iters = it;
   if (!conv) return ST_NO_CONV;
   double fL, dfL, fR, dfR;
-  pressure_fn(g, p, L, cL, fL, dfL);
-  pressure_fn(g, p, R, cR, fR, dfR);
+  pressure_fn<G75>(g, p, L, fL, dfL);
+  pressure_fn<G75>(g, p, R, fR, dfR);
   ps = p;
   us = 0.5 * (L.u + R.u) + 0.5 * (fR - fL);
   return ST_OK;
 }
 
+// Density behind a rarefaction from K to pressure ratio x = p/pK, and the
+// sound speed there: rho = rhoK x^(1/g), c = cK x^((g-1)/(2g)).
+template <bool G75>
+GRP_HD __forceinline__ void rarefied(double g, const Side& K, double x, double& rho, double& c)
+{
+  if (G75) {
+    const double w = inv_root7(x), w2 = w * w;
+    rho = K.r * x * w2;                  // x^(5/7)
+    c = K.c * x * (w2 * w2 * w2);        // x^(1/7)
+  } else {
+    rho = K.r * pow(x, 1.0 / g);
+    c = K.c * pow(x, (g - 1.0) / (2.0 * g));
+  }
+}
+
+// Sonic state inside a fan: rho = rhoK q^(2/(g-1)), p = pK q^(2g/(g-1)), q = c0/cK.
+template <bool G75>
+GRP_HD __forceinline__ Prim sonic(double g, const Side& K, double c0, double u0)
+{
+  const double q = c0 / K.c;
+  if (G75) {
+    const double q2 = q * q, q5 = q2 * q2 * q;
+    return Prim{K.r * q5, u0, K.p * q5 * q2};
+  }
+  return Prim{K.r * pow(q, 2.0 / (g - 1.0)), u0, K.p * pow(q, 2.0 * g / (g - 1.0))};
+}
+
 // Left of the contact when u* >= 0, sampled on the ray x/t = 0.  A contact
 // speed within TIE of the sound-speed scale is stationary and goes left.
-static GRP_HD Prim sample_zero(double g, Prim L, Prim R, double cL, double cR, double ps, double us)
+template <bool G75>
+static GRP_HD Prim sample_zero(double g, const Side& L, const Side& R, double ps, double us)
 {
   const double g1 = (g - 1.0) / (2.0 * g), g6 = (g - 1.0) / (g + 1.0);
-  if (us >= -TIE * (cL + cR)) {
-    const double ratio = ps / L.p;
+  const Prim WL{L.r, L.u, L.p}, WR{R.r, R.u, R.p};
+  if (us >= -TIE * (L.c + R.c)) {
+    const double ratio = ps * L.ip;
     if (ps > L.p) {
-      const double S = L.u - cL * sqrt((g + 1.0) / (2.0 * g) * ratio + g1);
-      if (S >= 0.0) return L;
+      const double S = L.u - L.c * sqrt((g + 1.0) / (2.0 * g) * ratio + g1);
+      if (S >= 0.0) return WL;
       return Prim{L.r * (ratio + g6) / (g6 * ratio + 1.0), us, ps};
     }
-    if (L.u - cL >= 0.0) return L;
-    const double cs = cL * pow(ratio, g1);
-    if (us - cs < 0.0) return Prim{L.r * pow(ratio, 1.0 / g), us, ps};
-    const double c0 = 2.0 / (g + 1.0) * (cL + 0.5 * (g - 1.0) * L.u);
-    return Prim{L.r * pow(c0 / cL, 2.0 / (g - 1.0)), c0, L.p * pow(c0 / cL, 2.0 * g / (g - 1.0))};
+    if (L.u - L.c >= 0.0) return WL;
+    double rho, cs;
+    rarefied<G75>(g, L, ratio, rho, cs);
+    if (us - cs < 0.0) return Prim{rho, us, ps};
+    const double c0 = 2.0 / (g + 1.0) * (L.c + 0.5 * (g - 1.0) * L.u);
+    return sonic<G75>(g, L, c0, c0);
   }
-  const double ratio = ps / R.p;
+  const double ratio = ps * R.ip;
   if (ps > R.p) {
-    const double S = R.u + cR * sqrt((g + 1.0) / (2.0 * g) * ratio + g1);
-    if (S <= 0.0) return R;
+    const double S = R.u + R.c * sqrt((g + 1.0) / (2.0 * g) * ratio + g1);
+    if (S <= 0.0) return WR;
     return Prim{R.r * (ratio + g6) / (g6 * ratio + 1.0), us, ps};
   }
-  if (R.u + cR <= 0.0) return R;
-  const double cs = cR * pow(ratio, g1);
-  if (us + cs > 0.0) return Prim{R.r * pow(ratio, 1.0 / g), us, ps};
-  const double c0 = 2.0 / (g + 1.0) * (cR - 0.5 * (g - 1.0) * R.u);
-  return Prim{R.r * pow(c0 / cR, 2.0 / (g - 1.0)), -c0, R.p * pow(c0 / cR, 2.0 * g / (g - 1.0))};
+  if (R.u + R.c <= 0.0) return WR;
+  double rho, cs;
+  rarefied<G75>(g, R, ratio, rho, cs);
+  if (us + cs > 0.0) return Prim{rho, us, ps};
+  const double c0 = 2.0 / (g + 1.0) * (R.c - 0.5 * (g - 1.0) * R.u);
+  return sonic<G75>(g, R, c0, -c0);
 }
 
 // Vacuum-generating data: two rarefactions around a vacuum, sampled at x/t = 0.
-static GRP_HD Prim sample_vacuum_zero(double g, Prim L, Prim R, double cL, double cR)
+template <bool G75>
+static GRP_HD Prim sample_vacuum_zero(double g, const Side& L, const Side& R)
 {
-  if (L.u - cL >= 0.0) return L;
-  if (L.u + 2.0 * cL / (g - 1.0) > 0.0) {
-    const double c0 = 2.0 / (g + 1.0) * (cL + 0.5 * (g - 1.0) * L.u);
-    return Prim{L.r * pow(c0 / cL, 2.0 / (g - 1.0)), c0, L.p * pow(c0 / cL, 2.0 * g / (g - 1.0))};
+  if (L.u - L.c >= 0.0) return Prim{L.r, L.u, L.p};
+  if (L.u + 2.0 * L.c / (g - 1.0) > 0.0) {
+    const double c0 = 2.0 / (g + 1.0) * (L.c + 0.5 * (g - 1.0) * L.u);
+    return sonic<G75>(g, L, c0, c0);
   }
-  if (R.u + cR <= 0.0) return R;
-  if (R.u - 2.0 * cR / (g - 1.0) < 0.0) {
-    const double c0 = 2.0 / (g + 1.0) * (cR - 0.5 * (g - 1.0) * R.u);
-    return Prim{R.r * pow(c0 / cR, 2.0 / (g - 1.0)), -c0, R.p * pow(c0 / cR, 2.0 * g / (g - 1.0))};
+  if (R.u + R.c <= 0.0) return Prim{R.r, R.u, R.p};
+  if (R.u - 2.0 * R.c / (g - 1.0) < 0.0) {
+    const double c0 = 2.0 / (g + 1.0) * (R.c - 0.5 * (g - 1.0) * R.u);
+    return sonic<G75>(g, R, c0, -c0);
   }
   return Prim{0.0, 0.0, 0.0};
 }
 
-// Conserved Godunov state at x/t = 0 of conserved data QL | QR.
-// allow_vacuum: vacuum data are sampled and ST_VACUUM returned with Q valid.
+// Godunov state at x/t = 0 of conserved data QL | QR, as conserved Q and
+// primitive W.  allow_vacuum: vacuum data are sampled and ST_VACUUM returned
+// with Q valid.
+template <bool G75>
 static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double QR[3], double p0,
-                             bool allow_vacuum, double Q[3], int& iters)
+                                bool allow_vacuum, double Q[3], Prim& W, int& iters)
 {
   const double g = ph.gamma;
-  const Prim L = to_prim(g, QL[0], QL[1], QL[2]);
-  const Prim R = to_prim(g, QR[0], QR[1], QR[2]);
-  const double cL = sqrt(g * L.p / L.r), cR = sqrt(g * R.p / R.r);
+  const Side L = make_side(g, to_prim(g, QL[0], QL[1], QL[2]));
+  const Side R = make_side(g, to_prim(g, QR[0], QR[1], QR[2]));
   double ps = 0.0, us = 0.0;
-  const int st = star_pressure(ph, L, R, cL, cR, p0, ps, us, iters);
+  const int st = star_pressure<G75>(ph, L, R, p0, ps, us, iters);
   if (st == ST_VACUUM && allow_vacuum) {
-    to_cons(g, sample_vacuum_zero(g, L, R, cL, cR), Q);
+    W = sample_vacuum_zero<G75>(g, L, R);
+    to_cons(g, W, Q);
     return ST_VACUUM;
   }
   if (st != ST_OK) return st;
-  to_cons(g, sample_zero(g, L, R, cL, cR, ps, us), Q);
+  W = sample_zero<G75>(g, L, R, ps, us);
+  to_cons(g, W, Q);
   return ST_OK;
 }
 
@@ -255,14 +373,15 @@ struct Eig {
   double lam[3];
 };
 
-GRP_HD __forceinline__ Eig make_eig(double g, const double Q0[3])
+GRP_HD __forceinline__ Eig make_eig(double g, const double Q0[3], Prim w)
 {
   Eig e;
-  const Prim w = to_prim(g, Q0[0], Q0[1], Q0[2]);
+  const double ir = 1.0 / w.r;
   e.u = w.u;
-  e.c = sqrt(g * w.p / w.r);
-  e.H = (Q0[2] + w.p) / w.r;
-  e.ic = 1.0 / e.c;
+  const double c2 = g * w.p * ir;
+  e.c = sqrt(c2);
+  e.H = (Q0[2] + w.p) * ir;
+  e.ic = e.c / c2;
   e.b1 = (g - 1.0) * e.ic * e.ic;
   e.b2 = 0.5 * e.u * e.u * e.b1;
   e.lam[0] = e.u - e.c; e.lam[1] = e.u; e.lam[2] = e.u + e.c;
@@ -415,7 +534,7 @@ GRP_HD __forceinline__ void grp_adv(double lam, double nu, const double tL[M + 1
 // then takes the first-order flux).  truncated: a state of the series at a
 // Gauss node or at dt was inadmissible, so the series was cut to its
 // leading term.
-template <int M>
+template <int M, bool G75>
 GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[3][M + 1],
                                      const double tR[3][M + 1], double F[3], double gnew[3], int& iters,
                                      bool& truncated)
@@ -423,14 +542,15 @@ GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[
   const double g = ph.gamma;
   const double QL[3] = {tL[0][0], tL[1][0], tL[2][0]}, QR[3] = {tR[0][0], tR[1][0], tR[2][0]};
   double Q0[3];
+  Prim W0;
   truncated = false;
-  const int st = riemann_state(ph, QL, QR, 0.0, false, Q0, iters);
+  const int st = riemann_state<G75>(ph, QL, QR, 0.0, false, Q0, W0, iters);
   if (st != ST_OK) return st;
   using T = Tri<M>;
   double rho[T::N], m[T::N], E[T::N];
   rho[0] = Q0[0]; m[0] = Q0[1]; E[0] = Q0[2];
   {
-    const Eig e = make_eig(g, Q0);
+    const Eig e = make_eig(g, Q0, W0);
 #pragma unroll
     for (int k = 1; k <= M; ++k) {
       const double DL[3] = {tL[0][k], tL[1][k], tL[2][k]}, DR[3] = {tR[0][k], tR[1][k], tR[2][k]};
@@ -441,12 +561,14 @@ GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[
   }
   double s[3][M + 1];
   ck_euler<M>(g, rho, m, E, s);
-  // states at the Gauss nodes and at tau = dt
-  double Qg[Gauss<M>::G + 1][3];
+  // states at the Gauss nodes and at tau = dt; one reciprocal per state
+  // serves both the admissibility test and the flux
+  constexpr int G = Gauss<M>::G;
+  double Qg[G + 1][3], ug[G + 1], pg[G + 1];
   bool ok = true;
 #pragma unroll
-  for (int al = 0; al <= Gauss<M>::G; ++al) {
-    const double Tn = al < Gauss<M>::G ? nu * Gauss<M>::node(al) : nu;
+  for (int al = 0; al <= G; ++al) {
+    const double Tn = al < G ? nu * Gauss<M>::node(al) : nu;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       double v = s[c][M];
@@ -454,22 +576,27 @@ GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[
       for (int k = M - 1; k >= 0; --k) v = v * Tn + s[c][k];
       Qg[al][c] = v;
     }
-    ok = ok && admissible(g, Qg[al][0], Qg[al][1], Qg[al][2]);
+    ug[al] = Qg[al][1] / Qg[al][0];
+    pg[al] = (g - 1.0) * (Qg[al][2] - 0.5 * Qg[al][1] * ug[al]);
+    ok = ok && Qg[al][0] > 0.0 && pg[al] > 0.0;
   }
   if (!ok) {
     truncated = true;
 #pragma unroll
-    for (int al = 0; al <= Gauss<M>::G; ++al) { Qg[al][0] = Q0[0]; Qg[al][1] = Q0[1]; Qg[al][2] = Q0[2]; }
+    for (int al = 0; al <= G; ++al) {
+      Qg[al][0] = Q0[0]; Qg[al][1] = Q0[1]; Qg[al][2] = Q0[2];
+      ug[al] = W0.u; pg[al] = W0.p;
+    }
   }
   F[0] = F[1] = F[2] = 0.0;
 #pragma unroll
-  for (int al = 0; al < Gauss<M>::G; ++al) {
-    double Fa[3];
-    euler_flux(g, Qg[al][0], Qg[al][1], Qg[al][2], Fa);
+  for (int al = 0; al < G; ++al) {
     const double w = Gauss<M>::weight(al);
-    F[0] += w * Fa[0]; F[1] += w * Fa[1]; F[2] += w * Fa[2];
+    F[0] += w * Qg[al][1];
+    F[1] += w * (Qg[al][1] * ug[al] + pg[al]);
+    F[2] += w * (ug[al] * (Qg[al][2] + pg[al]));
   }
-  gnew[0] = Qg[Gauss<M>::G][0]; gnew[1] = Qg[Gauss<M>::G][1]; gnew[2] = Qg[Gauss<M>::G][2];
+  gnew[0] = Qg[G][0]; gnew[1] = Qg[G][1]; gnew[2] = Qg[G][2];
   return ST_OK;
 }
 

@@ -7,10 +7,10 @@ cudaError_t launch_flux_adv(const StepArgs& a, cudaStream_t s)
 {
   const unsigned g = (unsigned)((a.nif + 127) / 128);
   switch (a.M) {
-    case 1: k_flux<SYS_ADV, 1><<<g, 128, 0, s>>>(a); break;
-    case 2: k_flux<SYS_ADV, 2><<<g, 128, 0, s>>>(a); break;
-    case 3: k_flux<SYS_ADV, 3><<<g, 128, 0, s>>>(a); break;
-    case 4: k_flux<SYS_ADV, 4><<<g, 128, 0, s>>>(a); break;
+    case 1: k_flux<SYS_ADV, 1, false><<<g, 128, 0, s>>>(a); break;
+    case 2: k_flux<SYS_ADV, 2, false><<<g, 128, 0, s>>>(a); break;
+    case 3: k_flux<SYS_ADV, 3, false><<<g, 128, 0, s>>>(a); break;
+    case 4: k_flux<SYS_ADV, 4, false><<<g, 128, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -1,11 +1,12 @@
-// Flux kernel of the Euler equations, M = 3.
+// Flux kernels of the Euler equations, M = 3 (gamma = 7/5 fast path and generic gamma).
 #include "grp_kernels.cuh"
 
 namespace grp {
 cudaError_t launch_flux_euler_m3(const StepArgs& a, cudaStream_t s)
 {
   const unsigned g = (unsigned)((a.nif + 127) / 128);
-  k_flux<SYS_EULER, 3><<<g, 128, 0, s>>>(a);
+  if (a.ph.gamma == 1.4) k_flux<SYS_EULER, 3, true><<<g, 128, 0, s>>>(a);
+  else k_flux<SYS_EULER, 3, false><<<g, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 }  // namespace grp

@@ -178,6 +178,7 @@ __device__ __forceinline__ void cell_coeffs(const StepArgs& a, long long c0, lon
 }
 
 // First-order Godunov flux and state at interface j from cell averages.
+template <bool G75>
 static __device__ int first_order(const StepArgs& a, long long c0, int N, int bc, int j, double F[3], double Q0[3], int& iters)
 {
   int cl, cr;
@@ -186,7 +187,8 @@ static __device__ int first_order(const StepArgs& a, long long c0, int N, int bc
   double QL[3], QR[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) { QL[c] = a.avg[c * a.ncell + c0 + cl]; QR[c] = a.avg[c * a.ncell + c0 + cr]; }
-  const int st = riemann_state(a.ph, QL, QR, 0.0, true, Q0, iters);
+  Prim W;
+  const int st = riemann_state<G75>(a.ph, QL, QR, 0.0, true, Q0, W, iters);
   if (st != ST_OK && st != ST_VACUUM) return st;
   if (Q0[0] > 0.0) euler_flux(a.ph.gamma, Q0[0], Q0[1], Q0[2], F);
   else F[0] = F[1] = F[2] = 0.0;
@@ -194,7 +196,7 @@ static __device__ int first_order(const StepArgs& a, long long c0, int N, int bc
 }
 
 // ------------------------------------------------------------------ k_flux
-template <int SYS, int M>
+template <int SYS, int M, bool G75>
 __device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d, unsigned st[6])
 {
   const long long i0 = a.if_off[d], c0 = a.cell_off[d];
@@ -254,13 +256,13 @@ __device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d,
   } else {
     int iters = 0;
     bool trunc = false;
-    int rs_st = grp_euler<M>(a.ph, nu, tL, tR, F, gnew, iters, trunc);
+    int rs_st = grp_euler<M, G75>(a.ph, nu, tL, tR, F, gnew, iters, trunc);
     st[2] = 1;
     st[3] = trunc ? 1u : 0u;
     if (rs_st != ST_OK) {
       // no solution of the traces' Riemann problem: first-order flux here
       int it2 = 0;
-      rs_st = first_order(a, c0, N, bc, j, F, gnew, it2);
+      rs_st = first_order<G75>(a, c0, N, bc, j, F, gnew, it2);
       iters += it2;
       st[2] = 2;
       st[4] = 1;
@@ -279,7 +281,7 @@ __device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d,
 
 // One thread per interface; every thread of the grid reaches the statistics
 // (no early return) so the warp-synchronous reductions see a full warp.
-template <int SYS, int M>
+template <int SYS, int M, bool G75>
 __global__ void __launch_bounds__(128) k_flux(StepArgs a)
 {
   const long long gj = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(128) k_flux(StepArgs a)
   int d = -1;
   if (gj < a.nif) {
     d = a.if_dom[gj];
-    flux_one<SYS, M>(a, gj, d, st);
+    flux_one<SYS, M, G75>(a, gj, d, st);
   }
   __syncwarp();
   if (SYS == SYS_EULER) {
@@ -372,6 +374,7 @@ __global__ void k_update(StepArgs a, int pass)
 // Interfaces of troubled cells (inadmissible, or outside the relaxed discrete
 // maximum principle) take the first-order Godunov flux (a-posteriori,
 // MOOD-like, bounded to MAX_REPAIR rounds).
+template <bool G75>
 static __device__ __forceinline__ void repair_one(const StepArgs& a, int pass, long long gj, int d, unsigned st[3])
 {
   if (!a.bad[pass * a.n_domains + d]) return;
@@ -390,7 +393,7 @@ static __device__ __forceinline__ void repair_one(const StepArgs& a, int pass, l
   if (!t) return;
   double F[3], Q0[3];
   int iters = 0;
-  const int rs = first_order(a, c0, N, bc, j, F, Q0, iters);
+  const int rs = first_order<G75>(a, c0, N, bc, j, F, Q0, iters);
   st[0] = (unsigned)iters;
   st[1] = 1u;
   if (rs != ST_OK) { atomicExch(a.fail + d, rs); return; }
@@ -403,7 +406,8 @@ static __device__ __forceinline__ void repair_one(const StepArgs& a, int pass, l
   a.changed[pass * a.n_domains + d] = 1;
 }
 
-static __global__ void __launch_bounds__(128) k_repair_flux(StepArgs a, int pass)
+template <bool G75>
+__global__ void __launch_bounds__(128) k_repair_flux(StepArgs a, int pass)
 {
   if (a.any_bad[pass] == 0) return;          // uniform over the grid
   const long long gj = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -411,7 +415,7 @@ static __global__ void __launch_bounds__(128) k_repair_flux(StepArgs a, int pass
   int d = -1;
   if (gj < a.nif) {
     d = a.if_dom[gj];
-    repair_one(a, pass, gj, d, st);
+    repair_one<G75>(a, pass, gj, d, st);
   }
   __syncwarp();
   warp_stat_add(a.stats, d, S_NEWTON_SUM, st[0]);
@@ -458,7 +462,9 @@ static __global__ void k_init_iface(int sys, Phys ph, long long nif, const doubl
   int it;
   Phys p2 = ph;
   p2.guess = 0;
-  const int st = riemann_state(p2, QL, QR, 0.0, true, Q, it);
+  Prim W;
+  const int st = ph.gamma == 1.4 ? riemann_state<true>(p2, QL, QR, 0.0, true, Q, W, it)
+                                 : riemann_state<false>(p2, QL, QR, 0.0, true, Q, W, it);
   if (st != ST_OK && st != ST_VACUUM) { Q[0] = QL[0]; Q[1] = QL[1]; Q[2] = QL[2]; }
   ifc[j] = Q[0]; ifc[nif + j] = Q[1]; ifc[2 * nif + j] = Q[2];
 }

@@ -135,3 +135,11 @@ def test_device_pointers_through_torch():
         s.get_state(avg=out)
     S = oracle_run(prob, avg, lm, lp, 50)
     assert rel_diff(out.cpu().numpy(), S.avg, prob).max() < SMOOTH_TOL
+
+
+def test_generic_gamma_path():
+    """gamma != 7/5 takes the pow() path of the Riemann solver."""
+    prob, avg, lm, lp = I.euler_wave(80, 2, gamma=5.0 / 3.0)
+    check_parity(prob, avg, lm, lp, 10 ** 6, SMOOTH_TOL, t_end=0.5)
+    prob, avg, lm, lp = I.sod(200, M=3, gamma=5.0 / 3.0)
+    check_parity(prob, avg, lm, lp, 10 ** 6, DISC_TOL, t_end=0.2)
