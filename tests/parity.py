@@ -61,7 +61,7 @@ def check_parity(prob, avg, lm, lp, n_steps, tol, t_end=np.inf, **kw):
     ok = (S.status == O.OK) | (S.status == O.NONPHYSICAL)
     assert ok.any()
     assert np.array_equal(stats[ok, 0].astype(np.int64), S.stats[ok, 0]), "step counts differ"
-    assert np.allclose(t[ok], S.t[ok], rtol=1e-12, atol=0)
+    assert np.allclose(t[ok], S.t[ok], rtol=tol, atol=0)   # dt follows S_max of the state
     rd = rel_diff(a, S.avg, prob)[ok]
     ri = rel_diff_iface(g, S.iface, prob)[ok]
     assert rd.max() <= tol, ("averages", rd.max())
