@@ -36,6 +36,9 @@ UNIT = "cell-updates/s"
 # pow touching the state counts one.
 FLUX_FLOPS_PER_UPDATE = {("batched", 1): 441.5, ("batched", 2): 766.5, ("batched", 3): 1178.8,
                          ("batched", 4): 1727.2}
+# ... and of the whole step (CFL reduction + reconstruction/GRP + update and
+# repair), the work of the persistent batched kernel
+STEP_FLOPS_PER_UPDATE = {("batched", 2): 838.5}
 PROFILE = os.path.join(ROOT, "profiles", "k_flux_batched_m2.txt")
 
 
@@ -48,6 +51,8 @@ def parse():
     ap.add_argument("--domains", type=int, default=65536)
     ap.add_argument("--M", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch", default="tune", choices=["tune", "auto", "flat", "batch"],
+                    help="launch configuration: autotuned (default), library default, or forced")
     return ap.parse_args()
 
 
@@ -106,10 +111,11 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(cells):
-    """DRAM bytes per flux launch from the committed ncu summary, scaled from
-    its workload to this one by cell count; None when the kernel source has
-    changed since the capture."""
+def profiled_traffic(cells, kname):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, scaled from its workload to this one by cell count; None when the
+    kernel source has changed since the capture or the summary is of another
+    kernel."""
     if not os.path.exists(PROFILE):
         return None
     kv = {}
@@ -117,7 +123,7 @@ def profiled_traffic(cells):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("source_digest") != source_digest():
+    if kv.get("source_digest") != source_digest() or kv.get("bench_kernel") != kname:
         return None
     return float(kv["dram_bytes_per_launch"]) * cells / float(kv["cells_per_launch"])
 
@@ -194,6 +200,14 @@ def main():
     peak = grprec.grp_probe_fp64_peak(local)
     stream = torch.cuda.Stream()
     s = grprec.Solver(prob, device=local, stream=stream.cuda_stream)
+    if args.launch == "tune":
+        from paper_2602_21911_gb300 import autotune
+        s.set_launch(*autotune.tune(prob, avg, lm, lp, device=local, use_cache=False))
+    elif args.launch == "flat":
+        s.set_launch(grprec.GRP_LAUNCH_FLAT)
+    elif args.launch == "batch":
+        s.set_launch(grprec.GRP_LAUNCH_BATCH)
+    launch = s.get_launch()
     s.set_initial(avg, lm, lp)
     s.step(args.warmup)
     stats0, _ = s.get_stats()
@@ -249,20 +263,28 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "batched Euler: %d domains x log-uniform 4..512 cells, M=%d, CFL 0.9, "
                                    "transmissive, guess PVRS" % (args.domains, args.M),
-                       "seed": 2602, "cells": int(prob["n_cells"].sum()),
+                       "seed": 2602, "cells": int(prob["n_cells"].sum()), "launch": launch,
                        "l2": "state larger than L2 (no flush needed)"},
             "e2e": {"value": upd_e2e / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": h2d / nsteps_e2e, "d2h_bytes_per_step": d2h / nsteps_e2e},
             "gpu_launches": launches, "clocks": clk.summary(),
-            "flux_kernel": {"ms_total": flux_ms, "launches": flux_n,
-                            "share_of_step": flux_ms / ms if ms > 0 else None},
+            "dominant_kernel": {"ms_total": flux_ms, "launches": flux_n,
+                                "share_of_timed_region": flux_ms / ms if ms > 0 else None},
             "frozen_domains": int((status != 0).sum())}
-    flops = FLUX_FLOPS_PER_UPDATE.get(("batched", args.M))
+    if launch["batched"]:
+        flops = STEP_FLOPS_PER_UPDATE.get(("batched", args.M))
+        kname = "k_batch<Euler,M=%d> (%d steps per launch)" % (args.M, launch["steps_per_launch"])
+        per_launch_updates = (upd / world) / args.steps * launch["steps_per_launch"]
+    else:
+        flops = FLUX_FLOPS_PER_UPDATE.get(("batched", args.M))
+        kname = "k_flux<Euler,M=%d>" % args.M
+        per_launch_updates = (upd / world) / args.steps
     if flops and flux_n:
-        ach = flops * (upd / world) / args.steps / (flux_ms / flux_n * 1e-3)
+        ach = flops * per_launch_updates / (flux_ms / flux_n * 1e-3)
         line["roofline"] = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                            "frac": ach / peak, "traffic": profiled_traffic(int(prob["n_cells"].sum())),
-                            "kernel": "k_flux<Euler,M=%d>" % args.M,
+                            "frac": ach / peak,
+                            "traffic": profiled_traffic(int(prob["n_cells"].sum()), kname),
+                            "kernel": kname,
                             "peak_source": "measured FP64 FMA-chain probe (grp_probe_fp64_peak), this GPU",
                             "flops_per_cell_update": flops}
     if not args.no_cpu_baseline:

@@ -39,6 +39,11 @@ struct grp_ctx {
   unsigned long long* stats = nullptr;
   double* scratch_norm = nullptr;
   float *mlp = nullptr, *mlp_norm = nullptr;
+  // launch configuration (grp_set_launch)
+  int mode = GRP_LAUNCH_AUTO, threads = 256, cells_per_block = 2048, steps_per_launch = 8;
+  int max_cells = 0;
+  int* grp = nullptr;            // device [n_blocks + 1] first domain of each block
+  int n_blocks = 0;
   // optional CUDA-event timing of the flux kernel launches
   bool timing = false;
   std::vector<cudaEvent_t> ev_free, ev_pending;   // pending: start/stop pairs
@@ -75,7 +80,7 @@ void free_all(grp_ctx* c)
   void* ptrs[] = {c->cell_off, c->if_off, c->cell_dom, c->if_dom, c->dx, c->bc, c->avg[0], c->avg[1],
                   c->ifc[0], c->ifc[1], c->flux, c->low, c->troubled, c->t, c->dt_prev, c->nstep,
                   c->status, c->smax_bits, c->bad, c->inad, c->changed, c->fail, c->any_bad, c->stats,
-                  c->scratch_norm, c->mlp, c->mlp_norm};
+                  c->scratch_norm, c->mlp, c->mlp_norm, c->grp};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -140,6 +145,72 @@ cudaError_t launch_flux(const StepArgs& a, cudaStream_t s)
   }
 }
 
+cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s)
+{
+  if (L.a.sys == SYS_ADV) return launch_batch_adv(L, s);
+  switch (L.a.M) {
+    case 1: return launch_batch_euler_m1(L, s);
+    case 2: return launch_batch_euler_m2(L, s);
+    case 3: return launch_batch_euler_m3(L, s);
+    case 4: return launch_batch_euler_m4(L, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool use_batch(const grp_ctx* c)
+{
+  if (c->mode == GRP_LAUNCH_FLAT) return false;
+  if (c->mode == GRP_LAUNCH_BATCH) return true;
+  // auto: whole domains per block pay off when the batch has many short domains
+  return c->D >= 1024 && c->max_cells <= 4096;
+}
+
+// Greedy grouping of consecutive domains into blocks of about
+// cells_per_block cells (a longer domain gets a block of its own).
+int build_groups(grp_ctx* c)
+{
+  std::vector<int> g(1, 0);
+  long long acc = 0;
+  for (int d = 0; d < c->D; ++d) {
+    const long long n = c->h_cell_off[d + 1] - c->h_cell_off[d];
+    if (acc > 0 && acc + n > c->cells_per_block) { g.push_back(d); acc = 0; }
+    acc += n;
+  }
+  g.push_back(c->D);
+  if (c->grp) cudaFree(c->grp);
+  c->grp = nullptr;
+  CK(cudaMalloc((void**)&c->grp, sizeof(int) * g.size()));
+  CK(cudaMemcpy(c->grp, g.data(), sizeof(int) * g.size(), cudaMemcpyHostToDevice));
+  c->n_blocks = (int)g.size() - 1;
+  return GRP_OK;
+}
+
+// nsteps steps of the persistent batched kernel in one launch
+int enqueue_batch(grp_ctx* c, int nsteps, double t_end)
+{
+  if (!c->grp) { const int rc = build_groups(c); if (rc) return rc; }
+  const StepArgs a = make_args(c, t_end);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->timing) {
+    for (cudaEvent_t* e : {&e0, &e1}) {
+      if (!c->ev_free.empty()) { *e = c->ev_free.back(); c->ev_free.pop_back(); }
+      else CK(cudaEventCreate(e));
+    }
+    CK(cudaEventRecord(e0, c->stream));
+  }
+  const BatchLaunch L{a, c->grp, (unsigned)c->n_blocks, (unsigned)c->threads, nsteps, c->cur,
+                      c->avg[0], c->avg[1], c->ifc[0], c->ifc[1]};
+  CK(launch_batch(L, c->stream));
+  c->launches++;
+  if (c->timing) {
+    CK(cudaEventRecord(e1, c->stream));
+    c->ev_pending.push_back(e0);
+    c->ev_pending.push_back(e1);
+  }
+  c->cur ^= (nsteps & 1);
+  return GRP_OK;
+}
+
 int enqueue_step(grp_ctx* c, double t_end)
 {
   const StepArgs a = make_args(c, t_end);
@@ -183,6 +254,8 @@ int enqueue_step(grp_ctx* c, double t_end)
   c->cur ^= 1;
   return GRP_OK;
 }
+
+int step_n(grp_ctx* c, int n_steps, double t_end);
 
 // true when every domain has reached t_end or is frozen (synchronises the stream)
 int all_done(grp_ctx* c, double t_end, bool& done)
@@ -252,6 +325,7 @@ int grp_create(grp_ctx** out, const grp_problem* p)
     c->h_if_off[d + 1] = c->h_if_off[d] + N + (p->bc[d] == GRP_BC_TRANSMISSIVE ? 1 : 0);
     c->h_dx[d] = (p->x_right[d] - p->x_left[d]) / N;
     hbc[d] = (unsigned char)p->bc[d];
+    if (N > c->max_cells) c->max_cells = N;
   }
   c->ncell = c->h_cell_off[c->D];
   c->nif = c->h_if_off[c->D];
@@ -343,21 +417,82 @@ int grp_step(grp_ctx* c, int n_steps, double t_end)
   if (!c->initialized) return GRP_E_NOT_INITIALIZED;
   if (c->p.guess == GRP_GUESS_MLP && !c->mlp) return GRP_E_NO_MODEL;
   CK(cudaSetDevice(c->p.device));
+  return step_n(c, n_steps, t_end);
+}
+
+int grp_set_launch(grp_ctx* c, int mode, int threads, int cells_per_block, int steps_per_launch)
+{
+  if (!c || mode < GRP_LAUNCH_AUTO || mode > GRP_LAUNCH_BATCH) return GRP_E_INVALID_ARG;
+  if (threads != 128 && threads != 256) return GRP_E_INVALID_ARG;
+  if (cells_per_block < 64 || cells_per_block > (1 << 20) || steps_per_launch < 1 || steps_per_launch > 1024)
+    return GRP_E_INVALID_ARG;
+  CK(cudaSetDevice(c->p.device));
+  CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+  const bool regroup = cells_per_block != c->cells_per_block;
+  c->mode = mode;
+  c->threads = threads;
+  c->cells_per_block = cells_per_block;
+  c->steps_per_launch = steps_per_launch;
+  if (regroup && c->grp) { cudaFree(c->grp); c->grp = nullptr; }
+  return GRP_OK;
+}
+
+int grp_get_launch(const grp_ctx* c, int* batched, int* threads, int* cells_per_block, int* steps_per_launch,
+                   int* blocks)
+{
+  if (!c) return GRP_E_INVALID_ARG;
+  if (batched) *batched = use_batch(c) ? 1 : 0;
+  if (threads) *threads = c->threads;
+  if (cells_per_block) *cells_per_block = c->cells_per_block;
+  if (steps_per_launch) *steps_per_launch = c->steps_per_launch;
+  if (blocks) {
+    long long nb = 0, acc = 0;
+    for (int d = 0; d < c->D; ++d) {
+      const long long n = c->h_cell_off[d + 1] - c->h_cell_off[d];
+      if (acc > 0 && acc + n > c->cells_per_block) { ++nb; acc = 0; }
+      acc += n;
+    }
+    *blocks = (int)(nb + 1);
+  }
+  return GRP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+int step_n(grp_ctx* c, int n_steps, double t_end)
+{
   // With a finite t_end, long requests test completion every DONE_CHECK steps
   // so that the steps left after every domain has arrived are not enqueued.
   const int DONE_CHECK = 64;
-  for (int i = 0; i < n_steps; ++i) {
-    if (isfinite(t_end) && i > 0 && i % DONE_CHECK == 0) {
+  const bool batch = use_batch(c);
+  int since_check = 0;
+  for (int i = 0; i < n_steps;) {
+    if (isfinite(t_end) && i > 0 && since_check >= DONE_CHECK) {
       bool done = false;
       const int rc = all_done(c, t_end, done);
       if (rc) return rc;
       if (done) break;
+      since_check = 0;
     }
-    const int rc = enqueue_step(c, t_end);
-    if (rc) return rc;
+    int k = 1;
+    if (batch) {
+      k = c->steps_per_launch;
+      if (k > n_steps - i) k = n_steps - i;
+      const int rc = enqueue_batch(c, k, t_end);
+      if (rc) return rc;
+    } else {
+      const int rc = enqueue_step(c, t_end);
+      if (rc) return rc;
+    }
+    i += k;
+    since_check += k;
   }
   return GRP_OK;
 }
+}  // namespace
+
+extern "C" {
 
 int grp_advance_to(grp_ctx* c, double t_end, int max_steps)
 {
@@ -373,10 +508,8 @@ int grp_advance_to(grp_ctx* c, double t_end, int max_steps)
     if (all) return GRP_OK;
     if (done_steps >= max_steps) return GRP_E_MAX_STEPS;
     const int n = max_steps - done_steps < block ? max_steps - done_steps : block;
-    for (int i = 0; i < n; ++i) {
-      const int rc = enqueue_step(c, t_end);
-      if (rc) return rc;
-    }
+    const int rc = step_n(c, n, t_end);
+    if (rc) return rc;
     done_steps += n;
   }
 }

@@ -106,39 +106,51 @@ __device__ __forceinline__ void nbr(int i, int N, int bc, int& im, int& ip)
   else { im = i == 0 ? 0 : i - 1; ip = i == N - 1 ? N - 1 : i + 1; }
 }
 
+__device__ __forceinline__ void reset_domain_words(const StepArgs& a, int d)
+{
+  for (int p = 0; p <= MAX_REPAIR; ++p) a.bad[p * a.n_domains + d] = a.inad[p * a.n_domains + d] = 0;
+  for (int p = 0; p < MAX_REPAIR; ++p) a.changed[p * a.n_domains + d] = 0;
+  a.fail[d] = 0;
+}
+
+// S_max contribution of cell gi (all 32 lanes call; valid = false lanes add nothing)
+__device__ __forceinline__ void smax_cell(const StepArgs& a, long long gi, bool valid)
+{
+  unsigned long long bits = 0ull;
+  int d = -1;
+  if (valid) {
+    d = a.cell_dom[gi];
+    const double g = a.ph.gamma;
+    const double r = a.avg[gi], m = a.avg[a.ncell + gi], E = a.avg[2 * a.ncell + gi];
+    const double u = __ddiv_rn(m, r);
+    const double p = __dmul_rn(g - 1.0, __dadd_rn(E, -__dmul_rn(__dmul_rn(0.5, m), u)));
+    double sp = __dadd_rn(fabs(u), __dsqrt_rn(__ddiv_rn(__dmul_rn(g, p), r)));
+    if (!(sp >= 0.0)) sp = 0.0;
+    bits = (unsigned long long)__double_as_longlong(sp);
+  }
+  const int d0 = __shfl_sync(0xffffffffu, d, 0);
+  if (__all_sync(0xffffffffu, d == d0 && d >= 0)) {
+    unsigned long long mx = bits;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
+      mx = o > mx ? o : mx;
+    }
+    if (lane_id() == 0) atomicMax(a.smax_bits + d, mx);
+  } else if (valid) {
+    atomicMax(a.smax_bits + d, bits);
+  }
+}
+
 // ------------------------------------------------------------------ k_smax
 static __global__ void k_smax(StepArgs a)
 {
   const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (blockIdx.x == 0 && threadIdx.x <= MAX_REPAIR) a.any_bad[threadIdx.x] = 0;
-  if (gi >= a.ncell) return;
-  const int d = a.cell_dom[gi];
-  if (gi == a.cell_off[d]) {                // one thread per domain resets the step words
-    for (int p = 0; p <= MAX_REPAIR; ++p) a.bad[p * a.n_domains + d] = a.inad[p * a.n_domains + d] = 0;
-    for (int p = 0; p < MAX_REPAIR; ++p) a.changed[p * a.n_domains + d] = 0;
-    a.fail[d] = 0;
-  }
-  if (a.sys != SYS_EULER) return;
-  const double g = a.ph.gamma;
-  const double r = a.avg[gi], m = a.avg[a.ncell + gi], E = a.avg[2 * a.ncell + gi];
-  // same operation order as the paper-level definition, no contraction
-  const double u = __ddiv_rn(m, r);
-  const double p = __dmul_rn(g - 1.0, __dadd_rn(E, -__dmul_rn(__dmul_rn(0.5, m), u)));
-  double s = __dadd_rn(fabs(u), __dsqrt_rn(__ddiv_rn(__dmul_rn(g, p), r)));
-  if (!(s >= 0.0)) s = 0.0;                 // NaN (inadmissible) contributes nothing
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(s);
-  const unsigned mask = __activemask();
-  if (mask == 0xffffffffu && __all_sync(mask, d == __shfl_sync(mask, d, 0))) {
-    unsigned long long mx = bits;   // whole warp in one domain: one atomic
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const unsigned long long o = __shfl_xor_sync(mask, mx, off);
-      mx = o > mx ? o : mx;
-    }
-    if (lane_id() == 0) atomicMax(a.smax_bits + d, mx);
-  } else {
-    atomicMax(a.smax_bits + d, bits);
-  }
+  const bool valid = gi < a.ncell;
+  if (valid && gi == a.cell_off[a.cell_dom[gi]]) reset_domain_words(a, a.cell_dom[gi]);
+  if (a.sys != SYS_EULER) return;                  // uniform
+  smax_cell(a, gi, valid);
 }
 
 // ------------------------------------------------------------------ traces
@@ -304,28 +316,27 @@ __global__ void __launch_bounds__(128) k_flux(StepArgs a)
 }
 
 // ------------------------------------------------------------------ update
-// Candidate averages from the flux array; flags inadmissible cells.
-// pass < 0: first update of the step (all active domains), else a repair
-// re-update of the domains flagged bad after pass `pass`.
+// Candidate average of cell gi from the flux array, with the a-posteriori
+// detection: inadmissible, or outside the relaxed discrete maximum principle
+// on density and pressure against the old averages of cells i-1, i, i+1.
+// pass < 0: first update of the step; else a repair re-update (only domains
+// flagged after pass `pass` whose repair changed something).
+// Returns bit 0: troubled, bit 1: inadmissible.
 template <int SYS>
-__global__ void k_update(StepArgs a, int pass)
+__device__ __forceinline__ int update_one(const StepArgs& a, long long gi, int d, int pass)
 {
-  const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (pass >= 0 && a.any_bad[pass] == 0) return;
-  if (gi >= a.ncell) return;
-  const int d = a.cell_dom[gi];
   constexpr int C = SYS == SYS_EULER ? 3 : 1;
   double dt, dt_cfl;
   bool last;
   const bool active = domain_dt(a, d, dt, dt_cfl, last);
   if (pass >= 0) {
-    if (!active || !a.bad[pass * a.n_domains + d]) return;
-    if (!a.changed[pass * a.n_domains + d]) return;     // nothing repaired: k_finish freezes it
+    if (!active || !a.bad[pass * a.n_domains + d]) return 0;
+    if (!a.changed[pass * a.n_domains + d]) return 0;     // nothing repaired: finish freezes it
   }
   if (!active) {
 #pragma unroll
     for (int c = 0; c < C; ++c) a.avg_new[c * a.ncell + gi] = a.avg[c * a.ncell + gi];
-    return;
+    return 0;
   }
   const long long c0 = a.cell_off[d], i0 = a.if_off[d];
   const int N = (int)(a.cell_off[d + 1] - c0);
@@ -338,36 +349,41 @@ __global__ void k_update(StepArgs a, int pass)
     Q[c] = a.avg[c * a.ncell + gi] - r * (a.flux[c * a.nif + i0 + jr] - a.flux[c * a.nif + i0 + jl]);
     a.avg_new[c * a.ncell + gi] = Q[c];
   }
-  if (SYS == SYS_EULER) {
-    const double g = a.ph.gamma;
-    const bool adm = admissible(g, Q[0], Q[1], Q[2]);
-    bool ok = adm;
-    if (adm) {
-      // relaxed discrete maximum principle on density and pressure against the
-      // old averages of cells i-1, i, i+1 (boundary rule for the neighbours)
-      int im, ip;
-      nbr(i, N, a.bc[d], im, ip);
-      const int nb[3] = {im, i, ip};
-      double lo0 = 0.0, hi0 = 0.0, lo1 = 0.0, hi1 = 0.0;
+  if (SYS != SYS_EULER) return 0;
+  const double g = a.ph.gamma;
+  const bool adm = admissible(g, Q[0], Q[1], Q[2]);
+  bool ok = adm;
+  if (adm) {
+    int im, ip;
+    nbr(i, N, a.bc[d], im, ip);
+    const int nb[3] = {im, i, ip};
+    double lo0 = 0.0, hi0 = 0.0, lo1 = 0.0, hi1 = 0.0;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const long long q = c0 + nb[k];
-        const Prim w = to_prim(g, a.avg[q], a.avg[a.ncell + q], a.avg[2 * a.ncell + q]);
-        lo0 = k == 0 ? w.r : fmin(lo0, w.r); hi0 = k == 0 ? w.r : fmax(hi0, w.r);
-        lo1 = k == 0 ? w.p : fmin(lo1, w.p); hi1 = k == 0 ? w.p : fmax(hi1, w.p);
-      }
-      const Prim wc = to_prim(g, Q[0], Q[1], Q[2]);
-      const double d0 = DMP_REL * fmax(fabs(lo0), fabs(hi0)), d1 = DMP_REL * fmax(fabs(lo1), fabs(hi1));
-      ok = wc.r >= lo0 - d0 && wc.r <= hi0 + d0 && wc.p >= lo1 - d1 && wc.p <= hi1 + d1;
+    for (int k = 0; k < 3; ++k) {
+      const long long q = c0 + nb[k];
+      const Prim w = to_prim(g, a.avg[q], a.avg[a.ncell + q], a.avg[2 * a.ncell + q]);
+      lo0 = k == 0 ? w.r : fmin(lo0, w.r); hi0 = k == 0 ? w.r : fmax(hi0, w.r);
+      lo1 = k == 0 ? w.p : fmin(lo1, w.p); hi1 = k == 0 ? w.p : fmax(hi1, w.p);
     }
-    a.troubled[gi] = ok ? 0 : 1;
-    const int np = pass + 1;
-    if (!ok && np < MAX_REPAIR + 1) {
-      a.bad[np * a.n_domains + d] = 1;
-      a.any_bad[np] = 1;
-    }
-    if (!adm) a.inad[np * a.n_domains + d] = 1;
+    const Prim wc = to_prim(g, Q[0], Q[1], Q[2]);
+    const double d0 = DMP_REL * fmax(fabs(lo0), fabs(hi0)), d1 = DMP_REL * fmax(fabs(lo1), fabs(hi1));
+    ok = wc.r >= lo0 - d0 && wc.r <= hi0 + d0 && wc.p >= lo1 - d1 && wc.p <= hi1 + d1;
   }
+  a.troubled[gi] = ok ? 0 : 1;
+  const int np = pass + 1;
+  if (!ok) a.bad[np * a.n_domains + d] = 1;
+  if (!adm) a.inad[np * a.n_domains + d] = 1;
+  return (ok ? 0 : 1) | (adm ? 0 : 2);
+}
+
+template <int SYS>
+__global__ void k_update(StepArgs a, int pass)
+{
+  const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pass >= 0 && a.any_bad[pass] == 0) return;
+  if (gi >= a.ncell) return;
+  const int d = a.cell_dom[gi];
+  if (update_one<SYS>(a, gi, d, pass) & 1) a.any_bad[pass + 1] = 1;
 }
 
 // ------------------------------------------------------------------ repair
@@ -425,10 +441,10 @@ __global__ void __launch_bounds__(128) k_repair_flux(StepArgs a, int pass)
 }
 
 // ------------------------------------------------------------------ finish
-static __global__ void k_finish(StepArgs a)
+// Per-domain bookkeeping at the end of a step: time, step count, the dt kept
+// for dt_hold, status; clears S_max for the next step's reduction.
+__device__ __forceinline__ void finish_one(const StepArgs& a, int d)
 {
-  const int d = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d >= a.n_domains) return;
   double dt, dt_cfl;
   bool last;
   const bool active = domain_dt(a, d, dt, dt_cfl, last);
@@ -444,6 +460,90 @@ static __global__ void k_finish(StepArgs a)
     int p = 0;
     while (p < MAX_REPAIR && a.bad[p * a.n_domains + d] && a.changed[p * a.n_domains + d]) ++p;
     if (a.inad[p * a.n_domains + d]) a.status[d] = ST_NONPHYS;
+  }
+}
+
+static __global__ void k_finish(StepArgs a)
+{
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d < a.n_domains) finish_one(a, d);
+}
+
+// ------------------------------------------------------------------ batched
+// Persistent form for batches of short domains: block b owns the contiguous
+// domains [grp[b], grp[b+1]) and advances them nsteps steps.  Every phase of a
+// step (reset, S_max, GRP fluxes, update, repair rounds, bookkeeping) is local
+// to the block, separated by __syncthreads, so one launch covers nsteps steps.
+// Buffers alternate per step starting from `parity` (0: A0/I0 current).
+template <int SYS, int M, bool G75>
+__global__ void __launch_bounds__(256, 2) k_batch(StepArgs a, const int* __restrict__ grp, int nsteps, int parity,
+                                               double* A0, double* A1, double* I0, double* I1)
+{
+  __shared__ int s_any[MAX_REPAIR + 1];
+  const int b = blockIdx.x, tid = threadIdx.x, bt = blockDim.x;
+  const int d0 = grp[b], d1 = grp[b + 1];
+  const long long cb = a.cell_off[d0], ce = a.cell_off[d1];
+  const long long ib = a.if_off[d0], ie = a.if_off[d1];
+  for (int s = 0; s < nsteps; ++s) {
+    StepArgs w = a;
+    const int par = (parity + s) & 1;
+    w.avg = par ? A1 : A0;
+    w.avg_new = par ? A0 : A1;
+    w.ifc = par ? I1 : I0;
+    w.ifc_new = par ? I0 : I1;
+    for (int d = d0 + tid; d < d1; d += bt) reset_domain_words(w, d);
+    if (tid <= MAX_REPAIR) s_any[tid] = 0;
+    __syncthreads();
+    if (SYS == SYS_EULER)
+      for (long long base = cb; base < ce; base += bt) smax_cell(w, base + tid, base + tid < ce);
+    __syncthreads();
+    for (long long base = ib; base < ie; base += bt) {
+      const long long gj = base + tid;
+      unsigned st[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+      int d = -1;
+      if (gj < ie) {
+        d = a.if_dom[gj];
+        flux_one<SYS, M, G75>(w, gj, d, st);
+      }
+      __syncwarp();
+      if (SYS == SYS_EULER) {
+        warp_stat_add(w.stats, d, S_NEWTON_SUM, st[0]);
+        warp_stat_max(w.stats, d, S_NEWTON_MAX, st[1]);
+        warp_stat_add(w.stats, d, S_RS_CALLS, st[2]);
+        warp_stat_add(w.stats, d, S_FLUX_FB, st[3]);
+        warp_stat_add(w.stats, d, S_LOW, st[4]);
+        warp_stat_add(w.stats, d, S_RECON_FB, st[5]);
+      }
+    }
+    __syncthreads();
+    for (long long gi = cb + tid; gi < ce; gi += bt)
+      if (update_one<SYS>(w, gi, a.cell_dom[gi], -1) & 1) s_any[0] = 1;
+    __syncthreads();
+    if (SYS == SYS_EULER) {
+      for (int r = 0; r < MAX_REPAIR; ++r) {
+        if (s_any[r] == 0) break;                       // uniform: read after a barrier
+        for (long long base = ib; base < ie; base += bt) {
+          const long long gj = base + tid;
+          unsigned st[3] = {0u, 0u, 0u};
+          int d = -1;
+          if (gj < ie) {
+            d = a.if_dom[gj];
+            repair_one<G75>(w, r, gj, d, st);
+          }
+          __syncwarp();
+          warp_stat_add(w.stats, d, S_NEWTON_SUM, st[0]);
+          warp_stat_max(w.stats, d, S_NEWTON_MAX, st[0]);
+          warp_stat_add(w.stats, d, S_RS_CALLS, st[1]);
+          warp_stat_add(w.stats, d, S_LOW, st[1]);
+        }
+        __syncthreads();
+        for (long long gi = cb + tid; gi < ce; gi += bt)
+          if (update_one<SYS>(w, gi, a.cell_dom[gi], r) & 1) s_any[r + 1] = 1;
+        __syncthreads();
+      }
+    }
+    for (int d = d0 + tid; d < d1; d += bt) finish_one(w, d);
+    __syncthreads();
   }
 }
 

@@ -1,13 +1,28 @@
-// Host-side launchers of the templated flux kernels (one translation unit per
-// system so the heavy FP64 instantiations compile in parallel).
+// Host-side launchers of the templated kernels (one translation unit per
+// system and degree, so the heavy FP64 instantiations compile in parallel).
 #pragma once
 #include <cuda_runtime.h>
 
 namespace grp {
 struct StepArgs;
+
+// One launch of the persistent batched kernel.
+struct BatchLaunch {
+  const StepArgs& a;
+  const int* grp;        // [blocks + 1] first domain of each block
+  unsigned blocks, threads;
+  int nsteps, parity;
+  double *A0, *A1, *I0, *I1;
+};
+
 cudaError_t launch_flux_adv(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_flux_euler_m1(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_flux_euler_m2(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_flux_euler_m3(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_flux_euler_m4(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_batch_adv(const BatchLaunch& L, cudaStream_t s);
+cudaError_t launch_batch_euler_m1(const BatchLaunch& L, cudaStream_t s);
+cudaError_t launch_batch_euler_m2(const BatchLaunch& L, cudaStream_t s);
+cudaError_t launch_batch_euler_m3(const BatchLaunch& L, cudaStream_t s);
+cudaError_t launch_batch_euler_m4(const BatchLaunch& L, cudaStream_t s);
 }  // namespace grp

@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 GRP_ADVECTION, GRP_EULER_IDEAL = 0, 1
 GRP_BC_PERIODIC, GRP_BC_TRANSMISSIVE = 0, 1
 GRP_GUESS_PVRS, GRP_GUESS_TRRS, GRP_GUESS_MLP = 0, 1, 2
+GRP_LAUNCH_AUTO, GRP_LAUNCH_FLAT, GRP_LAUNCH_BATCH = 0, 1, 2
 GRP_OK = 0
 GRP_NSTATS = 9
 (STAT_STEPS, STAT_NEWTON_SUM, STAT_NEWTON_MAX, STAT_RECON_FB, STAT_FLUX_FB, STAT_RS_CALLS,
@@ -65,6 +66,9 @@ def load(build_if_missing=True):
     L.grp_set_kernel_timing.argtypes = [_vp, ctypes.c_int]
     L.grp_get_kernel_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
     L.grp_probe_fp64_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.grp_set_launch.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    _ip = ctypes.POINTER(ctypes.c_int)
+    L.grp_get_launch.argtypes = [_vp, _ip, _ip, _ip, _ip, _ip]
     L.grp_destroy.argtypes = [_vp]
     L.grp_destroy.restype = None
     L.grp_status_string.argtypes = [ctypes.c_int]
@@ -197,6 +201,16 @@ class Solver:
         ms, n = ctypes.c_double(0.0), ctypes.c_longlong(0)
         _check(self.L.grp_get_kernel_timing(self.h, ctypes.byref(ms), ctypes.byref(n)), "grp_get_kernel_timing")
         return ms.value, n.value
+
+    def set_launch(self, mode=GRP_LAUNCH_AUTO, threads=256, cells_per_block=2048, steps_per_launch=8):
+        _check(self.L.grp_set_launch(self.h, int(mode), int(threads), int(cells_per_block),
+                                     int(steps_per_launch)), "grp_set_launch")
+
+    def get_launch(self):
+        v = [ctypes.c_int(0) for _ in range(5)]
+        _check(self.L.grp_get_launch(self.h, *[ctypes.byref(x) for x in v]), "grp_get_launch")
+        return dict(zip(("batched", "threads", "cells_per_block", "steps_per_launch", "blocks"),
+                        [x.value for x in v]))
 
     def launch_count(self):
         return int(self.L.grp_launch_count(self.h))
