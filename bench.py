@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--domains", type=int, default=65536)
     ap.add_argument("--M", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--launch", default="tune", choices=["tune", "auto", "flat", "batch"],
+    ap.add_argument("--launch", default="tune", choices=["tune", "auto", "flat", "fused", "split"],
                     help="launch configuration: autotuned (default), library default, or forced")
     return ap.parse_args()
 
@@ -205,8 +205,10 @@ def main():
         s.set_launch(*autotune.tune(prob, avg, lm, lp, device=local, use_cache=False))
     elif args.launch == "flat":
         s.set_launch(grprec.GRP_LAUNCH_FLAT)
-    elif args.launch == "batch":
-        s.set_launch(grprec.GRP_LAUNCH_BATCH)
+    elif args.launch == "fused":
+        s.set_launch(grprec.GRP_LAUNCH_FUSED)
+    elif args.launch == "split":
+        s.set_launch(grprec.GRP_LAUNCH_SPLIT)
     launch = s.get_launch()
     s.set_initial(avg, lm, lp)
     s.step(args.warmup)
@@ -271,7 +273,7 @@ def main():
             "dominant_kernel": {"ms_total": flux_ms, "launches": flux_n,
                                 "share_of_timed_region": flux_ms / ms if ms > 0 else None},
             "frozen_domains": int((status != 0).sum())}
-    if launch["batched"]:
+    if launch["form"] == grprec.GRP_LAUNCH_FUSED:
         flops = STEP_FLOPS_PER_UPDATE.get(("batched", args.M))
         kname = "k_batch<Euler,M=%d> (%d steps per launch)" % (args.M, launch["steps_per_launch"])
         per_launch_updates = (upd / world) / args.steps * launch["steps_per_launch"]

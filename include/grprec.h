@@ -47,7 +47,7 @@ typedef struct grp_ctx grp_ctx;   /* opaque, library-owned */
 enum { GRP_ADVECTION = 0, GRP_EULER_IDEAL = 1 };                 /* system (Sections 4.2, 4.3) */
 enum { GRP_BC_PERIODIC = 0, GRP_BC_TRANSMISSIVE = 1 };            /* per-domain boundary */
 enum { GRP_GUESS_PVRS = 0, GRP_GUESS_TRRS = 1, GRP_GUESS_MLP = 2 };/* Newton initial guess for p* */
-enum { GRP_LAUNCH_AUTO = 0, GRP_LAUNCH_FLAT = 1, GRP_LAUNCH_BATCH = 2 }; /* grp_set_launch modes */
+enum { GRP_LAUNCH_AUTO = 0, GRP_LAUNCH_FLAT = 1, GRP_LAUNCH_FUSED = 2, GRP_LAUNCH_SPLIT = 3 }; /* grp_set_launch */
 
 /* return codes */
 enum {
@@ -165,15 +165,19 @@ int grp_error_norms(grp_ctx *ctx, const double *exact_averages, int ptr_is_devic
  * Launch configuration of grp_step (the results do not depend on it).
  *   GRP_LAUNCH_FLAT:  one sequence of grid-wide kernels per step (S_max,
  *                     fluxes, update, repair rounds, bookkeeping); any domain size.
- *   GRP_LAUNCH_BATCH: a persistent kernel in which each block owns whole
+ *   GRP_LAUNCH_FUSED: one persistent kernel in which each block owns whole
  *                     consecutive domains (about cells_per_block cells) and
  *                     advances them steps_per_launch steps per launch, all
  *                     phases of a step separated by block barriers.
- *   GRP_LAUNCH_AUTO:  BATCH for >= 1024 domains of <= 4096 cells, else FLAT.
- * threads: 128 or 256 per block (BATCH); cells_per_block in [64, 2^20];
- * steps_per_launch in [1, 1024].  Synchronises the stream.  Defaults: AUTO,
- * 256, 2048, 8.  grp_get_launch reports the path grp_step will take and the
- * number of blocks of the batched kernel (any pointer may be NULL).
+ *   GRP_LAUNCH_SPLIT: two launches per step: the grid-wide flux kernel, then a
+ *                     per-domain-group kernel for update, repair, bookkeeping
+ *                     and the next step's S_max.
+ *   GRP_LAUNCH_AUTO:  SPLIT for >= 1024 domains of <= 4096 cells, else FLAT.
+ * threads: 128 or 256 per block (FUSED, SPLIT); cells_per_block in [64, 2^20];
+ * steps_per_launch in [1, 1024] (FUSED).  Synchronises the stream.  Defaults:
+ * AUTO, 256, 2048, 8.  grp_get_launch reports the form grp_step will take
+ * (*batched = GRP_LAUNCH_*) and the number of blocks of the per-group kernels
+ * (any pointer may be NULL).
  */
 int grp_set_launch(grp_ctx *ctx, int mode, int threads, int cells_per_block, int steps_per_launch);
 int grp_get_launch(const grp_ctx *ctx, int *batched, int *threads, int *cells_per_block,

@@ -1,8 +1,10 @@
 """Autotuner of the launch configuration of grp_step.
 
-Candidates: the flat per-step kernel sequence, and the persistent batched
-kernel with threads per block x cells per block (the tile of whole domains a
-block owns) x steps per launch (the temporal depth of one launch).  Each
+Candidates: the flat per-step kernel sequence; the split form (grid-wide flux
+kernel + a per-domain-group kernel for update, repair and bookkeeping) with
+threads per block x cells per block; and the fused persistent kernel with
+threads x cells per block (the tile of whole domains a block owns) x steps per
+launch (the temporal depth of one launch).  Each
 candidate advances a copy of the caller's initial data for a few steps and is
 timed on the device (stream-synchronised wall clock around the steps; the
 kernels are FP64-bound and run for milliseconds, so the host clock suffices).
@@ -43,9 +45,12 @@ def candidates(prob):
     out = [(grprec.GRP_LAUNCH_FLAT, 256, 2048, 1)]
     if int(np.max(prob["n_cells"])) <= 1 << 16:
         for threads in (128, 256):
-            for cells in (1024, 2048, 4096):
-                for k in (1, 4, 16):
-                    out.append((grprec.GRP_LAUNCH_BATCH, threads, cells, k))
+            for cells in (512, 2048, 8192):
+                out.append((grprec.GRP_LAUNCH_SPLIT, threads, cells, 1))
+        for threads in (128, 256):
+            for cells in (1024, 4096):
+                for k in (1, 16):
+                    out.append((grprec.GRP_LAUNCH_FUSED, threads, cells, k))
     return out
 
 

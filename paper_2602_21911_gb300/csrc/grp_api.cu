@@ -44,6 +44,7 @@ struct grp_ctx {
   int max_cells = 0;
   int* grp = nullptr;            // device [n_blocks + 1] first domain of each block
   int n_blocks = 0;
+  bool smax_ready = false;       // S_max of the current state already reduced (split form)
   // optional CUDA-event timing of the flux kernel launches
   bool timing = false;
   std::vector<cudaEvent_t> ev_free, ev_pending;   // pending: start/stop pairs
@@ -157,13 +158,15 @@ cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s)
   }
 }
 
-bool use_batch(const grp_ctx* c)
+// the launch form grp_step takes: FLAT, FUSED or SPLIT
+int launch_form(const grp_ctx* c)
 {
-  if (c->mode == GRP_LAUNCH_FLAT) return false;
-  if (c->mode == GRP_LAUNCH_BATCH) return true;
+  if (c->mode != GRP_LAUNCH_AUTO) return c->mode;
   // auto: whole domains per block pay off when the batch has many short domains
-  return c->D >= 1024 && c->max_cells <= 4096;
+  return c->D >= 1024 && c->max_cells <= 4096 ? GRP_LAUNCH_SPLIT : GRP_LAUNCH_FLAT;
 }
+
+bool use_batch(const grp_ctx* c) { return launch_form(c) != GRP_LAUNCH_FLAT; }
 
 // Greedy grouping of consecutive domains into blocks of about
 // cells_per_block cells (a longer domain gets a block of its own).
@@ -189,6 +192,7 @@ int build_groups(grp_ctx* c)
 int enqueue_batch(grp_ctx* c, int nsteps, double t_end)
 {
   if (!c->grp) { const int rc = build_groups(c); if (rc) return rc; }
+  c->smax_ready = false;
   const StepArgs a = make_args(c, t_end);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing) {
@@ -211,8 +215,43 @@ int enqueue_batch(grp_ctx* c, int nsteps, double t_end)
   return GRP_OK;
 }
 
+// one step in the split form: grid-wide k_flux, then k_post per domain group
+int enqueue_split(grp_ctx* c, double t_end)
+{
+  if (!c->grp) { const int rc = build_groups(c); if (rc) return rc; }
+  const StepArgs a = make_args(c, t_end);
+  cudaStream_t s = c->stream;
+  if (!c->smax_ready) {
+    k_smax<<<blocks(c->ncell, 256), 256, 0, s>>>(a);
+    c->launches++;
+    c->smax_ready = true;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->timing) {
+    for (cudaEvent_t* e : {&e0, &e1}) {
+      if (!c->ev_free.empty()) { *e = c->ev_free.back(); c->ev_free.pop_back(); }
+      else CK(cudaEventCreate(e));
+    }
+    CK(cudaEventRecord(e0, s));
+  }
+  CK(launch_flux(a, s));
+  c->launches++;
+  if (c->timing) {
+    CK(cudaEventRecord(e1, s));
+    c->ev_pending.push_back(e0);
+    c->ev_pending.push_back(e1);
+  }
+  const BatchLaunch L{a, c->grp, (unsigned)c->n_blocks, (unsigned)c->threads, 1, c->cur,
+                      c->avg[0], c->avg[1], c->ifc[0], c->ifc[1]};
+  CK(c->p.system == GRP_ADVECTION ? launch_post_adv(L, s) : launch_post_euler(L, s));
+  c->launches++;
+  c->cur ^= 1;
+  return GRP_OK;
+}
+
 int enqueue_step(grp_ctx* c, double t_end)
 {
+  c->smax_ready = false;
   const StepArgs a = make_args(c, t_end);
   cudaStream_t s = c->stream;
   const bool euler = c->p.system == GRP_EULER_IDEAL;
@@ -408,6 +447,7 @@ int grp_set_initial(grp_ctx* c, const double* averages, const double* lim_minus,
   CK(cudaMemsetAsync(c->low, 0, c->nif, s));
   CK(cudaMemsetAsync(c->troubled, 0, c->ncell, s));
   c->initialized = true;
+  c->smax_ready = false;
   return GRP_OK;
 }
 
@@ -422,7 +462,7 @@ int grp_step(grp_ctx* c, int n_steps, double t_end)
 
 int grp_set_launch(grp_ctx* c, int mode, int threads, int cells_per_block, int steps_per_launch)
 {
-  if (!c || mode < GRP_LAUNCH_AUTO || mode > GRP_LAUNCH_BATCH) return GRP_E_INVALID_ARG;
+  if (!c || mode < GRP_LAUNCH_AUTO || mode > GRP_LAUNCH_SPLIT) return GRP_E_INVALID_ARG;
   if (threads != 128 && threads != 256) return GRP_E_INVALID_ARG;
   if (cells_per_block < 64 || cells_per_block > (1 << 20) || steps_per_launch < 1 || steps_per_launch > 1024)
     return GRP_E_INVALID_ARG;
@@ -441,7 +481,7 @@ int grp_get_launch(const grp_ctx* c, int* batched, int* threads, int* cells_per_
                    int* blocks)
 {
   if (!c) return GRP_E_INVALID_ARG;
-  if (batched) *batched = use_batch(c) ? 1 : 0;
+  if (batched) *batched = launch_form(c);
   if (threads) *threads = c->threads;
   if (cells_per_block) *cells_per_block = c->cells_per_block;
   if (steps_per_launch) *steps_per_launch = c->steps_per_launch;
@@ -465,7 +505,6 @@ int step_n(grp_ctx* c, int n_steps, double t_end)
   // With a finite t_end, long requests test completion every DONE_CHECK steps
   // so that the steps left after every domain has arrived are not enqueued.
   const int DONE_CHECK = 64;
-  const bool batch = use_batch(c);
   int since_check = 0;
   for (int i = 0; i < n_steps;) {
     if (isfinite(t_end) && i > 0 && since_check >= DONE_CHECK) {
@@ -476,10 +515,14 @@ int step_n(grp_ctx* c, int n_steps, double t_end)
       since_check = 0;
     }
     int k = 1;
-    if (batch) {
+    const int form = launch_form(c);
+    if (form == GRP_LAUNCH_FUSED) {
       k = c->steps_per_launch;
       if (k > n_steps - i) k = n_steps - i;
       const int rc = enqueue_batch(c, k, t_end);
+      if (rc) return rc;
+    } else if (form == GRP_LAUNCH_SPLIT) {
+      const int rc = enqueue_split(c, t_end);
       if (rc) return rc;
     } else {
       const int rc = enqueue_step(c, t_end);

@@ -30,4 +30,9 @@ cudaError_t launch_batch_adv(const BatchLaunch& L, cudaStream_t s)
 #undef GRP_BATCH_ADV
   return cudaGetLastError();
 }
+cudaError_t launch_post_adv(const BatchLaunch& L, cudaStream_t s)
+{
+  k_post<SYS_ADV, false><<<L.blocks, L.threads, 0, s>>>(L.a, L.grp);
+  return cudaGetLastError();
+}
 }  // namespace grp

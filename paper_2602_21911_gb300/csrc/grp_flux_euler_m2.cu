@@ -20,4 +20,10 @@ cudaError_t launch_batch_euler_m2(const BatchLaunch& L, cudaStream_t s)
     k_batch<SYS_EULER, 2, false><<<L.blocks, L.threads, 0, s>>>(L.a, L.grp, L.nsteps, L.parity, L.A0, L.A1, L.I0, L.I1);
   return cudaGetLastError();
 }
+cudaError_t launch_post_euler(const BatchLaunch& L, cudaStream_t s)
+{
+  if (L.a.ph.gamma == 1.4) k_post<SYS_EULER, true><<<L.blocks, L.threads, 0, s>>>(L.a, L.grp);
+  else k_post<SYS_EULER, false><<<L.blocks, L.threads, 0, s>>>(L.a, L.grp);
+  return cudaGetLastError();
+}
 }  // namespace grp

@@ -547,6 +547,60 @@ __global__ void __launch_bounds__(256, 2) k_batch(StepArgs a, const int* __restr
   }
 }
 
+// ------------------------------------------------------------------ split
+// Second half of a step in the split form: block b owns the consecutive
+// domains [grp[b], grp[b+1]) whose fluxes k_flux has just computed; it updates
+// them, runs the repair rounds locally, does the bookkeeping, and then already
+// resets the per-domain words and reduces S_max of the new state for the next
+// step's k_flux.
+template <int SYS, bool G75>
+__global__ void __launch_bounds__(256) k_post(StepArgs a, const int* __restrict__ grp)
+{
+  __shared__ int s_any[MAX_REPAIR + 1];
+  const int b = blockIdx.x, tid = threadIdx.x, bt = blockDim.x;
+  const int d0 = grp[b], d1 = grp[b + 1];
+  const long long cb = a.cell_off[d0], ce = a.cell_off[d1];
+  const long long ib = a.if_off[d0], ie = a.if_off[d1];
+  if (tid <= MAX_REPAIR) s_any[tid] = 0;
+  __syncthreads();
+  for (long long gi = cb + tid; gi < ce; gi += bt)
+    if (update_one<SYS>(a, gi, a.cell_dom[gi], -1) & 1) s_any[0] = 1;
+  __syncthreads();
+  if (SYS == SYS_EULER) {
+    for (int r = 0; r < MAX_REPAIR; ++r) {
+      if (s_any[r] == 0) break;                       // uniform: read after a barrier
+      for (long long base = ib; base < ie; base += bt) {
+        const long long gj = base + tid;
+        unsigned st[3] = {0u, 0u, 0u};
+        int d = -1;
+        if (gj < ie) {
+          d = a.if_dom[gj];
+          repair_one<G75>(a, r, gj, d, st);
+        }
+        __syncwarp();
+        warp_stat_add(a.stats, d, S_NEWTON_SUM, st[0]);
+        warp_stat_max(a.stats, d, S_NEWTON_MAX, st[0]);
+        warp_stat_add(a.stats, d, S_RS_CALLS, st[1]);
+        warp_stat_add(a.stats, d, S_LOW, st[1]);
+      }
+      __syncthreads();
+      for (long long gi = cb + tid; gi < ce; gi += bt)
+        if (update_one<SYS>(a, gi, a.cell_dom[gi], r) & 1) s_any[r + 1] = 1;
+      __syncthreads();
+    }
+  }
+  for (int d = d0 + tid; d < d1; d += bt) {
+    finish_one(a, d);
+    reset_domain_words(a, d);
+  }
+  __syncthreads();
+  if (SYS == SYS_EULER) {
+    StepArgs n = a;                                   // S_max of the state just written
+    n.avg = a.avg_new;
+    for (long long base = cb; base < ce; base += bt) smax_cell(n, base + tid, base + tid < ce);
+  }
+}
+
 // ------------------------------------------------------------------ init
 // Initial interface data: classical Riemann state of the one-sided limits.
 static __global__ void k_init_iface(int sys, Phys ph, long long nif, const double* lm, const double* lp, double* ifc)

@@ -25,4 +25,6 @@ cudaError_t launch_batch_euler_m1(const BatchLaunch& L, cudaStream_t s);
 cudaError_t launch_batch_euler_m2(const BatchLaunch& L, cudaStream_t s);
 cudaError_t launch_batch_euler_m3(const BatchLaunch& L, cudaStream_t s);
 cudaError_t launch_batch_euler_m4(const BatchLaunch& L, cudaStream_t s);
+cudaError_t launch_post_adv(const BatchLaunch& L, cudaStream_t s);
+cudaError_t launch_post_euler(const BatchLaunch& L, cudaStream_t s);
 }  // namespace grp

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 GRP_ADVECTION, GRP_EULER_IDEAL = 0, 1
 GRP_BC_PERIODIC, GRP_BC_TRANSMISSIVE = 0, 1
 GRP_GUESS_PVRS, GRP_GUESS_TRRS, GRP_GUESS_MLP = 0, 1, 2
-GRP_LAUNCH_AUTO, GRP_LAUNCH_FLAT, GRP_LAUNCH_BATCH = 0, 1, 2
+GRP_LAUNCH_AUTO, GRP_LAUNCH_FLAT, GRP_LAUNCH_FUSED, GRP_LAUNCH_SPLIT = 0, 1, 2, 3
 GRP_OK = 0
 GRP_NSTATS = 9
 (STAT_STEPS, STAT_NEWTON_SUM, STAT_NEWTON_MAX, STAT_RECON_FB, STAT_FLUX_FB, STAT_RS_CALLS,
@@ -209,7 +209,7 @@ class Solver:
     def get_launch(self):
         v = [ctypes.c_int(0) for _ in range(5)]
         _check(self.L.grp_get_launch(self.h, *[ctypes.byref(x) for x in v]), "grp_get_launch")
-        return dict(zip(("batched", "threads", "cells_per_block", "steps_per_launch", "blocks"),
+        return dict(zip(("form", "threads", "cells_per_block", "steps_per_launch", "blocks"),
                         [x.value for x in v]))
 
     def launch_count(self):

@@ -145,18 +145,20 @@ def test_generic_gamma_path():
     check_parity(prob, avg, lm, lp, 10 ** 6, DISC_TOL, t_end=0.2)
 
 
-BATCH_CONFIGS = [(256, 2048, 8), (128, 256, 1), (256, 700, 3), (128, 4096, 16)]
+BATCH_CONFIGS = [(2, 256, 2048, 8), (2, 128, 256, 1), (2, 256, 700, 3), (2, 128, 4096, 16),
+                 (3, 256, 2048, 1), (3, 128, 300, 1), (3, 256, 8192, 1)]
 
 
-@pytest.mark.parametrize("threads,cells,k", BATCH_CONFIGS)
-def test_batched_kernel_matches_oracle(threads, cells, k):
-    """The persistent per-domain-group kernel, in several launch shapes."""
+@pytest.mark.parametrize("form,threads,cells,k", BATCH_CONFIGS)
+def test_batched_kernels_match_oracle(form, threads, cells, k):
+    """The fused persistent kernel (form 2) and the split form (form 3), in
+    several launch shapes."""
     ids = np.arange(0, 65536, 211)[:200]
     prob, avg, lm, lp = I.batched(domains=ids)
     from paper_2602_21911_gb300 import grprec
     s = grprec.Solver(prob)
-    s.set_launch(grprec.GRP_LAUNCH_BATCH, threads, cells, k)
-    assert s.get_launch()["batched"] == 1
+    s.set_launch(form, threads, cells, k)
+    assert s.get_launch()["form"] == form
     check_parity(prob, avg, lm, lp, 37, DISC_TOL, solver=s)
 
 
@@ -165,26 +167,31 @@ def test_batched_and_flat_kernels_agree():
     prob, avg, lm, lp = I.batched(domains=ids)
     from paper_2602_21911_gb300 import grprec
     out = []
-    for mode in (grprec.GRP_LAUNCH_FLAT, grprec.GRP_LAUNCH_BATCH):
+    for mode in (grprec.GRP_LAUNCH_FLAT, grprec.GRP_LAUNCH_FUSED, grprec.GRP_LAUNCH_SPLIT):
         s = grprec.Solver(prob)
         s.set_launch(mode, 256, 2048, 8)
         s.set_initial(avg, lm, lp)
         s.step(60)
         out.append(s.get_state())
-    assert rel_diff(out[0][0], out[1][0], prob).max() < 1e-12
-    assert np.allclose(out[0][2], out[1][2], rtol=1e-12)
+    for other in out[1:]:
+        assert rel_diff(out[0][0], other[0], prob).max() < 1e-12
+        assert np.allclose(out[0][2], other[2], rtol=1e-12)
 
 
 def test_batched_kernel_advection_and_periodic_domains():
     prob, avg, lm, lp = I.advection_sine(96, M=3)
     from paper_2602_21911_gb300 import grprec
     s = grprec.Solver(prob)
-    s.set_launch(grprec.GRP_LAUNCH_BATCH, 128, 1024, 5)
+    s.set_launch(grprec.GRP_LAUNCH_FUSED, 128, 1024, 5)
     check_parity(prob, avg, lm, lp, 10 ** 6, SMOOTH_TOL, t_end=0.7, solver=s)
     prob, avg, lm, lp = I.euler_wave(64, 4)
     s = grprec.Solver(prob)
-    s.set_launch(grprec.GRP_LAUNCH_BATCH, 256, 2048, 7)
+    s.set_launch(grprec.GRP_LAUNCH_FUSED, 256, 2048, 7)
     check_parity(prob, avg, lm, lp, 10 ** 6, SMOOTH_TOL, t_end=1.0, solver=s)
+    prob, avg, lm, lp = I.sod(500, M=2)
+    s = grprec.Solver(prob)
+    s.set_launch(grprec.GRP_LAUNCH_SPLIT, 256, 2048, 1)
+    check_parity(prob, avg, lm, lp, 10 ** 6, DISC_TOL, t_end=0.2, solver=s)
 
 
 def test_launch_configuration_is_validated():
@@ -194,4 +201,4 @@ def test_launch_configuration_is_validated():
     for bad in ((5, 256, 2048, 8), (1, 100, 2048, 8), (1, 256, 10, 8), (1, 256, 2048, 0)):
         with pytest.raises(grprec.GrpError):
             s.set_launch(*bad)
-    assert s.get_launch()["batched"] == 0          # auto: one short domain runs flat
+    assert s.get_launch()["form"] == grprec.GRP_LAUNCH_FLAT     # auto: one short domain runs flat
