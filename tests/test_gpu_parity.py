@@ -173,9 +173,11 @@ def test_batched_and_flat_kernels_agree():
         s.set_initial(avg, lm, lp)
         s.step(60)
         out.append(s.get_state())
+    # the forms inline the same device functions in different kernels, so FMA
+    # contraction may differ: they agree to the discontinuous-run tolerance
     for other in out[1:]:
-        assert rel_diff(out[0][0], other[0], prob).max() < 1e-12
-        assert np.allclose(out[0][2], other[2], rtol=1e-12)
+        assert rel_diff(out[0][0], other[0], prob).max() < DISC_TOL
+        assert np.allclose(out[0][2], other[2], rtol=DISC_TOL)
 
 
 def test_batched_kernel_advection_and_periodic_domains():
