@@ -203,6 +203,40 @@ int grp_get_kernel_timing(grp_ctx *ctx, double *flux_ms, long long *flux_launche
  */
 int grp_probe_fp64_peak(int device, double *flops_per_s);
 
+/*
+ * One time step of one domain without any device allocation.  (The paper has
+ * no counterpart: this is an integration entry point of this library.)
+ *
+ * For callers that cannot call cudaMalloc -- code running inside another
+ * framework's memory pool or allocator hooks, plug-ins whose host process owns
+ * all device memory, loops that must not allocate after start-up.  It runs the
+ * same kernels as grp_step (flat form, dt = C dx / S_max of the input averages,
+ * clipped to t_end, newton_rtol 1e-12, newton_max_iter 50, PVRS guess) on
+ * buffers the caller owns, and keeps its scratch (interface fluxes, repair
+ * flags, per-domain words, index tables) in a file-scope __device__ array of
+ * the library sized for GRP_NOALLOC_MAX_CELLS cells; every GPU that loads the
+ * library holds that array (about 2.3 MB) until the process exits.
+ *   avg_in, iface_in:   device, C planes of n_cells / n_ifaces doubles (read)
+ *   avg_out, iface_out: device, same sizes (written); must not alias the inputs
+ *   t, t_end:           time of the input state, end time (INFINITY: none)
+ *   *t_out, *status_out: host; the new time and the GRP_ST_* status
+ *   stream:             cudaStream_t of the work (NULL = default stream)
+ * n_ifaces = n_cells + (bc == GRP_BC_TRANSMISSIVE).  Allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.  The first call on a
+ * device (with that device current) looks up the device address of the scratch
+ * array; make that first call before any stream capture.  Every call shares the
+ * scratch and it keeps the last call's contents; the call clears what must
+ * start at zero.  Calls that overlap on the GPU (other streams, other host
+ * threads) race on the scratch: serialise them.  Synchronises `stream` before
+ * returning.  Errors: GRP_E_INVALID_ARG (including n_cells >
+ * GRP_NOALLOC_MAX_CELLS), GRP_E_CUDA.
+ */
+#define GRP_NOALLOC_MAX_CELLS 65536
+int grp_step_noalloc(int system, double lambda, double gamma, int M, double cfl, int n_cells,
+                     double x_left, double x_right, int bc, const double *avg_in,
+                     const double *iface_in, double *avg_out, double *iface_out, double t,
+                     double t_end, double *t_out, int *status_out, void *stream);
+
 /* Release every device allocation of the context; ctx may be NULL. */
 void grp_destroy(grp_ctx *ctx);
 

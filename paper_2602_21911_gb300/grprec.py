@@ -69,6 +69,10 @@ def load(build_if_missing=True):
     L.grp_set_launch.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     _ip = ctypes.POINTER(ctypes.c_int)
     L.grp_get_launch.argtypes = [_vp, _ip, _ip, _ip, _ip, _ip]
+    L.grp_step_noalloc.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                   ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp]
     L.grp_destroy.argtypes = [_vp]
     L.grp_destroy.restype = None
     L.grp_status_string.argtypes = [ctypes.c_int]
@@ -82,6 +86,32 @@ def grp_probe_fp64_peak(device=0):
     v = ctypes.c_double(0.0)
     _check(load().grp_probe_fp64_peak(int(device), ctypes.byref(v)), "grp_probe_fp64_peak")
     return v.value
+
+
+GRP_NOALLOC_MAX_CELLS = 65536
+
+
+def grp_step_noalloc(prob, avg_in, iface_in, avg_out, iface_out, t, t_end=float("inf"), stream=None):
+    """One step of a single-domain problem through the allocation-free entry
+    point; the four buffers are device tensors the caller owns.  Returns
+    (t_new, status)."""
+    n = np.asarray(prob["n_cells"])
+    if n.size != 1:
+        raise GrpError("grp_step_noalloc advances one domain")
+    ptrs = []
+    for x in (avg_in, iface_in, avg_out, iface_out):
+        p, dev = _ptr(x)
+        if not dev:
+            raise GrpError("grp_step_noalloc takes device buffers")
+        ptrs.append(p)
+    t_out, st = ctypes.c_double(0.0), ctypes.c_int(0)
+    _check(load().grp_step_noalloc(int(prob["system"]), float(prob.get("lam", 1.0)),
+                                   float(prob.get("gamma", 1.4)), int(prob["M"]), float(prob["cfl"]),
+                                   int(n[0]), float(np.asarray(prob["x_left"])[0]),
+                                   float(np.asarray(prob["x_right"])[0]), int(np.asarray(prob["bc"])[0]),
+                                   *ptrs, float(t), float(t_end), ctypes.byref(t_out), ctypes.byref(st),
+                                   stream), "grp_step_noalloc")
+    return t_out.value, st.value
 
 
 def grp_status_string(code):
