@@ -35,7 +35,7 @@ struct grp_ctx {
   double *t = nullptr, *dt_prev = nullptr;
   int *nstep = nullptr, *status = nullptr;
   unsigned long long* smax_bits = nullptr;
-  int *bad = nullptr, *inad = nullptr, *changed = nullptr, *fail = nullptr, *any_bad = nullptr;
+  int *bad = nullptr, *inad = nullptr, *fail = nullptr, *any_bad = nullptr;
   unsigned long long* stats = nullptr;
   double* scratch_norm = nullptr;
   float *mlp = nullptr, *mlp_norm = nullptr;
@@ -80,7 +80,7 @@ void free_all(grp_ctx* c)
   c->ev_pending.clear();
   void* ptrs[] = {c->cell_off, c->if_off, c->cell_dom, c->if_dom, c->dx, c->bc, c->avg[0], c->avg[1],
                   c->ifc[0], c->ifc[1], c->flux, c->low, c->troubled, c->t, c->dt_prev, c->nstep,
-                  c->status, c->smax_bits, c->bad, c->inad, c->changed, c->fail, c->any_bad, c->stats,
+                  c->status, c->smax_bits, c->bad, c->inad, c->fail, c->any_bad, c->stats,
                   c->scratch_norm, c->mlp, c->mlp_norm, c->grp};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -123,7 +123,6 @@ StepArgs make_args(const grp_ctx* c, double t_end)
   a.smax_bits = c->smax_bits;
   a.bad = c->bad;
   a.inad = c->inad;
-  a.changed = c->changed;
   a.fail = c->fail;
   a.any_bad = c->any_bad;
   a.stats = c->stats;
@@ -384,7 +383,7 @@ int grp_create(grp_ctx** out, const grp_problem* p)
   AL(cell_off, D + 1) AL(if_off, D + 1) AL(cell_dom, c->ncell) AL(if_dom, c->nif) AL(dx, D) AL(bc, D)
   AL(avg[0], C * c->ncell) AL(avg[1], C * c->ncell) AL(ifc[0], C * c->nif) AL(ifc[1], C * c->nif)
   AL(flux, C * c->nif) AL(low, c->nif) AL(troubled, c->ncell) AL(t, D) AL(dt_prev, D) AL(nstep, D)
-  AL(status, D) AL(smax_bits, D) AL(bad, (MAX_REPAIR + 1) * D) AL(inad, (MAX_REPAIR + 1) * D) AL(changed, MAX_REPAIR * D) AL(fail, D)
+  AL(status, D) AL(smax_bits, D) AL(bad, (MAX_REPAIR + 1) * D) AL(inad, D) AL(fail, D)
   AL(any_bad, MAX_REPAIR + 1) AL(stats, (long long)NSTATS * D) AL(scratch_norm, 3 * D)
 #undef AL
   struct Cp { void* dst; const void* src; size_t n; } cps[] = {

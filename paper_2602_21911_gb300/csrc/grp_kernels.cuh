@@ -39,17 +39,16 @@ struct StepArgs {
   const double* ifc;                 // current interface data [C][nif]
   double* ifc_new;                   // next interface data    [C][nif]
   double* flux;                      // scratch [C][nif]
-  unsigned char* low;                // [nif] interface recomputed at first order this step
-  unsigned char* troubled;           // [ncell]
+  unsigned char* low;                // [nif] 0 high order; 1 first order (flux kernel); 2+r repaired in round r
+  unsigned char* troubled;           // [ncell] 0 ok; 1 outside the relaxed DMP; 2 inadmissible
   // per-domain words
   double* t;                         // [D]
   double* dt_prev;                   // [D]
   int* nstep;                        // [D]
   int* status;                       // [D]
   unsigned long long* smax_bits;     // [D] S_max as the bits of a non-negative double
-  int* bad;                          // [(MAX_REPAIR+1) * D] troubled cells (repair wanted) after pass p
-  int* inad;                         // [(MAX_REPAIR+1) * D] inadmissible cells after pass p
-  int* changed;                      // [MAX_REPAIR * D] interfaces repaired in pass p
+  int* bad;                          // [(MAX_REPAIR+1) * D] newly troubled cells (repair wanted) after pass p
+  int* inad;                         // [D] number of inadmissible candidate averages
   int* fail;                         // [D] non-zero: solver failure code this step
   int* any_bad;                      // [MAX_REPAIR+1] any domain troubled after pass p
   unsigned long long* stats;         // [D][NSTATS]
@@ -108,8 +107,8 @@ __device__ __forceinline__ void nbr(int i, int N, int bc, int& im, int& ip)
 
 __device__ __forceinline__ void reset_domain_words(const StepArgs& a, int d)
 {
-  for (int p = 0; p <= MAX_REPAIR; ++p) a.bad[p * a.n_domains + d] = a.inad[p * a.n_domains + d] = 0;
-  for (int p = 0; p < MAX_REPAIR; ++p) a.changed[p * a.n_domains + d] = 0;
+  for (int p = 0; p <= MAX_REPAIR; ++p) a.bad[p * a.n_domains + d] = 0;
+  a.inad[d] = 0;
   a.fail[d] = 0;
 }
 
@@ -319,29 +318,33 @@ __global__ void __launch_bounds__(128) k_flux(StepArgs a)
 // Candidate average of cell gi from the flux array, with the a-posteriori
 // detection: inadmissible, or outside the relaxed discrete maximum principle
 // on density and pressure against the old averages of cells i-1, i, i+1.
-// pass < 0: first update of the step; else a repair re-update (only domains
-// flagged after pass `pass` whose repair changed something).
+// pass < 0: first update of the step; else the re-update after repair round
+// `pass`, which recomputes only the cells next to an interface repaired in
+// that round (every other candidate depends on unchanged fluxes).
 // Returns bit 0: troubled, bit 1: inadmissible.
 template <int SYS>
 __device__ __forceinline__ int update_one(const StepArgs& a, long long gi, int d, int pass)
 {
   constexpr int C = SYS == SYS_EULER ? 3 : 1;
-  double dt, dt_cfl;
-  bool last;
-  const bool active = domain_dt(a, d, dt, dt_cfl, last);
-  if (pass >= 0) {
-    if (!active || !a.bad[pass * a.n_domains + d]) return 0;
-    if (!a.changed[pass * a.n_domains + d]) return 0;     // nothing repaired: finish freezes it
-  }
-  if (!active) {
-#pragma unroll
-    for (int c = 0; c < C; ++c) a.avg_new[c * a.ncell + gi] = a.avg[c * a.ncell + gi];
-    return 0;
-  }
   const long long c0 = a.cell_off[d], i0 = a.if_off[d];
   const int N = (int)(a.cell_off[d + 1] - c0);
   const int i = (int)(gi - c0);
   const int jl = i, jr = (a.bc[d] == 0) ? (i == N - 1 ? 0 : i + 1) : i + 1;
+  if (pass >= 0) {
+    // a re-update only concerns cells next to an interface repaired in this round
+    const unsigned char mark = (unsigned char)(2 + pass);
+    if (a.low[i0 + jl] != mark && a.low[i0 + jr] != mark) return 0;
+  }
+  double dt, dt_cfl;
+  bool last;
+  const bool active = domain_dt(a, d, dt, dt_cfl, last);
+  if (!active) {
+    if (pass < 0) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) a.avg_new[c * a.ncell + gi] = a.avg[c * a.ncell + gi];
+    }
+    return 0;
+  }
   const double r = dt / a.dx[d];
   double Q[3];
 #pragma unroll
@@ -369,10 +372,12 @@ __device__ __forceinline__ int update_one(const StepArgs& a, long long gi, int d
     const double d0 = DMP_REL * fmax(fabs(lo0), fabs(hi0)), d1 = DMP_REL * fmax(fabs(lo1), fabs(hi1));
     ok = wc.r >= lo0 - d0 && wc.r <= hi0 + d0 && wc.p >= lo1 - d1 && wc.p <= hi1 + d1;
   }
-  a.troubled[gi] = ok ? 0 : 1;
-  const int np = pass + 1;
-  if (!ok) a.bad[np * a.n_domains + d] = 1;
-  if (!adm) a.inad[np * a.n_domains + d] = 1;
+  const unsigned char flag = adm ? (ok ? 0 : 1) : 2;
+  const unsigned char before = pass < 0 ? 0 : a.troubled[gi];
+  a.troubled[gi] = flag;
+  if (flag) a.bad[(pass + 1) * a.n_domains + d] = 1;
+  if (flag == 2 && before != 2) atomicAdd(a.inad + d, 1);
+  if (flag != 2 && before == 2) atomicSub(a.inad + d, 1);
   return (ok ? 0 : 1) | (adm ? 0 : 2);
 }
 
@@ -393,10 +398,7 @@ __global__ void k_update(StepArgs a, int pass)
 template <bool G75>
 static __device__ __forceinline__ void repair_one(const StepArgs& a, int pass, long long gj, int d, unsigned st[3])
 {
-  if (!a.bad[pass * a.n_domains + d]) return;
-  double dt, dt_cfl;
-  bool last;
-  if (!domain_dt(a, d, dt, dt_cfl, last)) return;
+  if (!a.bad[pass * a.n_domains + d]) return;         // only domains with new troubled cells (all active)
   if (a.low[gj]) return;
   const long long i0 = a.if_off[d], c0 = a.cell_off[d];
   const int j = (int)(gj - i0);
@@ -418,8 +420,7 @@ static __device__ __forceinline__ void repair_one(const StepArgs& a, int pass, l
     a.flux[c * a.nif + gj] = F[c];
     a.ifc_new[c * a.nif + gj] = Q0[c];
   }
-  a.low[gj] = 1;
-  a.changed[pass * a.n_domains + d] = 1;
+  a.low[gj] = (unsigned char)(2 + pass);
 }
 
 template <bool G75>
@@ -455,12 +456,7 @@ __device__ __forceinline__ void finish_one(const StepArgs& a, int d)
   a.nstep[d] += 1;
   a.dt_prev[d] = dt_cfl;
   a.stats[(long long)d * NSTATS + S_STEPS] += 1;
-  if (a.sys == SYS_EULER) {
-    // the committed candidate is the one of the last pass that changed something
-    int p = 0;
-    while (p < MAX_REPAIR && a.bad[p * a.n_domains + d] && a.changed[p * a.n_domains + d]) ++p;
-    if (a.inad[p * a.n_domains + d]) a.status[d] = ST_NONPHYS;
-  }
+  if (a.sys == SYS_EULER && a.inad[d] > 0) a.status[d] = ST_NONPHYS;
 }
 
 static __global__ void k_finish(StepArgs a)

@@ -39,7 +39,7 @@ struct Words {
   unsigned long long smax_bits;
   unsigned long long stats[NSTATS];
   int nstep, status, fail;
-  int bad[MAX_REPAIR + 1], inad[MAX_REPAIR + 1], changed[MAX_REPAIR], any_bad[MAX_REPAIR + 1];
+  int bad[MAX_REPAIR + 1], inad, any_bad[MAX_REPAIR + 1];
   unsigned char bc;
 };
 constexpr size_t SCRATCH_BYTES = align256(OFF_WORDS + sizeof(Words));
@@ -66,8 +66,8 @@ __global__ void k_noalloc_setup(unsigned char* base, int N, int nif, double dx, 
     w->smax_bits = 0ull;
     for (int k = 0; k < NSTATS; ++k) w->stats[k] = 0ull;
     w->nstep = 0; w->status = 0; w->fail = 0;
-    for (int p = 0; p <= MAX_REPAIR; ++p) { w->bad[p] = 0; w->inad[p] = 0; w->any_bad[p] = 0; }
-    for (int p = 0; p < MAX_REPAIR; ++p) w->changed[p] = 0;
+    for (int p = 0; p <= MAX_REPAIR; ++p) { w->bad[p] = 0; w->any_bad[p] = 0; }
+    w->inad = 0;
     w->bc = (unsigned char)bc;
   }
 }
@@ -133,7 +133,7 @@ extern "C" int grp_step_noalloc(int system, double lambda, double gamma, int M, 
   a.low = base + OFF_LOW; a.troubled = base + OFF_TROUBLED;
   a.t = &w->t; a.dt_prev = &w->dt_prev; a.nstep = &w->nstep; a.status = &w->status;
   a.smax_bits = &w->smax_bits;
-  a.bad = w->bad; a.inad = w->inad; a.changed = w->changed; a.fail = &w->fail; a.any_bad = w->any_bad;
+  a.bad = w->bad; a.inad = &w->inad; a.fail = &w->fail; a.any_bad = w->any_bad;
   a.stats = w->stats;
   a.mlp = nullptr; a.mlp_norm = nullptr;
 
