@@ -92,11 +92,7 @@ StepArgs make_args(const grp_ctx* c, double t_end)
   a.sys = c->p.system;
   a.M = c->p.M;
   a.C = c->C;
-  a.ph.lambda = c->p.lambda;
-  a.ph.gamma = c->p.gamma;
-  a.ph.rtol = c->p.newton_rtol;
-  a.ph.max_iter = c->p.newton_max_iter;
-  a.ph.guess = c->p.guess;
+  a.ph = make_phys(c->p.lambda, c->p.gamma, c->p.newton_rtol, c->p.newton_max_iter, c->p.guess);
   a.cfl = c->p.cfl;
   a.t_end = t_end;
   a.dt_hold = c->p.dt_hold;
@@ -429,9 +425,7 @@ int grp_set_initial(grp_ctx* c, const double* averages, const double* lim_minus,
     double* lp = c->ifc[1];
     CK(cudaMemcpyAsync(lm, lim_minus, sizeof(double) * c->C * c->nif, k, s));
     CK(cudaMemcpyAsync(lp, lim_plus, sizeof(double) * c->C * c->nif, k, s));
-    Phys ph;
-    ph.lambda = c->p.lambda; ph.gamma = c->p.gamma; ph.rtol = c->p.newton_rtol;
-    ph.max_iter = c->p.newton_max_iter; ph.guess = 0;
+    const Phys ph = make_phys(c->p.lambda, c->p.gamma, c->p.newton_rtol, c->p.newton_max_iter, 0);
     k_init_iface<<<blocks(c->nif, 128), 128, 0, s>>>(c->p.system, ph, c->nif, lm, lp, c->ifc[0]);
     c->launches++;
     CK(cudaGetLastError());

@@ -29,7 +29,27 @@ struct Phys {
   double rtol;
   int max_iter;
   int guess;  // 0 PVRS, 1 TRRS, 2 learned
+  // gamma-dependent constants, computed once on the host (make_phys)
+  double gm1, i_gm1, c2_gm1, c2_gp1, gm1_gp1, gm1_2g, gp1_2g, c2g_gm1, i_g, sqrt_c2_gp1;
 };
+
+inline Phys make_phys(double lambda, double gamma, double rtol, int max_iter, int guess)
+{
+  Phys p;
+  p.lambda = lambda; p.gamma = gamma; p.rtol = rtol; p.max_iter = max_iter; p.guess = guess;
+  const double g = gamma;
+  p.gm1 = g - 1.0;
+  p.i_gm1 = 1.0 / (g - 1.0);
+  p.c2_gm1 = 2.0 / (g - 1.0);
+  p.c2_gp1 = 2.0 / (g + 1.0);
+  p.gm1_gp1 = (g - 1.0) / (g + 1.0);
+  p.gm1_2g = (g - 1.0) / (2.0 * g);
+  p.gp1_2g = (g + 1.0) / (2.0 * g);
+  p.c2g_gm1 = 2.0 * g / (g - 1.0);
+  p.i_g = 1.0 / g;
+  p.sqrt_c2_gp1 = sqrt(2.0 / (g + 1.0));
+  return p;
+}
 
 // ---------------------------------------------------------------------------
 // Section 3.1, GRPrec: closed forms of the four constrained fits in the
@@ -86,18 +106,18 @@ GRP_HD __forceinline__ Prim to_prim(double g, double r, double m, double E)
   return w;
 }
 
-GRP_HD __forceinline__ void to_cons(double g, Prim w, double Q[3])
+GRP_HD __forceinline__ void to_cons(const Phys& ph, Prim w, double Q[3])
 {
   Q[0] = w.r;
   Q[1] = w.r * w.u;
-  Q[2] = w.p / (g - 1.0) + 0.5 * w.r * w.u * w.u;
+  Q[2] = w.p * ph.i_gm1 + 0.5 * w.r * w.u * w.u;
 }
 
+// rho > 0 and p = (g-1)(E - m^2/(2 rho)) > 0, written without a division
 GRP_HD __forceinline__ bool admissible(double g, double r, double m, double E)
 {
-  if (!(r > 0.0)) return false;
-  const double p = (g - 1.0) * (E - 0.5 * m * (m / r));
-  return p > 0.0;
+  (void)g;
+  return r > 0.0 && 2.0 * E * r > m * m;
 }
 
 GRP_HD __forceinline__ void euler_flux(double g, double r, double m, double E, double F[3])
@@ -168,34 +188,44 @@ GRP_HD __forceinline__ double inv_root7(double x)
 // ---------------------------------------------------------------------------
 struct Side {
   double r, u, p, c;     // primitive state and sound speed
-  double A, B;           // shock branch: A = 2/((g+1) rho), B = (g-1)/(g+1) p
+  double ir, ic;         // 1/rho, 1/c
+  double sA, B;          // shock branch: sqrt(2/((g+1) rho)), (g-1)/(g+1) p
   double ip;             // 1/p
   double k;              // rarefaction branch: 2 c/(g-1)
   double d;              // rarefaction branch: 1/(rho c)
 };
 
-GRP_HD __forceinline__ Side make_side(double g, Prim W)
+// One side of a Riemann problem from its conserved state: two reciprocal
+// square roots and one division (1/p) replace the divisions of the textbook
+// expressions.
+GRP_HD __forceinline__ Side make_side(const Phys& ph, const double Q[3])
 {
   Side s;
-  s.r = W.r; s.u = W.u; s.p = W.p;
-  s.c = sqrt(g * W.p / W.r);
-  s.A = 2.0 / ((g + 1.0) * W.r);
-  s.B = (g - 1.0) / (g + 1.0) * W.p;
-  s.ip = 1.0 / W.p;
-  s.k = 2.0 * s.c / (g - 1.0);
-  s.d = 1.0 / (W.r * s.c);
+  const double tr = rsqrt(Q[0]);                 // rho^(-1/2)
+  s.r = Q[0];
+  s.ir = tr * tr;
+  s.u = Q[1] * s.ir;
+  s.p = ph.gm1 * (Q[2] - 0.5 * Q[1] * s.u);
+  const double c2 = ph.gamma * s.p * s.ir;
+  s.ic = rsqrt(c2);
+  s.c = c2 * s.ic;
+  s.sA = ph.sqrt_c2_gp1 * tr;
+  s.B = ph.gm1_gp1 * s.p;
+  s.ip = 1.0 / s.p;
+  s.k = ph.c2_gm1 * s.c;
+  s.d = s.ir * s.ic;
   return s;
 }
 
 // pressure function f_K(p) and its derivative
 template <bool G75>
-GRP_HD __forceinline__ void pressure_fn(double g, double p, const Side& K, double& f, double& df)
+GRP_HD __forceinline__ void pressure_fn(const Phys& ph, double p, const Side& K, double& f, double& df)
 {
   if (p > K.p) {
-    const double q = p + K.B;
-    const double s = sqrt(K.A / q);
+    const double t = rsqrt(p + K.B);             // (p + B)^(-1/2)
+    const double s = K.sA * t;                    // sqrt(A / (p + B))
     f = (p - K.p) * s;
-    df = s * (1.0 - (p - K.p) / (2.0 * q));
+    df = s * (1.0 - 0.5 * (p - K.p) * (t * t));
   } else if (G75) {
     const double x = p * K.ip;
     const double w = inv_root7(x);
@@ -204,8 +234,8 @@ GRP_HD __forceinline__ void pressure_fn(double g, double p, const Side& K, doubl
     df = K.d * w6;                        // (p/pK)^(-6/7)
   } else {
     const double x = p * K.ip;
-    f = K.k * (pow(x, (g - 1.0) / (2.0 * g)) - 1.0);
-    df = K.d * pow(x, -(g + 1.0) / (2.0 * g));
+    f = K.k * (pow(x, ph.gm1_2g) - 1.0);
+    df = K.d * pow(x, -ph.gp1_2g);
   }
 }
 
@@ -215,17 +245,16 @@ template <bool G75>
 static GRP_HD int star_pressure(const Phys& ph, const Side& L, const Side& R, double p0, double& ps, double& us,
                                 int& iters)
 {
-  const double g = ph.gamma;
   const double du = R.u - L.u;
   iters = 0;
-  if (2.0 * (L.c + R.c) / (g - 1.0) <= du) return ST_VACUUM;
+  if (ph.c2_gm1 * (L.c + R.c) <= du) return ST_VACUUM;
   const double pfloor = 1e-14 * fmax(L.p, R.p);
   double p;
   if (p0 > 0.0 && isfinite(p0)) {
     p = p0;
   } else if (ph.guess == 1) {
-    const double z = (g - 1.0) / (2.0 * g);
-    const double num = L.c + R.c - 0.5 * (g - 1.0) * du;
+    const double z = ph.gm1_2g;
+    const double num = L.c + R.c - 0.5 * ph.gm1 * du;
     const double den = L.c * pow(L.p, -z) + R.c * pow(R.p, -z);
     p = pow(num / den, 1.0 / z);
   } else {
@@ -237,8 +266,8 @@ static GRP_HD int star_pressure(const Phys& ph, const Side& L, const Side& R, do
   int it = 0;
   while (it < ph.max_iter) {
     double fL, dfL, fR, dfR;
-    pressure_fn<G75>(g, p, L, fL, dfL);
-    pressure_fn<G75>(g, p, R, fR, dfR);
+    pressure_fn<G75>(ph, p, L, fL, dfL);
+    pressure_fn<G75>(ph, p, R, fR, dfR);
     double step = -(fL + fR + du) * rcp_newton_step(dfL + dfR);
     double pn = p + step;
     for (int h = 0; h < 64 && !(pn > 0.0); ++h) { step *= 0.5; pn = p + step; }
@@ -251,8 +280,8 @@ static GRP_HD int star_pressure(const Phys& ph, const Side& L, const Side& R, do
   iters = it;
   if (!conv) return ST_NO_CONV;
   double fL, dfL, fR, dfR;
-  pressure_fn<G75>(g, p, L, fL, dfL);
-  pressure_fn<G75>(g, p, R, fR, dfR);
+  pressure_fn<G75>(ph, p, L, fL, dfL);
+  pressure_fn<G75>(ph, p, R, fR, dfR);
   ps = p;
   us = 0.5 * (L.u + R.u) + 0.5 * (fR - fL);
   return ST_OK;
@@ -261,78 +290,78 @@ static GRP_HD int star_pressure(const Phys& ph, const Side& L, const Side& R, do
 // Density behind a rarefaction from K to pressure ratio x = p/pK, and the
 // sound speed there: rho = rhoK x^(1/g), c = cK x^((g-1)/(2g)).
 template <bool G75>
-GRP_HD __forceinline__ void rarefied(double g, const Side& K, double x, double& rho, double& c)
+GRP_HD __forceinline__ void rarefied(const Phys& ph, const Side& K, double x, double& rho, double& c)
 {
   if (G75) {
     const double w = inv_root7(x), w2 = w * w;
     rho = K.r * x * w2;                  // x^(5/7)
     c = K.c * x * (w2 * w2 * w2);        // x^(1/7)
   } else {
-    rho = K.r * pow(x, 1.0 / g);
-    c = K.c * pow(x, (g - 1.0) / (2.0 * g));
+    rho = K.r * pow(x, ph.i_g);
+    c = K.c * pow(x, ph.gm1_2g);
   }
 }
 
 // Sonic state inside a fan: rho = rhoK q^(2/(g-1)), p = pK q^(2g/(g-1)), q = c0/cK.
 template <bool G75>
-GRP_HD __forceinline__ Prim sonic(double g, const Side& K, double c0, double u0)
+GRP_HD __forceinline__ Prim sonic(const Phys& ph, const Side& K, double c0, double u0)
 {
-  const double q = c0 / K.c;
+  const double q = c0 * K.ic;
   if (G75) {
     const double q2 = q * q, q5 = q2 * q2 * q;
     return Prim{K.r * q5, u0, K.p * q5 * q2};
   }
-  return Prim{K.r * pow(q, 2.0 / (g - 1.0)), u0, K.p * pow(q, 2.0 * g / (g - 1.0))};
+  return Prim{K.r * pow(q, ph.c2_gm1), u0, K.p * pow(q, ph.c2g_gm1)};
 }
 
 // Left of the contact when u* >= 0, sampled on the ray x/t = 0.  A contact
 // speed within TIE of the sound-speed scale is stationary and goes left.
 template <bool G75>
-static GRP_HD Prim sample_zero(double g, const Side& L, const Side& R, double ps, double us)
+static GRP_HD Prim sample_zero(const Phys& ph, const Side& L, const Side& R, double ps, double us)
 {
-  const double g1 = (g - 1.0) / (2.0 * g), g6 = (g - 1.0) / (g + 1.0);
+  const double g1 = ph.gm1_2g, g6 = ph.gm1_gp1;
   const Prim WL{L.r, L.u, L.p}, WR{R.r, R.u, R.p};
   if (us >= -TIE * (L.c + R.c)) {
     const double ratio = ps * L.ip;
     if (ps > L.p) {
-      const double S = L.u - L.c * sqrt((g + 1.0) / (2.0 * g) * ratio + g1);
+      const double S = L.u - L.c * sqrt(ph.gp1_2g * ratio + g1);
       if (S >= 0.0) return WL;
       return Prim{L.r * (ratio + g6) / (g6 * ratio + 1.0), us, ps};
     }
     if (L.u - L.c >= 0.0) return WL;
     double rho, cs;
-    rarefied<G75>(g, L, ratio, rho, cs);
+    rarefied<G75>(ph, L, ratio, rho, cs);
     if (us - cs < 0.0) return Prim{rho, us, ps};
-    const double c0 = 2.0 / (g + 1.0) * (L.c + 0.5 * (g - 1.0) * L.u);
-    return sonic<G75>(g, L, c0, c0);
+    const double c0 = ph.c2_gp1 * (L.c + 0.5 * ph.gm1 * L.u);
+    return sonic<G75>(ph, L, c0, c0);
   }
   const double ratio = ps * R.ip;
   if (ps > R.p) {
-    const double S = R.u + R.c * sqrt((g + 1.0) / (2.0 * g) * ratio + g1);
+    const double S = R.u + R.c * sqrt(ph.gp1_2g * ratio + g1);
     if (S <= 0.0) return WR;
     return Prim{R.r * (ratio + g6) / (g6 * ratio + 1.0), us, ps};
   }
   if (R.u + R.c <= 0.0) return WR;
   double rho, cs;
-  rarefied<G75>(g, R, ratio, rho, cs);
+  rarefied<G75>(ph, R, ratio, rho, cs);
   if (us + cs > 0.0) return Prim{rho, us, ps};
-  const double c0 = 2.0 / (g + 1.0) * (R.c - 0.5 * (g - 1.0) * R.u);
-  return sonic<G75>(g, R, c0, -c0);
+  const double c0 = ph.c2_gp1 * (R.c - 0.5 * ph.gm1 * R.u);
+  return sonic<G75>(ph, R, c0, -c0);
 }
 
 // Vacuum-generating data: two rarefactions around a vacuum, sampled at x/t = 0.
 template <bool G75>
-static GRP_HD Prim sample_vacuum_zero(double g, const Side& L, const Side& R)
+static GRP_HD Prim sample_vacuum_zero(const Phys& ph, const Side& L, const Side& R)
 {
   if (L.u - L.c >= 0.0) return Prim{L.r, L.u, L.p};
-  if (L.u + 2.0 * L.c / (g - 1.0) > 0.0) {
-    const double c0 = 2.0 / (g + 1.0) * (L.c + 0.5 * (g - 1.0) * L.u);
-    return sonic<G75>(g, L, c0, c0);
+  if (L.u + ph.c2_gm1 * L.c > 0.0) {
+    const double c0 = ph.c2_gp1 * (L.c + 0.5 * ph.gm1 * L.u);
+    return sonic<G75>(ph, L, c0, c0);
   }
   if (R.u + R.c <= 0.0) return Prim{R.r, R.u, R.p};
-  if (R.u - 2.0 * R.c / (g - 1.0) < 0.0) {
-    const double c0 = 2.0 / (g + 1.0) * (R.c - 0.5 * (g - 1.0) * R.u);
-    return sonic<G75>(g, R, c0, -c0);
+  if (R.u - ph.c2_gm1 * R.c < 0.0) {
+    const double c0 = ph.c2_gp1 * (R.c - 0.5 * ph.gm1 * R.u);
+    return sonic<G75>(ph, R, c0, -c0);
   }
   return Prim{0.0, 0.0, 0.0};
 }
@@ -344,19 +373,18 @@ template <bool G75>
 static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double QR[3], double p0,
                                 bool allow_vacuum, double Q[3], Prim& W, int& iters)
 {
-  const double g = ph.gamma;
-  const Side L = make_side(g, to_prim(g, QL[0], QL[1], QL[2]));
-  const Side R = make_side(g, to_prim(g, QR[0], QR[1], QR[2]));
+  const Side L = make_side(ph, QL);
+  const Side R = make_side(ph, QR);
   double ps = 0.0, us = 0.0;
   const int st = star_pressure<G75>(ph, L, R, p0, ps, us, iters);
   if (st == ST_VACUUM && allow_vacuum) {
-    W = sample_vacuum_zero<G75>(g, L, R);
-    to_cons(g, W, Q);
+    W = sample_vacuum_zero<G75>(ph, L, R);
+    to_cons(ph, W, Q);
     return ST_VACUUM;
   }
   if (st != ST_OK) return st;
-  W = sample_zero<G75>(g, L, R, ps, us);
-  to_cons(g, W, Q);
+  W = sample_zero<G75>(ph, L, R, ps, us);
+  to_cons(ph, W, Q);
   return ST_OK;
 }
 
@@ -373,16 +401,16 @@ struct Eig {
   double lam[3];
 };
 
-GRP_HD __forceinline__ Eig make_eig(double g, const double Q0[3], Prim w)
+GRP_HD __forceinline__ Eig make_eig(const Phys& ph, const double Q0[3], Prim w)
 {
   Eig e;
   const double ir = 1.0 / w.r;
   e.u = w.u;
-  const double c2 = g * w.p * ir;
-  e.c = sqrt(c2);
+  const double c2 = ph.gamma * w.p * ir;
+  e.ic = rsqrt(c2);
+  e.c = c2 * e.ic;
   e.H = (Q0[2] + w.p) * ir;
-  e.ic = e.c / c2;
-  e.b1 = (g - 1.0) * e.ic * e.ic;
+  e.b1 = ph.gm1 * e.ic * e.ic;
   e.b2 = 0.5 * e.u * e.u * e.b1;
   e.lam[0] = e.u - e.c; e.lam[1] = e.u; e.lam[2] = e.u + e.c;
   e.tie = TIE * (fabs(e.u) + e.c);
@@ -550,7 +578,7 @@ GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[
   double rho[T::N], m[T::N], E[T::N];
   rho[0] = Q0[0]; m[0] = Q0[1]; E[0] = Q0[2];
   {
-    const Eig e = make_eig(g, Q0, W0);
+    const Eig e = make_eig(ph, Q0, W0);
 #pragma unroll
     for (int k = 1; k <= M; ++k) {
       const double DL[3] = {tL[0][k], tL[1][k], tL[2][k]}, DR[3] = {tR[0][k], tR[1][k], tR[2][k]};

@@ -122,7 +122,7 @@ extern "C" int grp_step_noalloc(int system, double lambda, double gamma, int M, 
 
   StepArgs a;
   a.sys = system; a.M = M; a.C = system == GRP_EULER_IDEAL ? 3 : 1;
-  a.ph.lambda = lambda; a.ph.gamma = gamma; a.ph.rtol = 1e-12; a.ph.max_iter = 50; a.ph.guess = 0;
+  a.ph = make_phys(lambda, gamma, 1e-12, 50, 0);
   a.cfl = cfl; a.t_end = t_end; a.dt_hold = 1;
   a.n_domains = 1; a.ncell = N; a.nif = nif;
   a.cell_off = w->cell_off; a.if_off = w->if_off;
