@@ -183,6 +183,52 @@ int grp_set_launch(grp_ctx *ctx, int mode, int threads, int cells_per_block, int
 int grp_get_launch(const grp_ctx *ctx, int *batched, int *threads, int *cells_per_block,
                    int *steps_per_launch, int *blocks);
 
+/*
+ * Learned Newton initial guess for the star pressure (not in the paper: an
+ * FP32 network that replaces the PVRS start of the exact Riemann solver on
+ * non-trivial data; the converged p* is unchanged).
+ *
+ * Network: 6 -> 64 -> 64 -> 1 with tanh hidden layers.  Inputs, for primitive
+ * states (rho,u,p)_L,R with rbar = sqrt(rhoL rhoR), pbar = sqrt(pL pR),
+ * cbar = sqrt(gamma pbar / rbar), ubar = (uL+uR)/2:
+ *   ln(rhoL/rbar), ln(rhoR/rbar), ln(pL/pbar), ln(pR/pbar), (uL-ubar)/cbar, (uR-ubar)/cbar
+ * Output: y = ln(p* / pbar).  Data count as non-trivial when |ln(pL/pR)| > 0.05
+ * or |uR-uL|/cbar > 0.05.  Parameters (GRP_MLP_NPARAM floats): W1[6][64],
+ * b1[64], W2[64][64], b2[64], w3[64], b3.
+ *
+ * grp_set_guess_model: load the weights and the input box (12 floats: lo[6],
+ * hi[6]); used when grp_problem.guess == GRP_GUESS_MLP.  An input outside the
+ * box, an output that is not finite or outside |y| <= ln 1e8, or no
+ * convergence within 8 Newton iterations falls back to PVRS; the counters
+ * GRP_STAT_GUESS_USED / GRP_STAT_GUESS_REJECTED record both.  Pointers host or
+ * device (ptr_is_device); copied, not kept.  Synchronises.
+ *
+ * grp_set_harvest: record (6 inputs, ln(p* / pbar), Newton iterations) of one
+ * non-trivial interface in 2^log2_stride, by a hash of (interface, step),
+ * into the caller's device buffer records[capacity][8] during later steps;
+ * *count (device, caller-zeroed) counts the offered records and may exceed
+ * capacity (the excess is dropped).  records = NULL stops harvesting.
+ *
+ * Training kernels (device pointers, FP32, ordered on `stream`):
+ *   grp_mlp_forward:   y[n] = network(x[n][6])
+ *   grp_mlp_loss_grad: *loss = mean (network(x) - t)^2 over n samples (device
+ *                      float), grad[GRP_MLP_NPARAM] its gradient; work holds
+ *                      GRP_MLP_WORK_FLOATS(n) floats of scratch
+ *   grp_mlp_adam:      one Adam step (Kingma & Ba) of the weights with moments
+ *                      m, v (GRP_MLP_NPARAM each, zero before step 1)
+ */
+#define GRP_MLP_NPARAM 4673
+#define GRP_MLP_WORK_FLOATS(n) ((long long)(n) * 257)
+int grp_set_guess_model(grp_ctx *ctx, const float *weights, int n_weights, const float *box,
+                        int ptr_is_device);
+int grp_set_harvest(grp_ctx *ctx, float *records, unsigned long long *count, long long capacity,
+                    int log2_stride);
+int grp_mlp_forward(const float *weights, const float *x, long long n, float *y, void *stream);
+int grp_mlp_loss_grad(const float *weights, const float *x, const float *target, long long n,
+                      float *grad, float *loss, float *work, void *stream);
+int grp_mlp_adam(float *weights, const float *grad, float *m, float *v, int step, float lr,
+                 float beta1, float beta2, float eps, void *stream);
+
 /* Number of kernel launches this context has enqueued since grp_create. */
 long long grp_launch_count(const grp_ctx *ctx);
 

@@ -38,7 +38,11 @@ struct grp_ctx {
   int *bad = nullptr, *inad = nullptr, *fail = nullptr, *any_bad = nullptr;
   unsigned long long* stats = nullptr;
   double* scratch_norm = nullptr;
-  float *mlp = nullptr, *mlp_norm = nullptr;
+  float *mlp = nullptr, *mlp_norm = nullptr;     // learned guess: weights, input box (library-owned)
+  float* harvest = nullptr;                        // caller-owned harvest buffer and counter
+  unsigned long long* harvest_count = nullptr;
+  long long harvest_cap = 0;
+  int harvest_log2_stride = 0;
   // launch configuration (grp_set_launch)
   int mode = GRP_LAUNCH_AUTO, threads = 256, cells_per_block = 2048, steps_per_launch = 8;
   int max_cells = 0;
@@ -122,8 +126,13 @@ StepArgs make_args(const grp_ctx* c, double t_end)
   a.fail = c->fail;
   a.any_bad = c->any_bad;
   a.stats = c->stats;
-  a.mlp = c->mlp;
-  a.mlp_norm = c->mlp_norm;
+  a.ph.mlp_w = c->mlp;
+  a.ph.mlp_box = c->mlp_norm;
+  a.ph.features = (c->p.guess == GRP_GUESS_MLP && c->mlp) || c->harvest ? 1 : 0;
+  a.harvest = c->harvest;
+  a.harvest_count = c->harvest_count;
+  a.harvest_cap = c->harvest_cap;
+  a.harvest_log2_stride = c->harvest_log2_stride;
   return a;
 }
 
@@ -601,6 +610,30 @@ int grp_error_norms(grp_ctx* c, const double* exact, int ptr_is_device, double* 
 }
 
 long long grp_launch_count(const grp_ctx* c) { return c ? c->launches : 0; }
+
+int grp_set_guess_model(grp_ctx* c, const float* weights, int n_weights, const float* box, int ptr_is_device)
+{
+  if (!c || !weights || !box || n_weights != MLP_NPARAM) return GRP_E_INVALID_ARG;
+  CK(cudaSetDevice(c->p.device));
+  if (!c->mlp) CK(cudaMalloc((void**)&c->mlp, sizeof(float) * MLP_NPARAM));
+  if (!c->mlp_norm) CK(cudaMalloc((void**)&c->mlp_norm, sizeof(float) * 12));
+  const cudaMemcpyKind k = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(c->mlp, weights, sizeof(float) * MLP_NPARAM, k, c->stream));
+  CK(cudaMemcpyAsync(c->mlp_norm, box, sizeof(float) * 12, k, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return GRP_OK;
+}
+
+int grp_set_harvest(grp_ctx* c, float* records, unsigned long long* count, long long capacity, int log2_stride)
+{
+  if (!c || log2_stride < 0 || log2_stride > 30) return GRP_E_INVALID_ARG;
+  if (records && (!count || capacity < 1)) return GRP_E_INVALID_ARG;
+  c->harvest = records;
+  c->harvest_count = records ? count : nullptr;
+  c->harvest_cap = records ? capacity : 0;
+  c->harvest_log2_stride = log2_stride;
+  return GRP_OK;
+}
 
 int grp_set_kernel_timing(grp_ctx* c, int enable)
 {

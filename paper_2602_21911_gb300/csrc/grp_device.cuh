@@ -31,6 +31,10 @@ struct Phys {
   int guess;  // 0 PVRS, 1 TRRS, 2 learned
   // gamma-dependent constants, computed once on the host (make_phys)
   double gm1, i_gm1, c2_gm1, c2_gp1, gm1_gp1, gm1_2g, gp1_2g, c2g_gm1, i_g, sqrt_c2_gp1;
+  // learned Newton guess: FP32 weights (MLP_NPARAM) and input box lo[6], hi[6]
+  const float* mlp_w;
+  const float* mlp_box;
+  int features;          // compute the network features (learned guess or harvest)
 };
 
 inline Phys make_phys(double lambda, double gamma, double rtol, int max_iter, int guess)
@@ -48,6 +52,9 @@ inline Phys make_phys(double lambda, double gamma, double rtol, int max_iter, in
   p.c2g_gm1 = 2.0 * g / (g - 1.0);
   p.i_g = 1.0 / g;
   p.sqrt_c2_gp1 = sqrt(2.0 / (g + 1.0));
+  p.mlp_w = nullptr;
+  p.mlp_box = nullptr;
+  p.features = 0;
   return p;
 }
 
@@ -366,17 +373,117 @@ static GRP_HD Prim sample_vacuum_zero(const Phys& ph, const Side& L, const Side&
   return Prim{0.0, 0.0, 0.0};
 }
 
+// ---------------------------------------------------------------------------
+// Learned Newton initial guess (FP32): a 6 -> 64 -> 64 -> 1 tanh network on
+// features invariant under the scaling and Galilean symmetries of the Riemann
+// problem, predicting y = ln(p*/pbar) with pbar = sqrt(pL pR).  Used only for
+// non-trivial data; PVRS stays the fallback.
+// Parameter layout: W1[6][64], b1[64], W2[64][64], b2[64], w3[64], b3.
+// ---------------------------------------------------------------------------
+constexpr int MLP_NIN = 6, MLP_NH = 64;
+constexpr int MLP_NPARAM = MLP_NIN * MLP_NH + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NH + 1;
+constexpr int MLP_GUESS_MAX_ITER = 8;     // Newton from the learned guess gives up after this
+constexpr float MLP_GATE = 0.05f;         // |ln(pL/pR)| or |du|/cbar above this: non-trivial data
+constexpr float MLP_YMAX = 18.420681f;    // |ln(p*/pbar)| <= ln 1e8
+
+GRP_HD __forceinline__ float fast_tanh(float x)
+{
+#ifdef __CUDA_ARCH__
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+#else
+  return tanhf(x);
+#endif
+}
+
+// Features x[6] and pbar; returns false for trivial data (no guess needed).
+GRP_HD __forceinline__ bool mlp_features(const Phys& ph, const Side& L, const Side& R, float x[6], double& pbar)
+{
+  const float lp = logf((float)(L.p * R.ip));
+  const float lr = logf((float)(L.r * R.ir));
+  pbar = sqrt(L.p * R.p);
+  const double cbar = sqrt(ph.gamma * pbar * sqrt(L.ir * R.ir));
+  const float du = (float)((R.u - L.u) / cbar);
+  x[0] = 0.5f * lr; x[1] = -0.5f * lr;
+  x[2] = 0.5f * lp; x[3] = -0.5f * lp;
+  x[4] = -0.5f * du; x[5] = 0.5f * du;
+  return fabsf(lp) > MLP_GATE || fabsf(du) > MLP_GATE;
+}
+
+GRP_HD __forceinline__ float mlp_eval(const float* __restrict__ w, const float x[6])
+{
+  const float* W1 = w;
+  const float* b1 = W1 + MLP_NIN * MLP_NH;
+  const float* W2 = b1 + MLP_NH;
+  const float* b2 = W2 + MLP_NH * MLP_NH;
+  const float* w3 = b2 + MLP_NH;
+  const float b3 = w3[MLP_NH];
+  float h1[MLP_NH];
+#pragma unroll
+  for (int j = 0; j < MLP_NH; ++j) {
+    float z = b1[j];
+#pragma unroll
+    for (int i = 0; i < MLP_NIN; ++i) z = fmaf(x[i], W1[i * MLP_NH + j], z);
+    h1[j] = fast_tanh(z);
+  }
+  float y = b3;
+#pragma unroll 4
+  for (int k = 0; k < MLP_NH; ++k) {
+    float z = b2[k];
+#pragma unroll
+    for (int j = 0; j < MLP_NH; ++j) z = fmaf(h1[j], W2[j * MLP_NH + k], z);
+    y = fmaf(fast_tanh(z), w3[k], y);
+  }
+  return y;
+}
+
+struct RSInfo {
+  double ps = 0.0, pbar = 0.0;   // star pressure; pbar of the features
+  float x[6];                    // features (valid when has_x)
+  bool has_x = false;
+  int guess = 0;                 // 0 not tried, 1 learned guess used, 2 learned guess rejected
+};
+
 // Godunov state at x/t = 0 of conserved data QL | QR, as conserved Q and
 // primitive W.  allow_vacuum: vacuum data are sampled and ST_VACUUM returned
-// with Q valid.
+// with Q valid.  With a learned model (ph.guess == 2) non-trivial data start
+// Newton from the network's prediction; an input outside the training box, a
+// prediction out of range or not finite, or no convergence within
+// MLP_GUESS_MAX_ITER iterations falls back to PVRS (iterations add up).
 template <bool G75>
-static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double QR[3], double p0,
-                                bool allow_vacuum, double Q[3], Prim& W, int& iters)
+static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double QR[3], bool allow_vacuum,
+                                double Q[3], Prim& W, int& iters, RSInfo* info = nullptr)
 {
   const Side L = make_side(ph, QL);
   const Side R = make_side(ph, QR);
   double ps = 0.0, us = 0.0;
-  const int st = star_pressure<G75>(ph, L, R, p0, ps, us, iters);
+  int st = -1;
+  iters = 0;
+  if (ph.features && info) {
+    info->has_x = mlp_features(ph, L, R, info->x, info->pbar);
+    if (ph.guess == 2 && ph.mlp_w && info->has_x) {
+      bool inbox = true;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) inbox = inbox && info->x[i] >= ph.mlp_box[i] && info->x[i] <= ph.mlp_box[6 + i];
+      const float y = inbox ? mlp_eval(ph.mlp_w, info->x) : 0.0f;
+      info->guess = 2;
+      if (inbox && y == y && fabsf(y) <= MLP_YMAX) {
+        Phys pg = ph;
+        pg.max_iter = ph.max_iter < MLP_GUESS_MAX_ITER ? ph.max_iter : MLP_GUESS_MAX_ITER;
+        st = star_pressure<G75>(pg, L, R, info->pbar * exp((double)y), ps, us, iters);
+        if (st == ST_OK) info->guess = 1;
+      }
+    }
+  }
+  if (st != ST_OK && st != ST_VACUUM) {
+    int it2 = 0;
+    Phys pv = ph;
+    pv.guess = ph.guess == 2 ? 0 : ph.guess;       // classical guess (PVRS) as the fallback
+    st = star_pressure<G75>(pv, L, R, 0.0, ps, us, it2);
+    iters += it2;
+  }
+  if (info) info->ps = ps;
   if (st == ST_VACUUM && allow_vacuum) {
     W = sample_vacuum_zero<G75>(ph, L, R);
     to_cons(ph, W, Q);
@@ -565,14 +672,14 @@ GRP_HD __forceinline__ void grp_adv(double lam, double nu, const double tL[M + 1
 template <int M, bool G75>
 GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[3][M + 1],
                                      const double tR[3][M + 1], double F[3], double gnew[3], int& iters,
-                                     bool& truncated)
+                                     bool& truncated, RSInfo* info = nullptr)
 {
   const double g = ph.gamma;
   const double QL[3] = {tL[0][0], tL[1][0], tL[2][0]}, QR[3] = {tR[0][0], tR[1][0], tR[2][0]};
   double Q0[3];
   Prim W0;
   truncated = false;
-  const int st = riemann_state<G75>(ph, QL, QR, 0.0, false, Q0, W0, iters);
+  const int st = riemann_state<G75>(ph, QL, QR, false, Q0, W0, iters, info);
   if (st != ST_OK) return st;
   using T = Tri<M>;
   double rho[T::N], m[T::N], E[T::N];

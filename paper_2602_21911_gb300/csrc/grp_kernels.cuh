@@ -52,9 +52,11 @@ struct StepArgs {
   int* fail;                         // [D] non-zero: solver failure code this step
   int* any_bad;                      // [MAX_REPAIR+1] any domain troubled after pass p
   unsigned long long* stats;         // [D][NSTATS]
-  // learned guess (FP32 network), may be null
-  const float* mlp;                  // packed weights
-  const float* mlp_norm;             // input / output normalisation
+  // harvest of (features, ln(p*/pbar), iterations) records, may be null
+  float* harvest;                    // [harvest_cap][8]
+  unsigned long long* harvest_count; // records offered (may exceed the capacity)
+  long long harvest_cap;
+  int harvest_log2_stride;           // keep one offered interface in 2^k
 };
 
 // ------------------------------------------------------------------ helpers
@@ -199,7 +201,7 @@ static __device__ int first_order(const StepArgs& a, long long c0, int N, int bc
 #pragma unroll
   for (int c = 0; c < 3; ++c) { QL[c] = a.avg[c * a.ncell + c0 + cl]; QR[c] = a.avg[c * a.ncell + c0 + cr]; }
   Prim W;
-  const int st = riemann_state<G75>(a.ph, QL, QR, 0.0, true, Q0, W, iters);
+  const int st = riemann_state<G75>(a.ph, QL, QR, true, Q0, W, iters);
   if (st != ST_OK && st != ST_VACUUM) return st;
   if (Q0[0] > 0.0) euler_flux(a.ph.gamma, Q0[0], Q0[1], Q0[2], F);
   else F[0] = F[1] = F[2] = 0.0;
@@ -208,7 +210,7 @@ static __device__ int first_order(const StepArgs& a, long long c0, int N, int bc
 
 // ------------------------------------------------------------------ k_flux
 template <int SYS, int M, bool G75>
-__device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d, unsigned st[6])
+__device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d, unsigned st[8])
 {
   const long long i0 = a.if_off[d], c0 = a.cell_off[d];
   const int j = (int)(gj - i0);
@@ -267,9 +269,27 @@ __device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d,
   } else {
     int iters = 0;
     bool trunc = false;
-    int rs_st = grp_euler<M, G75>(a.ph, nu, tL, tR, F, gnew, iters, trunc);
+    RSInfo info;
+    int rs_st = grp_euler<M, G75>(a.ph, nu, tL, tR, F, gnew, iters, trunc, &info);
     st[2] = 1;
     st[3] = trunc ? 1u : 0u;
+    st[6] = info.guess == 1 ? 1u : 0u;
+    st[7] = info.guess == 2 ? 1u : 0u;
+    if (a.harvest && info.has_x && rs_st == ST_OK) {
+      // keep one non-trivial interface in 2^k, by a hash of (interface, step)
+      unsigned h = (unsigned)gj * 2654435761u ^ ((unsigned)a.nstep[d] * 2246822519u);
+      h ^= h >> 15; h *= 2654435761u; h ^= h >> 13;
+      if ((h & ((1u << a.harvest_log2_stride) - 1u)) == 0u) {
+        const unsigned long long k = atomicAdd(a.harvest_count, 1ull);
+        if ((long long)k < a.harvest_cap) {
+          float* r = a.harvest + 8 * k;
+#pragma unroll
+          for (int i = 0; i < 6; ++i) r[i] = info.x[i];
+          r[6] = (float)log(info.ps / info.pbar);
+          r[7] = (float)iters;
+        }
+      }
+    }
     if (rs_st != ST_OK) {
       // no solution of the traces' Riemann problem: first-order flux here
       int it2 = 0;
@@ -296,8 +316,9 @@ template <int SYS, int M, bool G75>
 __global__ void __launch_bounds__(128) k_flux(StepArgs a)
 {
   const long long gj = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  // st: newton sum, newton max, RS calls, truncated, first order, recon fallback
-  unsigned st[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+  // st: newton sum, newton max, RS calls, truncated, first order, recon fallback,
+  //     learned guess used, learned guess rejected
+  unsigned st[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
   int d = -1;
   if (gj < a.nif) {
     d = a.if_dom[gj];
@@ -311,6 +332,10 @@ __global__ void __launch_bounds__(128) k_flux(StepArgs a)
     warp_stat_add(a.stats, d, S_FLUX_FB, st[3]);
     warp_stat_add(a.stats, d, S_LOW, st[4]);
     warp_stat_add(a.stats, d, S_RECON_FB, st[5]);
+    if (a.ph.guess == 2) {
+      warp_stat_add(a.stats, d, S_GUESS_USED, st[6]);
+      warp_stat_add(a.stats, d, S_GUESS_REJ, st[7]);
+    }
   }
 }
 
@@ -495,7 +520,7 @@ __global__ void __launch_bounds__(256, 2) k_batch(StepArgs a, const int* __restr
     __syncthreads();
     for (long long base = ib; base < ie; base += bt) {
       const long long gj = base + tid;
-      unsigned st[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+      unsigned st[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
       int d = -1;
       if (gj < ie) {
         d = a.if_dom[gj];
@@ -509,6 +534,10 @@ __global__ void __launch_bounds__(256, 2) k_batch(StepArgs a, const int* __restr
         warp_stat_add(w.stats, d, S_FLUX_FB, st[3]);
         warp_stat_add(w.stats, d, S_LOW, st[4]);
         warp_stat_add(w.stats, d, S_RECON_FB, st[5]);
+        if (w.ph.guess == 2) {
+          warp_stat_add(w.stats, d, S_GUESS_USED, st[6]);
+          warp_stat_add(w.stats, d, S_GUESS_REJ, st[7]);
+        }
       }
     }
     __syncthreads();
@@ -613,8 +642,8 @@ static __global__ void k_init_iface(int sys, Phys ph, long long nif, const doubl
   Phys p2 = ph;
   p2.guess = 0;
   Prim W;
-  const int st = ph.gamma == 1.4 ? riemann_state<true>(p2, QL, QR, 0.0, true, Q, W, it)
-                                 : riemann_state<false>(p2, QL, QR, 0.0, true, Q, W, it);
+  const int st = ph.gamma == 1.4 ? riemann_state<true>(p2, QL, QR, true, Q, W, it)
+                                 : riemann_state<false>(p2, QL, QR, true, Q, W, it);
   if (st != ST_OK && st != ST_VACUUM) { Q[0] = QL[0]; Q[1] = QL[1]; Q[2] = QL[2]; }
   ifc[j] = Q[0]; ifc[nif + j] = Q[1]; ifc[2 * nif + j] = Q[2];
 }

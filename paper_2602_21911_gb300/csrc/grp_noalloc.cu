@@ -135,7 +135,7 @@ extern "C" int grp_step_noalloc(int system, double lambda, double gamma, int M, 
   a.smax_bits = &w->smax_bits;
   a.bad = w->bad; a.inad = &w->inad; a.fail = &w->fail; a.any_bad = w->any_bad;
   a.stats = w->stats;
-  a.mlp = nullptr; a.mlp_norm = nullptr;
+  a.harvest = nullptr; a.harvest_count = nullptr; a.harvest_cap = 0; a.harvest_log2_stride = 0;
 
   // the flat step sequence of grp_step
   const bool euler = system == GRP_EULER_IDEAL;

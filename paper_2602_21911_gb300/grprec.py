@@ -73,6 +73,12 @@ def load(build_if_missing=True):
                                    ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp]
+    L.grp_set_guess_model.argtypes = [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int]
+    L.grp_set_harvest.argtypes = [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_int]
+    L.grp_mlp_forward.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp]
+    L.grp_mlp_loss_grad.argtypes = [_vp, _vp, _vp, ctypes.c_longlong, _vp, _vp, _vp, _vp]
+    L.grp_mlp_adam.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_float, ctypes.c_float, _vp]
     L.grp_destroy.argtypes = [_vp]
     L.grp_destroy.restype = None
     L.grp_status_string.argtypes = [ctypes.c_int]
@@ -89,6 +95,35 @@ def grp_probe_fp64_peak(device=0):
 
 
 GRP_NOALLOC_MAX_CELLS = 65536
+GRP_MLP_NPARAM = 4673
+
+
+def mlp_work_floats(n):
+    return int(n) * 257
+
+
+def _dev(x, what):
+    p, dev = _ptr(x)
+    if not dev:
+        raise GrpError("%s must be a device tensor" % what)
+    return p
+
+
+def grp_mlp_forward(weights, x, y, stream=None):
+    _check(load().grp_mlp_forward(_dev(weights, "weights"), _dev(x, "x"), int(x.shape[0]), _dev(y, "y"),
+                                  stream), "grp_mlp_forward")
+
+
+def grp_mlp_loss_grad(weights, x, target, grad, loss, work, stream=None):
+    _check(load().grp_mlp_loss_grad(_dev(weights, "weights"), _dev(x, "x"), _dev(target, "target"),
+                                    int(x.shape[0]), _dev(grad, "grad"), _dev(loss, "loss"),
+                                    _dev(work, "work"), stream), "grp_mlp_loss_grad")
+
+
+def grp_mlp_adam(weights, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().grp_mlp_adam(_dev(weights, "weights"), _dev(grad, "grad"), _dev(m, "m"), _dev(v, "v"),
+                               int(step), float(lr), float(beta1), float(beta2), float(eps), stream),
+           "grp_mlp_adam")
 
 
 def grp_step_noalloc(prob, avg_in, iface_in, avg_out, iface_out, t, t_end=float("inf"), stream=None):
@@ -241,6 +276,20 @@ class Solver:
         _check(self.L.grp_get_launch(self.h, *[ctypes.byref(x) for x in v]), "grp_get_launch")
         return dict(zip(("form", "threads", "cells_per_block", "steps_per_launch", "blocks"),
                         [x.value for x in v]))
+
+    def set_guess_model(self, weights, box):
+        w, dw = _ptr(weights)
+        b, db = _ptr(box)
+        if dw != db:
+            raise GrpError("weights and box must live on the same side")
+        _check(self.L.grp_set_guess_model(self.h, w, GRP_MLP_NPARAM, b, dw), "grp_set_guess_model")
+
+    def set_harvest(self, records=None, count=None, log2_stride=0):
+        if records is None:
+            _check(self.L.grp_set_harvest(self.h, None, None, 0, 0), "grp_set_harvest")
+            return
+        _check(self.L.grp_set_harvest(self.h, _dev(records, "records"), _dev(count, "count"),
+                                      int(records.shape[0]), int(log2_stride)), "grp_set_harvest")
 
     def launch_count(self):
         return int(self.L.grp_launch_count(self.h))

@@ -1,0 +1,139 @@
+"""The learned Newton guess on the GPU: training kernels against the FP64
+reference network (forward, loss, gradient, Adam), harvesting from the scheme,
+training, and the guess inside the flux kernel (p* unchanged, fallbacks,
+iterations saved)."""
+import numpy as np
+import pytest
+
+from oracle import mlp as R
+from paper_2602_21911_gb300 import inputs as I
+
+from parity import DISC_TOL, check_parity, rel_diff
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def dev(a, dtype=torch.float32):
+    return torch.tensor(np.asarray(a), dtype=dtype, device="cuda").contiguous()
+
+
+def test_forward_loss_and_gradient_match_fp64_reference():
+    from paper_2602_21911_gb300 import grprec
+    rng = np.random.default_rng(5)
+    theta = R.init(seed=2) + 0.05 * rng.normal(size=R.NPARAM)
+    theta32 = theta.astype(np.float32).astype(np.float64)      # the kernels see FP32 weights
+    n = 3000
+    x = rng.normal(size=(n, 6)).astype(np.float32)
+    t = rng.normal(size=n).astype(np.float32)
+    w = dev(theta32)
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    grprec.grp_mlp_forward(w, dev(x), y)
+    y_ref, _ = R.forward(theta32, x.astype(np.float64))
+    assert np.abs(y.cpu().numpy() - y_ref).max() < 1e-4 * max(1.0, np.abs(y_ref).max())
+    grad = torch.zeros(R.NPARAM, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    work = torch.empty(grprec.mlp_work_floats(n), dtype=torch.float32, device="cuda")
+    grprec.grp_mlp_loss_grad(w, dev(x), dev(t), grad, loss, work)
+    l_ref, g_ref = R.loss_grad(theta32, x.astype(np.float64), t.astype(np.float64))
+    assert loss.item() == pytest.approx(l_ref, rel=1e-4)
+    g = grad.cpu().numpy().astype(np.float64)
+    # FP32 accumulation over 3000 samples: normwise agreement
+    assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
+    for name_lo, name_hi in ((0, 384), (384, 448), (448, 4544), (4544, 4608), (4608, 4672), (4672, 4673)):
+        blk, ref = g[name_lo:name_hi], g_ref[name_lo:name_hi]
+        assert np.linalg.norm(blk - ref) <= 1e-3 * max(np.linalg.norm(ref), 1e-6)
+
+
+def test_adam_matches_reference():
+    from paper_2602_21911_gb300 import grprec
+    rng = np.random.default_rng(6)
+    theta = rng.normal(size=R.NPARAM)
+    m = np.zeros(R.NPARAM)
+    v = np.zeros(R.NPARAM)
+    wt, mt, vt = dev(theta), dev(m), dev(v)
+    for step in (1, 2, 3):
+        g = rng.normal(size=R.NPARAM)
+        gt = dev(g)
+        grprec.grp_mlp_adam(wt, gt, mt, vt, step, lr=1e-2)
+        theta, m, v = R.adam_step(theta, g.astype(np.float32).astype(np.float64), m, v, step, lr=1e-2)
+    assert np.abs(wt.cpu().numpy() - theta).max() < 1e-5
+
+
+def _batch_subset(k=150, step=311):
+    return I.batched(domains=np.arange(0, 65536, step)[:k])
+
+
+@pytest.fixture(scope="module")
+def trained():
+    from paper_2602_21911_gb300 import learned
+    runs = []
+    prob, avg, lm, lp = I.batched(65536, seed=2603, domains=np.arange(0, 65536, 16))
+    runs.append((prob, avg, lm, lp, 120))
+    prob, avg, lm, lp = I.sod(4096)
+    runs.append((prob, avg, lm, lp, 300))
+    rec = learned.harvest(runs, capacity=400_000, log2_stride=1)
+    assert rec.shape[0] > 20_000
+    w, box, info = learned.fit_from_records(rec, epochs=12, batch=4096)
+    return w, box, info, rec
+
+
+def test_training_learns_the_star_pressure(trained):
+    w, box, info, rec = trained
+    assert info["train_mse"][-1] < 0.2 * info["train_mse"][0]
+    # a useful guess: ln p* to within about 0.1 on held-out harvested data
+    assert info["val_rms"] < 0.1
+
+
+def test_learned_guess_leaves_results_unchanged_and_saves_iterations(trained):
+    from paper_2602_21911_gb300 import grprec
+    w, box, info, rec = trained
+    prob, avg, lm, lp = _batch_subset()
+    out = {}
+    for guess in (grprec.GRP_GUESS_PVRS, grprec.GRP_GUESS_MLP):
+        s = grprec.Solver(dict(prob, guess=guess))
+        if guess == grprec.GRP_GUESS_MLP:
+            s.set_guess_model(w, box)
+        s.set_initial(avg, lm, lp)
+        s.step(80)
+        out[guess] = (s.get_state(), s.get_stats())
+    (a0, g0, t0), (st0, _) = out[grprec.GRP_GUESS_PVRS]
+    (a1, g1, t1), (st1, _) = out[grprec.GRP_GUESS_MLP]
+    assert rel_diff(a1, a0, prob).max() < DISC_TOL
+    used = st1[:, grprec.STAT_GUESS_USED].sum()
+    assert used > 0
+    # Newton iterations of the solves that used the network, against PVRS on the same runs
+    n0 = st0[:, grprec.STAT_NEWTON_SUM].sum()
+    n1 = st1[:, grprec.STAT_NEWTON_SUM].sum()
+    assert n1 < n0
+    # and the oracle (PVRS) agrees with the learned-guess run
+    check_parity(dict(prob, guess=grprec.GRP_GUESS_MLP), avg, lm, lp, 30, DISC_TOL,
+                 solver=_with_model(prob, w, box))
+
+
+def _with_model(prob, w, box):
+    from paper_2602_21911_gb300 import grprec
+    s = grprec.Solver(dict(prob, guess=grprec.GRP_GUESS_MLP))
+    s.set_guess_model(w, box)
+    return s
+
+
+def test_garbage_model_falls_back_to_pvrs():
+    from paper_2602_21911_gb300 import grprec
+    prob, avg, lm, lp = _batch_subset(60)
+    bad = torch.full((R.NPARAM,), float("nan"), dtype=torch.float32, device="cuda")
+    box = torch.tensor([-1e3] * 6 + [1e3] * 6, dtype=torch.float32, device="cuda")
+    s = grprec.Solver(dict(prob, guess=grprec.GRP_GUESS_MLP))
+    s.set_guess_model(bad, box)
+    S, (a, g, t, stats, status), rd = check_parity(prob, avg, lm, lp, 25, DISC_TOL, solver=s)
+    assert stats[:, grprec.STAT_GUESS_USED].sum() == 0
+    assert stats[:, grprec.STAT_GUESS_REJECTED].sum() > 0
+
+
+def test_mlp_mode_needs_a_model():
+    from paper_2602_21911_gb300 import grprec
+    prob, avg, lm, lp = _batch_subset(10)
+    s = grprec.Solver(dict(prob, guess=grprec.GRP_GUESS_MLP))
+    s.set_initial(avg, lm, lp)
+    with pytest.raises(grprec.GrpError, match="model"):
+        s.step(1)
