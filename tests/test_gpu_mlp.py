@@ -68,12 +68,12 @@ def _batch_subset(k=150, step=311):
 def trained():
     from paper_2602_21911_gb300 import learned
     runs = []
-    prob, avg, lm, lp = I.batched(65536, seed=2603, domains=np.arange(0, 65536, 16))
-    runs.append((prob, avg, lm, lp, 120))
+    prob, avg, lm, lp = I.batched(65536, seed=2603, domains=np.arange(0, 65536, 4))
+    runs.append((prob, avg, lm, lp, 200))
     prob, avg, lm, lp = I.sod(4096)
-    runs.append((prob, avg, lm, lp, 300))
-    rec = learned.harvest(runs, capacity=400_000, log2_stride=1)
-    assert rec.shape[0] > 20_000
+    runs.append((prob, avg, lm, lp, 400))
+    rec = learned.harvest(runs, capacity=600_000, log2_stride=0)
+    assert rec.shape[0] > 50_000
     w, box, info = learned.fit_from_records(rec, epochs=12, batch=4096)
     return w, box, info, rec
 
