@@ -203,7 +203,7 @@ int grp_get_launch(const grp_ctx *ctx, int *batched, int *threads, int *cells_pe
  * GRP_STAT_GUESS_USED / GRP_STAT_GUESS_REJECTED record both.  Pointers host or
  * device (ptr_is_device); copied, not kept.  Synchronises.
  *
- * grp_set_harvest: record (6 inputs, ln(p* / pbar), Newton iterations) of one
+ * grp_set_harvest: record (6 inputs, ln(p* / p_PVRS), Newton iterations) of one
  * non-trivial interface in 2^log2_stride, by a hash of (interface, step),
  * into the caller's device buffer records[capacity][8] during later steps;
  * *count (device, caller-zeroed) counts the offered records and may exceed

@@ -246,6 +246,13 @@ GRP_HD __forceinline__ void pressure_fn(const Phys& ph, double p, const Side& K,
   }
 }
 
+// PVRS estimate of the star pressure, floored at 1e-14 max(pL, pR)
+GRP_HD __forceinline__ double pvrs(const Side& L, const Side& R)
+{
+  const double ppv = 0.5 * (L.p + R.p) - 0.125 * (R.u - L.u) * (L.r + R.r) * (L.c + R.c);
+  return fmax(ppv, 1e-14 * fmax(L.p, R.p));
+}
+
 // Returns ST_OK / ST_NO_CONV / ST_VACUUM.  p0 > 0 is used as the start when
 // given (learned guess), otherwise PVRS or TRRS per ph.guess.
 template <bool G75>
@@ -265,8 +272,7 @@ static GRP_HD int star_pressure(const Phys& ph, const Side& L, const Side& R, do
     const double den = L.c * pow(L.p, -z) + R.c * pow(R.p, -z);
     p = pow(num / den, 1.0 / z);
   } else {
-    const double ppv = 0.5 * (L.p + R.p) - 0.125 * du * (L.r + R.r) * (L.c + R.c);
-    p = fmax(ppv, pfloor);
+    p = pvrs(L, R);
   }
   if (!(p > pfloor)) p = pfloor;
   bool conv = false;
@@ -376,8 +382,9 @@ static GRP_HD Prim sample_vacuum_zero(const Phys& ph, const Side& L, const Side&
 // ---------------------------------------------------------------------------
 // Learned Newton initial guess (FP32): a 6 -> 64 -> 64 -> 1 tanh network on
 // features invariant under the scaling and Galilean symmetries of the Riemann
-// problem, predicting y = ln(p*/pbar) with pbar = sqrt(pL pR).  Used only for
-// non-trivial data; PVRS stays the fallback.
+// problem, predicting the correction y = ln(p*/p_PVRS) of the PVRS estimate,
+// so that the guess is p_PVRS e^y.  Used only for non-trivial data; plain
+// PVRS stays the fallback.
 // Parameter layout: W1[6][64], b1[64], W2[64][64], b2[64], w3[64], b3.
 // ---------------------------------------------------------------------------
 constexpr int MLP_NIN = 6, MLP_NH = 64;
@@ -440,6 +447,7 @@ GRP_HD __forceinline__ float mlp_eval(const float* __restrict__ w, const float x
 
 struct RSInfo {
   double ps = 0.0, pbar = 0.0;   // star pressure; pbar of the features
+  double ppv = 0.0;              // PVRS estimate (the base of the learned correction)
   float x[6];                    // features (valid when has_x)
   bool has_x = false;
   int guess = 0;                 // 0 not tried, 1 learned guess used, 2 learned guess rejected
@@ -462,6 +470,7 @@ static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double
   iters = 0;
   if (ph.features && info) {
     info->has_x = mlp_features(ph, L, R, info->x, info->pbar);
+    info->ppv = pvrs(L, R);
     if (ph.guess == 2 && ph.mlp_w && info->has_x) {
       bool inbox = true;
 #pragma unroll
@@ -471,7 +480,7 @@ static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double
       if (inbox && y == y && fabsf(y) <= MLP_YMAX) {
         Phys pg = ph;
         pg.max_iter = ph.max_iter < MLP_GUESS_MAX_ITER ? ph.max_iter : MLP_GUESS_MAX_ITER;
-        st = star_pressure<G75>(pg, L, R, info->pbar * exp((double)y), ps, us, iters);
+        st = star_pressure<G75>(pg, L, R, info->ppv * exp((double)y), ps, us, iters);
         if (st == ST_OK) info->guess = 1;
       }
     }
