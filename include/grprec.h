@@ -186,14 +186,16 @@ int grp_get_launch(const grp_ctx *ctx, int *batched, int *threads, int *cells_pe
 /*
  * Learned Newton initial guess for the star pressure (not in the paper: an
  * FP32 network that replaces the PVRS start of the exact Riemann solver on
- * non-trivial data; the converged p* is unchanged).
+ * strong data; the converged p* is unchanged).
  *
  * Network: 6 -> 64 -> 64 -> 1 with tanh hidden layers.  Inputs, for primitive
  * states (rho,u,p)_L,R with rbar = sqrt(rhoL rhoR), pbar = sqrt(pL pR),
  * cbar = sqrt(gamma pbar / rbar), ubar = (uL+uR)/2:
  *   ln(rhoL/rbar), ln(rhoR/rbar), ln(pL/pbar), ln(pR/pbar), (uL-ubar)/cbar, (uR-ubar)/cbar
- * Output: y = ln(p* / pbar).  Data count as non-trivial when |ln(pL/pR)| > 0.05
- * or |uR-uL|/cbar > 0.05.  Parameters (GRP_MLP_NPARAM floats): W1[6][64],
+ * Output: y = ln(p* / p_TR), the correction of the two-rarefaction estimate
+ * p_TR; the Newton start is p_TR e^y.  The network serves strong data only,
+ * |ln(pL/pR)| > 0.5 or |uR-uL|/cbar > 0.5 (PVRS starts the rest).
+ * Parameters (GRP_MLP_NPARAM floats): W1[6][64],
  * b1[64], W2[64][64], b2[64], w3[64], b3.
  *
  * grp_set_guess_model: load the weights and the input box (12 floats: lo[6],
@@ -203,8 +205,8 @@ int grp_get_launch(const grp_ctx *ctx, int *batched, int *threads, int *cells_pe
  * GRP_STAT_GUESS_USED / GRP_STAT_GUESS_REJECTED record both.  Pointers host or
  * device (ptr_is_device); copied, not kept.  Synchronises.
  *
- * grp_set_harvest: record (6 inputs, ln(p* / p_PVRS), Newton iterations) of one
- * non-trivial interface in 2^log2_stride, by a hash of (interface, step),
+ * grp_set_harvest: record (6 inputs, ln(p* / p_TR), Newton iterations) of one
+ * strong-data interface in 2^log2_stride, by a hash of (interface, step),
  * into the caller's device buffer records[capacity][8] during later steps;
  * *count (device, caller-zeroed) counts the offered records and may exceed
  * capacity (the excess is dropped).  records = NULL stops harvesting.

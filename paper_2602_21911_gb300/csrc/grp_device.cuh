@@ -246,6 +246,22 @@ GRP_HD __forceinline__ void pressure_fn(const Phys& ph, double p, const Side& K,
   }
 }
 
+// Two-rarefaction estimate of the star pressure (exact when both waves are
+// rarefactions); 0 when the data generate vacuum.
+template <bool G75>
+GRP_HD __forceinline__ double trrs(const Phys& ph, const Side& L, const Side& R)
+{
+  const double num = L.c + R.c - 0.5 * ph.gm1 * (R.u - L.u);
+  if (!(num > 0.0)) return 0.0;
+  if (G75) {                                        // z = 1/7: p^-z by a 7th root, ^(1/z) = ^7
+    const double q = num / (L.c * inv_root7(L.p) + R.c * inv_root7(R.p));
+    const double q2 = q * q, q4 = q2 * q2;
+    return q4 * q2 * q;
+  }
+  const double z = ph.gm1_2g;
+  return pow(num / (L.c * pow(L.p, -z) + R.c * pow(R.p, -z)), 1.0 / z);
+}
+
 // PVRS estimate of the star pressure, floored at 1e-14 max(pL, pR)
 GRP_HD __forceinline__ double pvrs(const Side& L, const Side& R)
 {
@@ -382,15 +398,15 @@ static GRP_HD Prim sample_vacuum_zero(const Phys& ph, const Side& L, const Side&
 // ---------------------------------------------------------------------------
 // Learned Newton initial guess (FP32): a 6 -> 64 -> 64 -> 1 tanh network on
 // features invariant under the scaling and Galilean symmetries of the Riemann
-// problem, predicting the correction y = ln(p*/p_PVRS) of the PVRS estimate,
-// so that the guess is p_PVRS e^y.  Used only for non-trivial data; plain
-// PVRS stays the fallback.
+// problem, predicting the correction y = ln(p*/p_TR) of the two-rarefaction
+// estimate, so that the guess is p_TR e^y.  Used only for strong data (where
+// PVRS is poor); PVRS stays the start elsewhere and the fallback.
 // Parameter layout: W1[6][64], b1[64], W2[64][64], b2[64], w3[64], b3.
 // ---------------------------------------------------------------------------
 constexpr int MLP_NIN = 6, MLP_NH = 64;
 constexpr int MLP_NPARAM = MLP_NIN * MLP_NH + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NH + 1;
 constexpr int MLP_GUESS_MAX_ITER = 8;     // Newton from the learned guess gives up after this
-constexpr float MLP_GATE = 0.05f;         // |ln(pL/pR)| or |du|/cbar above this: non-trivial data
+constexpr float MLP_GATE = 0.5f;          // |ln(pL/pR)| or |du|/cbar above this: strong data
 constexpr float MLP_YMAX = 18.420681f;    // |ln(p*/pbar)| <= ln 1e8
 
 GRP_HD __forceinline__ float fast_tanh(float x)
@@ -447,7 +463,7 @@ GRP_HD __forceinline__ float mlp_eval(const float* __restrict__ w, const float x
 
 struct RSInfo {
   double ps = 0.0, pbar = 0.0;   // star pressure; pbar of the features
-  double ppv = 0.0;              // PVRS estimate (the base of the learned correction)
+  double base = 0.0;             // two-rarefaction estimate (the base of the learned correction)
   float x[6];                    // features (valid when has_x)
   bool has_x = false;
   int guess = 0;                 // 0 not tried, 1 learned guess used, 2 learned guess rejected
@@ -470,7 +486,10 @@ static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double
   iters = 0;
   if (ph.features && info) {
     info->has_x = mlp_features(ph, L, R, info->x, info->pbar);
-    info->ppv = pvrs(L, R);
+    if (info->has_x) {
+      info->base = trrs<G75>(ph, L, R);
+      info->has_x = info->base > 0.0 && isfinite(info->base);
+    }
     if (ph.guess == 2 && ph.mlp_w && info->has_x) {
       bool inbox = true;
 #pragma unroll
@@ -480,7 +499,7 @@ static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double
       if (inbox && y == y && fabsf(y) <= MLP_YMAX) {
         Phys pg = ph;
         pg.max_iter = ph.max_iter < MLP_GUESS_MAX_ITER ? ph.max_iter : MLP_GUESS_MAX_ITER;
-        st = star_pressure<G75>(pg, L, R, info->ppv * exp((double)y), ps, us, iters);
+        st = star_pressure<G75>(pg, L, R, info->base * exp((double)y), ps, us, iters);
         if (st == ST_OK) info->guess = 1;
       }
     }

@@ -1,8 +1,8 @@
 """Learned Newton initial guess: harvest, training and loading (marshalling only).
 
 1. harvest: run the scheme with grp_set_harvest on; the flux kernel records the
-   network inputs and the converged FP64 correction ln(p*/p_PVRS) of the
-   non-trivial interfaces.
+   network inputs and the converged FP64 correction ln(p*/p_TR) of the
+   two-rarefaction estimate at the strong-data interfaces.
 2. train: mini-batch Adam on the mean-squared error, every batch through the
    library's FP32 kernels grp_mlp_loss_grad and grp_mlp_adam.
 3. load: grp_set_guess_model with the weights and the input box of the data.
@@ -20,7 +20,7 @@ NPARAM = grprec.GRP_MLP_NPARAM
 
 def harvest(runs, capacity=2_000_000, log2_stride=2, device=0):
     """runs: iterable of (prob, avg, lim_minus, lim_plus, n_steps).  Returns a
-    float32 device tensor [n, 8]: 6 inputs, ln(p*/p_PVRS), Newton iterations."""
+    float32 device tensor [n, 8]: 6 inputs, ln(p*/p_TR), Newton iterations."""
     import torch
     dev = torch.device("cuda", device)
     out = []
@@ -112,7 +112,7 @@ def predict(w, x):
 
 def fit_from_records(records, val_fraction=0.1, seed=0, **kw):
     """Split harvested records, train, and report the validation RMS error of
-    ln(p*/p_PVRS) and the input box."""
+    ln(p*/p_TR) and the input box."""
     import torch
     n = records.shape[0]
     gen = torch.Generator(device=records.device).manual_seed(seed + 1)

@@ -68,13 +68,13 @@ def _batch_subset(k=150, step=311):
 def trained():
     from paper_2602_21911_gb300 import learned
     runs = []
-    prob, avg, lm, lp = I.batched(65536, seed=2603, domains=np.arange(0, 65536, 4))
-    runs.append((prob, avg, lm, lp, 200))
+    prob, avg, lm, lp = I.batched(65536, seed=2603, domains=np.arange(0, 65536, 2))
+    runs.append((prob, avg, lm, lp, 300))
     prob, avg, lm, lp = I.sod(4096)
     runs.append((prob, avg, lm, lp, 400))
     rec = learned.harvest(runs, capacity=600_000, log2_stride=0)
-    assert rec.shape[0] > 50_000
-    w, box, info = learned.fit_from_records(rec, epochs=40, batch=4096)
+    assert rec.shape[0] > 10_000
+    w, box, info = learned.fit_from_records(rec, epochs=80, batch=2048)
     return w, box, info, rec
 
 
