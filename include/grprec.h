@@ -184,6 +184,19 @@ int grp_get_launch(const grp_ctx *ctx, int *batched, int *threads, int *cells_pe
                    int *steps_per_launch, int *blocks);
 
 /*
+ * CUDA graphs.  grp_step captures the launch sequence of steps_per_graph
+ * consecutive steps (whole launches of the current form) into a CUDA graph
+ * once and replays it for every further run of that many steps; shorter
+ * remainders are launched directly.  A graph is kept per start buffer, t_end
+ * and launch state, and dropped by grp_set_launch, grp_set_graph,
+ * grp_set_guess_model, grp_set_harvest and a change of grp_set_kernel_timing.
+ * steps_per_graph in [0, 1024]; 0 launches every kernel directly; a value that
+ * is not a multiple of steps_per_launch in the FUSED form also launches
+ * directly.  Default 16.  Synchronises the stream.
+ */
+int grp_set_graph(grp_ctx *ctx, int steps_per_graph);
+
+/*
  * Learned Newton initial guess for the star pressure (not in the paper: an
  * FP32 network that replaces the PVRS start of the exact Riemann solver on
  * strong data; the converged p* is unchanged).
@@ -230,6 +243,25 @@ int grp_mlp_loss_grad(const float *weights, const float *x, const float *target,
                       float *grad, float *loss, float *work, void *stream);
 int grp_mlp_adam(float *weights, const float *grad, float *m, float *v, int step, float lr,
                  float beta1, float beta2, float eps, void *stream);
+
+/*
+ * Leading-term Riemann problems in bulk: the exact ideal-gas solver of the
+ * flux kernel (Toro-Titarev GRP, Section 2.2: Newton on the star pressure to a
+ * relative change below newton_rtol, then one more iteration) applied to n
+ * independent pairs of conserved states, from the start `guess` (GRP_GUESS_*;
+ * GRP_GUESS_MLP needs `weights` and `box` as for grp_set_guess_model, device
+ * pointers, and serves strong data only, the rest starting from PVRS).
+ * QL, QR: device, 3 planes of n doubles (rho, m, E).  Out (device): ps[n] the
+ * star pressure (0 unless status is 0), iters[n] the Newton iterations of all
+ * attempts, status[n] 0 ok / 1 no convergence within newton_max_iter /
+ * 2 vacuum data, used[n] (may be NULL) 1 where the learned guess started the
+ * converged run.  Ordered on `stream`.  Errors: GRP_E_INVALID_ARG,
+ * GRP_E_NO_MODEL, GRP_E_CUDA.
+ */
+int grp_riemann_batch(double gamma, int guess, double newton_rtol, int newton_max_iter,
+                      const float *weights, const float *box, long long n, const double *QL,
+                      const double *QR, double *ps, int *iters, int *status, unsigned char *used,
+                      void *stream);
 
 /* Number of kernel launches this context has enqueued since grp_create. */
 long long grp_launch_count(const grp_ctx *ctx);

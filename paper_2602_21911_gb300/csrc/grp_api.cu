@@ -52,6 +52,21 @@ struct grp_ctx {
   // optional CUDA-event timing of the flux kernel launches
   bool timing = false;
   std::vector<cudaEvent_t> ev_free, ev_pending;   // pending: start/stop pairs
+  // CUDA graphs of graph_steps steps, replayed by grp_step (grp_set_graph)
+  struct Graph {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    int start_cur = 0;
+    bool smax_ready = false;
+    unsigned long long t_end_bits = 0;
+    int steps = 0;
+    long long launches = 0;
+    std::vector<cudaGraphNode_t> ev_nodes;   // event-record nodes of the flux timing, in pair order
+  };
+  int graph_steps = 16;
+  bool capturing = false;
+  std::vector<Graph> graphs;
+  cudaStream_t cap_stream = nullptr;
 };
 
 namespace {
@@ -76,8 +91,20 @@ cudaError_t dalloc(T** p, size_t n)
   return cudaMalloc((void**)p, (n ? n : 1) * sizeof(T));
 }
 
+void drop_graphs(grp_ctx* c)
+{
+  for (auto& g : c->graphs) {
+    if (g.x) cudaGraphExecDestroy(g.x);
+    if (g.g) cudaGraphDestroy(g.g);
+  }
+  c->graphs.clear();
+}
+
 void free_all(grp_ctx* c)
 {
+  drop_graphs(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  c->cap_stream = nullptr;
   for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_pending) cudaEventDestroy(e);
   c->ev_free.clear();
@@ -137,6 +164,14 @@ StepArgs make_args(const grp_ctx* c, double t_end)
 }
 
 unsigned blocks(long long n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }
+
+// Timing event on the context's stream; under graph capture an event-record
+// node of the graph (an ordinary record would only mark a capture dependency).
+cudaError_t record(const grp_ctx* c, cudaEvent_t e)
+{
+  return c->capturing ? cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal)
+                      : cudaEventRecord(e, c->stream);
+}
 
 cudaError_t launch_flux(const StepArgs& a, cudaStream_t s)
 {
@@ -204,14 +239,14 @@ int enqueue_batch(grp_ctx* c, int nsteps, double t_end)
       if (!c->ev_free.empty()) { *e = c->ev_free.back(); c->ev_free.pop_back(); }
       else CK(cudaEventCreate(e));
     }
-    CK(cudaEventRecord(e0, c->stream));
+    CK(record(c, e0));
   }
   const BatchLaunch L{a, c->grp, (unsigned)c->n_blocks, (unsigned)c->threads, nsteps, c->cur,
                       c->avg[0], c->avg[1], c->ifc[0], c->ifc[1]};
   CK(launch_batch(L, c->stream));
   c->launches++;
   if (c->timing) {
-    CK(cudaEventRecord(e1, c->stream));
+    CK(record(c, e1));
     c->ev_pending.push_back(e0);
     c->ev_pending.push_back(e1);
   }
@@ -236,12 +271,12 @@ int enqueue_split(grp_ctx* c, double t_end)
       if (!c->ev_free.empty()) { *e = c->ev_free.back(); c->ev_free.pop_back(); }
       else CK(cudaEventCreate(e));
     }
-    CK(cudaEventRecord(e0, s));
+    CK(record(c, e0));
   }
   CK(launch_flux(a, s));
   c->launches++;
   if (c->timing) {
-    CK(cudaEventRecord(e1, s));
+    CK(record(c, e1));
     c->ev_pending.push_back(e0);
     c->ev_pending.push_back(e1);
   }
@@ -269,12 +304,12 @@ int enqueue_step(grp_ctx* c, double t_end)
       if (!c->ev_free.empty()) { *e = c->ev_free.back(); c->ev_free.pop_back(); }
       else CK(cudaEventCreate(e));
     }
-    CK(cudaEventRecord(e0, s));
+    CK(record(c, e0));
   }
   CK(launch_flux(a, s));
   c->launches++;
   if (c->timing) {
-    CK(cudaEventRecord(e1, s));
+    CK(record(c, e1));
     c->ev_pending.push_back(e0);
     c->ev_pending.push_back(e1);
   }
@@ -470,6 +505,7 @@ int grp_set_launch(grp_ctx* c, int mode, int threads, int cells_per_block, int s
     return GRP_E_INVALID_ARG;
   CK(cudaSetDevice(c->p.device));
   CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+  drop_graphs(c);
   const bool regroup = cells_per_block != c->cells_per_block;
   c->mode = mode;
   c->threads = threads;
@@ -502,6 +538,130 @@ int grp_get_launch(const grp_ctx* c, int* batched, int* threads, int* cells_per_
 }  // extern "C"
 
 namespace {
+// steps one launch unit of the current form advances
+int unit_steps(const grp_ctx* c) { return launch_form(c) == GRP_LAUNCH_FUSED ? c->steps_per_launch : 1; }
+
+int enqueue_unit(grp_ctx* c, int k, double t_end)
+{
+  const int form = launch_form(c);
+  if (form == GRP_LAUNCH_FUSED) return enqueue_batch(c, k, t_end);
+  if (form == GRP_LAUNCH_SPLIT) return enqueue_split(c, t_end);
+  return enqueue_step(c, t_end);
+}
+
+unsigned long long bits_of(double x)
+{
+  unsigned long long b;
+  memcpy(&b, &x, sizeof b);
+  return b;
+}
+
+// Captures `steps` steps (whole launch units) starting from the context's
+// current buffer parity into a CUDA graph.  The kernels' arguments (buffer
+// pointers, t_end) are fixed in the graph, so a graph serves one start parity,
+// one split-form S_max state and one t_end.
+int capture_graph(grp_ctx* c, int steps, double t_end, grp_ctx::Graph& out)
+{
+  if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  // the domain groups are built (allocation, copy) before capture begins
+  if (launch_form(c) != GRP_LAUNCH_FLAT && !c->grp) {
+    const int rc = build_groups(c);
+    if (rc) return rc;
+  }
+  // timing events are created before capture begins
+  if (c->timing)
+    while (c->ev_free.size() < (size_t)(2 * steps)) {
+      cudaEvent_t e = nullptr;
+      CK(cudaEventCreate(&e));
+      c->ev_free.push_back(e);
+    }
+  out = grp_ctx::Graph();
+  out.start_cur = c->cur;
+  out.smax_ready = c->smax_ready;
+  out.t_end_bits = bits_of(t_end);
+  out.steps = steps;
+  const int cur0 = c->cur;
+  const long long launches0 = c->launches;
+  const size_t ev0 = c->ev_pending.size();
+  const bool smax0 = c->smax_ready;
+  cudaStream_t user = c->stream;
+  CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  c->stream = c->cap_stream;
+  c->capturing = true;
+  int rc = GRP_OK;
+  const int k = unit_steps(c);
+  for (int i = 0; i < steps && rc == GRP_OK; i += k) rc = enqueue_unit(c, k, t_end);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e_end = cudaStreamEndCapture(c->cap_stream, &g);
+  c->stream = user;
+  c->capturing = false;
+  out.launches = c->launches - launches0;
+  // the timing events recorded during capture become nodes of the graph
+  std::vector<cudaEvent_t> evs(c->ev_pending.begin() + ev0, c->ev_pending.end());
+  c->ev_pending.resize(ev0);
+  for (cudaEvent_t e : evs) c->ev_free.push_back(e);
+  c->cur = cur0;
+  c->launches = launches0;
+  c->smax_ready = smax0;
+  if (rc != GRP_OK) { if (g) cudaGraphDestroy(g); return rc; }
+  if (e_end != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e_end, "cudaStreamEndCapture"); }
+  out.g = g;
+  if (!evs.empty()) {
+    size_t nn = 0;
+    CK(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+    out.ev_nodes.assign(evs.size(), nullptr);
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType ty;
+      CK(cudaGraphNodeGetType(nd, &ty));
+      if (ty != cudaGraphNodeTypeEventRecord) continue;
+      cudaEvent_t ev = nullptr;
+      CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+      for (size_t j = 0; j < evs.size(); ++j)
+        if (evs[j] == ev && !out.ev_nodes[j]) { out.ev_nodes[j] = nd; break; }
+    }
+    for (cudaGraphNode_t nd : out.ev_nodes)
+      if (!nd) { cudaGraphDestroy(g); out.g = nullptr; snprintf(g_err, sizeof(g_err), "graph event nodes"); return GRP_E_CUDA; }
+  }
+  const cudaError_t e_inst = cudaGraphInstantiate(&out.x, g, 0);
+  if (e_inst != cudaSuccess) { cudaGraphDestroy(g); out.g = nullptr; return cuda_fail(e_inst, "cudaGraphInstantiate"); }
+  return GRP_OK;
+}
+
+// Replays (capturing first if needed) the graph of c->graph_steps steps.
+int replay_graph(grp_ctx* c, double t_end)
+{
+  const unsigned long long tb = bits_of(t_end);
+  grp_ctx::Graph* G = nullptr;
+  for (auto& g : c->graphs)
+    if (g.start_cur == c->cur && g.smax_ready == c->smax_ready && g.t_end_bits == tb && g.steps == c->graph_steps)
+      G = &g;
+  if (!G) {
+    if (c->graphs.size() >= 8) drop_graphs(c);      // t_end changed repeatedly: start over
+    grp_ctx::Graph g;
+    const int rc = capture_graph(c, c->graph_steps, t_end, g);
+    if (rc) return rc;
+    c->graphs.push_back(g);
+    G = &c->graphs.back();
+  }
+  if (c->timing) {
+    for (size_t j = 0; j < G->ev_nodes.size(); ++j) {
+      cudaEvent_t e = nullptr;
+      if (!c->ev_free.empty()) { e = c->ev_free.back(); c->ev_free.pop_back(); }
+      else CK(cudaEventCreate(&e));
+      CK(cudaGraphExecEventRecordNodeSetEvent(G->x, G->ev_nodes[j], e));
+      c->ev_pending.push_back(e);
+    }
+  }
+  CK(cudaGraphLaunch(G->x, c->stream));
+  c->launches += G->launches;
+  c->cur ^= (G->steps & 1);
+  if (launch_form(c) == GRP_LAUNCH_SPLIT) c->smax_ready = true;
+  else c->smax_ready = false;
+  return GRP_OK;
+}
+
 int step_n(grp_ctx* c, int n_steps, double t_end)
 {
   // With a finite t_end, long requests test completion every DONE_CHECK steps
@@ -516,18 +676,14 @@ int step_n(grp_ctx* c, int n_steps, double t_end)
       if (done) break;
       since_check = 0;
     }
-    int k = 1;
-    const int form = launch_form(c);
-    if (form == GRP_LAUNCH_FUSED) {
-      k = c->steps_per_launch;
-      if (k > n_steps - i) k = n_steps - i;
-      const int rc = enqueue_batch(c, k, t_end);
+    int k = unit_steps(c);
+    if (c->graph_steps > 0 && n_steps - i >= c->graph_steps && c->graph_steps % k == 0) {
+      const int rc = replay_graph(c, t_end);
       if (rc) return rc;
-    } else if (form == GRP_LAUNCH_SPLIT) {
-      const int rc = enqueue_split(c, t_end);
-      if (rc) return rc;
+      k = c->graph_steps;
     } else {
-      const int rc = enqueue_step(c, t_end);
+      if (k > n_steps - i) k = n_steps - i;
+      const int rc = enqueue_unit(c, k, t_end);
       if (rc) return rc;
     }
     i += k;
@@ -615,6 +771,8 @@ int grp_set_guess_model(grp_ctx* c, const float* weights, int n_weights, const f
 {
   if (!c || !weights || !box || n_weights != MLP_NPARAM) return GRP_E_INVALID_ARG;
   CK(cudaSetDevice(c->p.device));
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
   if (!c->mlp) CK(cudaMalloc((void**)&c->mlp, sizeof(float) * MLP_NPARAM));
   if (!c->mlp_norm) CK(cudaMalloc((void**)&c->mlp_norm, sizeof(float) * 12));
   const cudaMemcpyKind k = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -628,6 +786,9 @@ int grp_set_harvest(grp_ctx* c, float* records, unsigned long long* count, long 
 {
   if (!c || log2_stride < 0 || log2_stride > 30) return GRP_E_INVALID_ARG;
   if (records && (!count || capacity < 1)) return GRP_E_INVALID_ARG;
+  CK(cudaSetDevice(c->p.device));
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
   c->harvest = records;
   c->harvest_count = records ? count : nullptr;
   c->harvest_cap = records ? capacity : 0;
@@ -638,7 +799,22 @@ int grp_set_harvest(grp_ctx* c, float* records, unsigned long long* count, long 
 int grp_set_kernel_timing(grp_ctx* c, int enable)
 {
   if (!c) return GRP_E_INVALID_ARG;
+  if (c->timing != (enable != 0)) {
+    CK(cudaSetDevice(c->p.device));
+    CK(cudaStreamSynchronize(c->stream));
+    drop_graphs(c);
+  }
   c->timing = enable != 0;
+  return GRP_OK;
+}
+
+int grp_set_graph(grp_ctx* c, int steps_per_graph)
+{
+  if (!c || steps_per_graph < 0 || steps_per_graph > 1024) return GRP_E_INVALID_ARG;
+  CK(cudaSetDevice(c->p.device));
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
+  c->graph_steps = steps_per_graph;
   return GRP_OK;
 }
 

@@ -283,10 +283,7 @@ static GRP_HD int star_pressure(const Phys& ph, const Side& L, const Side& R, do
   if (p0 > 0.0 && isfinite(p0)) {
     p = p0;
   } else if (ph.guess == 1) {
-    const double z = ph.gm1_2g;
-    const double num = L.c + R.c - 0.5 * ph.gm1 * du;
-    const double den = L.c * pow(L.p, -z) + R.c * pow(R.p, -z);
-    p = pow(num / den, 1.0 / z);
+    p = trrs<G75>(ph, L, R);
   } else {
     p = pvrs(L, R);
   }

@@ -79,6 +79,9 @@ def load(build_if_missing=True):
     L.grp_mlp_loss_grad.argtypes = [_vp, _vp, _vp, ctypes.c_longlong, _vp, _vp, _vp, _vp]
     L.grp_mlp_adam.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                ctypes.c_float, ctypes.c_float, _vp]
+    L.grp_riemann_batch.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int, _vp, _vp,
+                                    ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.grp_set_graph.argtypes = [_vp, ctypes.c_int]
     L.grp_destroy.argtypes = [_vp]
     L.grp_destroy.restype = None
     L.grp_status_string.argtypes = [ctypes.c_int]
@@ -124,6 +127,20 @@ def grp_mlp_adam(weights, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps
     _check(load().grp_mlp_adam(_dev(weights, "weights"), _dev(grad, "grad"), _dev(m, "m"), _dev(v, "v"),
                                int(step), float(lr), float(beta1), float(beta2), float(eps), stream),
            "grp_mlp_adam")
+
+
+def grp_riemann_batch(QL, QR, ps, iters, status, used=None, gamma=1.4, guess=0, weights=None, box=None,
+                      newton_rtol=1e-12, newton_max_iter=50, stream=None):
+    """Star pressures of n independent Riemann problems.  QL, QR: device float64
+    [3, n] (rho, m, E); ps float64 [n], iters and status int32 [n], used uint8
+    [n] or None: device outputs."""
+    n = int(QL.shape[-1])
+    _check(load().grp_riemann_batch(float(gamma), int(guess), float(newton_rtol), int(newton_max_iter),
+                                    _dev(weights, "weights") if weights is not None else None,
+                                    _dev(box, "box") if box is not None else None, n,
+                                    _dev(QL, "QL"), _dev(QR, "QR"), _dev(ps, "ps"), _dev(iters, "iters"),
+                                    _dev(status, "status"), _dev(used, "used") if used is not None else None,
+                                    stream), "grp_riemann_batch")
 
 
 def grp_step_noalloc(prob, avg_in, iface_in, avg_out, iface_out, t, t_end=float("inf"), stream=None):
@@ -270,6 +287,10 @@ class Solver:
     def set_launch(self, mode=GRP_LAUNCH_AUTO, threads=256, cells_per_block=2048, steps_per_launch=8):
         _check(self.L.grp_set_launch(self.h, int(mode), int(threads), int(cells_per_block),
                                      int(steps_per_launch)), "grp_set_launch")
+
+    def set_graph(self, steps_per_graph=16):
+        """CUDA graphs of steps_per_graph steps for grp_step (0: direct launches)."""
+        _check(self.L.grp_set_graph(self.h, int(steps_per_graph)), "grp_set_graph")
 
     def get_launch(self):
         v = [ctypes.c_int(0) for _ in range(5)]

@@ -110,6 +110,23 @@ def predict(w, x):
     return y
 
 
+def states_from_features(x, gamma=1.4):
+    """A Riemann problem with the given network inputs (float device [n, 6]):
+    the representative with rbar = pbar = 1 and ubar = 0 of the family that the
+    scaling and Galilean symmetries map onto one input vector.  Returns
+    conserved QL, QR as float64 device [3, n] (rho, m, E)."""
+    import torch
+    x = x.double()
+    cbar = math.sqrt(gamma)
+    rl, rr = torch.exp(x[:, 0]), torch.exp(x[:, 1])
+    pl, pr = torch.exp(x[:, 2]), torch.exp(x[:, 3])
+    ul, ur = x[:, 4] * cbar, x[:, 5] * cbar
+
+    def cons(r, u, p):
+        return torch.stack([r, r * u, p / (gamma - 1.0) + 0.5 * r * u * u]).contiguous()
+    return cons(rl, ul, pl), cons(rr, ur, pr)
+
+
 def fit_from_records(records, val_fraction=0.1, seed=0, **kw):
     """Split harvested records, train, and report the validation RMS error of
     ln(p*/p_TR) and the input box."""

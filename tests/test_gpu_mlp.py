@@ -74,15 +74,15 @@ def trained():
     runs.append((prob, avg, lm, lp, 400))
     rec = learned.harvest(runs, capacity=600_000, log2_stride=0)
     assert rec.shape[0] > 10_000
-    w, box, info = learned.fit_from_records(rec, epochs=80, batch=2048)
+    w, box, info = learned.fit_from_records(rec, epochs=200, batch=2048)
     return w, box, info, rec
 
 
 def test_training_learns_the_star_pressure(trained):
     w, box, info, rec = trained
     assert info["train_mse"][-1] < 0.5 * info["train_mse"][0]
-    # the correction of PVRS is learned: held-out RMS error well below the
-    # RMS of the correction itself (what plain PVRS gets wrong)
+    # the correction of the two-rarefaction estimate is learned: held-out RMS
+    # error well below the RMS of the correction itself (what p_TR gets wrong)
     t = rec[:, 6]
     assert info["val_rms"] < 0.5 * float(torch.sqrt(torch.mean(t * t)).item())
 
@@ -111,6 +111,42 @@ def test_learned_guess_leaves_results_unchanged_and_saves_iterations(trained):
     # and the oracle (PVRS) agrees with the learned-guess run
     check_parity(dict(prob, guess=grprec.GRP_GUESS_MLP), avg, lm, lp, 30, DISC_TOL,
                  solver=_with_model(prob, w, box))
+
+
+def test_learned_guess_gain_per_strong_solve(trained):
+    """What the trained network gains over the solver without it: Newton
+    iterations per strong-data Riemann problem, held-out interfaces of another
+    seed, from the PVRS start (the plain solver), the two-rarefaction start
+    (the network's base) and the learned start; p* itself is the same."""
+    from paper_2602_21911_gb300 import grprec, learned
+    w, box, info, rec = trained
+    prob, avg, lm, lp = I.batched(65536, seed=2604, domains=np.arange(1, 65536, 4))
+    ev = learned.harvest([(prob, avg, lm, lp, 200)], capacity=200_000, log2_stride=0)
+    assert ev.shape[0] > 2000
+    QL, QR = learned.states_from_features(ev[:, :6])
+    n = QL.shape[1]
+    res = {}
+    for g in (grprec.GRP_GUESS_PVRS, grprec.GRP_GUESS_TRRS, grprec.GRP_GUESS_MLP):
+        ps = torch.empty(n, dtype=torch.float64, device="cuda")
+        it = torch.empty(n, dtype=torch.int32, device="cuda")
+        st = torch.empty(n, dtype=torch.int32, device="cuda")
+        used = torch.empty(n, dtype=torch.uint8, device="cuda")
+        mlp = g == grprec.GRP_GUESS_MLP
+        grprec.grp_riemann_batch(QL, QR, ps, it, st, used, guess=g, weights=w if mlp else None,
+                                 box=box if mlp else None)
+        assert int((st != 0).sum()) == 0
+        res[g] = (ps, it.double(), used)
+    p0 = res[grprec.GRP_GUESS_PVRS][0]
+    for g in res:
+        # p* does not depend on the start (converged, then one more iteration)
+        assert float(((res[g][0] - p0).abs() / p0).max()) < 1e-13
+    m = {g: float(res[g][1].mean()) for g in res}
+    frac = float(res[grprec.GRP_GUESS_MLP][2].double().mean())
+    print("\nNewton iterations per strong-data solve (%d held-out): PVRS %.3f  TRRS %.3f  learned %.3f "
+          "(learned start used on %.1f%%)" % (n, m[0], m[1], m[2], 100 * frac))
+    assert frac > 0.9
+    assert m[grprec.GRP_GUESS_MLP] < m[grprec.GRP_GUESS_PVRS] - 0.5
+    assert m[grprec.GRP_GUESS_MLP] < m[grprec.GRP_GUESS_TRRS]
 
 
 def _with_model(prob, w, box):

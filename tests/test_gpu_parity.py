@@ -204,3 +204,48 @@ def test_launch_configuration_is_validated():
         with pytest.raises(grprec.GrpError):
             s.set_launch(*bad)
     assert s.get_launch()["form"] == grprec.GRP_LAUNCH_FLAT     # auto: one short domain runs flat
+
+
+@pytest.mark.parametrize("form,k", [(1, 1), (2, 4), (3, 1)])
+def test_graph_replay_is_bitwise_the_direct_launch(form, k):
+    """A CUDA graph replays the same kernels with the same arguments, so the
+    result, the counters and the launch count equal those of direct launches
+    bit for bit (graph of 16 steps; 5 steps, not a multiple of k = 4 in the
+    fused form, falls back to direct launches there)."""
+    from paper_2602_21911_gb300 import grprec
+    ids = np.arange(0, 65536, 173)[:300]
+    prob, avg, lm, lp = I.batched(domains=ids)
+    out = []
+    for graph in (0, 16, 5):
+        s = grprec.Solver(prob)
+        s.set_launch(form, 256, 2048, k)
+        s.set_graph(graph)
+        s.set_initial(avg, lm, lp)
+        s.step(37)
+        s.step(16)
+        s.step(19, 0.05)          # a finite t_end: another graph
+        a, g, t = s.get_state()
+        stats, status = s.get_stats()
+        out.append((a, g, t, stats, status, s.launch_count()))
+    for other in out[1:]:
+        for x, y in zip(out[0][:5], other[:5]):
+            assert np.array_equal(x, y)
+        assert out[0][5] == other[5]
+
+
+def test_kernel_timing_through_graphs():
+    from paper_2602_21911_gb300 import grprec
+    prob, avg, lm, lp = I.batched(domains=np.arange(0, 65536, 64)[:1024])
+    res = {}
+    for graph in (0, 16):
+        s = grprec.Solver(prob)
+        s.set_launch(grprec.GRP_LAUNCH_FLAT)
+        s.set_graph(graph)
+        s.set_initial(avg, lm, lp)
+        s.step(16)
+        s.set_kernel_timing(True)
+        s.step(32)
+        ms, n = s.kernel_timing()
+        assert n == 32 and ms > 0
+        res[graph] = ms / n
+    assert 0.5 < res[16] / res[0] < 2.0
