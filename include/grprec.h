@@ -76,7 +76,7 @@ enum {
   GRP_STAT_FLUX_FB = 4,        /* interfaces whose time series was cut to its leading term */
   GRP_STAT_RS_CALLS = 5,       /* exact Riemann solves */
   GRP_STAT_LOW_ORDER = 6,      /* interfaces recomputed with the first-order Godunov flux */
-  GRP_STAT_GUESS_USED = 7,     /* Newton solves started from the learned guess */
+  GRP_STAT_GUESS_USED = 7,     /* Newton solves started by the learned guess (network, or p_TR for two rarefactions) */
   GRP_STAT_GUESS_REJECTED = 8, /* learned guesses rejected (range / non-finite / stall) */
   GRP_NSTATS = 9
 };
@@ -206,8 +206,10 @@ int grp_set_graph(grp_ctx *ctx, int steps_per_graph);
  * cbar = sqrt(gamma pbar / rbar), ubar = (uL+uR)/2:
  *   ln(rhoL/rbar), ln(rhoR/rbar), ln(pL/pbar), ln(pR/pbar), (uL-ubar)/cbar, (uR-ubar)/cbar
  * Output: y = ln(p* / p_TR), the correction of the two-rarefaction estimate
- * p_TR; the Newton start is p_TR e^y.  The network serves strong data only,
- * |ln(pL/pR)| > 0.5 or |uR-uL|/cbar > 0.5 (PVRS starts the rest).
+ * p_TR; the Newton start is p_TR e^y.  The network serves strong data with a
+ * shock: |ln(pL/pR)| > 0.5 or |uR-uL|/cbar > 0.5, and p_TR > min(pL, pR).
+ * Strong data with two rarefactions (p_TR <= min(pL, pR)) start at p_TR,
+ * which is p* there; PVRS starts the rest.
  * Parameters (GRP_MLP_NPARAM floats): W1[6][64],
  * b1[64], W2[64][64], b2[64], w3[64], b3.
  *
@@ -219,7 +221,7 @@ int grp_set_graph(grp_ctx *ctx, int steps_per_graph);
  * device (ptr_is_device); copied, not kept.  Synchronises.
  *
  * grp_set_harvest: record (6 inputs, ln(p* / p_TR), Newton iterations) of one
- * strong-data interface in 2^log2_stride, by a hash of (interface, step),
+ * strong-data interface with a shock in 2^log2_stride, by a hash of (interface, step),
  * into the caller's device buffer records[capacity][8] during later steps;
  * *count (device, caller-zeroed) counts the offered records and may exceed
  * capacity (the excess is dropped).  records = NULL stops harvesting.

@@ -396,8 +396,9 @@ static GRP_HD Prim sample_vacuum_zero(const Phys& ph, const Side& L, const Side&
 // Learned Newton initial guess (FP32): a 6 -> 64 -> 64 -> 1 tanh network on
 // features invariant under the scaling and Galilean symmetries of the Riemann
 // problem, predicting the correction y = ln(p*/p_TR) of the two-rarefaction
-// estimate, so that the guess is p_TR e^y.  Used only for strong data (where
-// PVRS is poor); PVRS stays the start elsewhere and the fallback.
+// estimate, so that the guess is p_TR e^y.  Used only for strong data with a
+// shock (p_TR > min(pL, pR)); strong data with two rarefactions start at p_TR,
+// which is exact there; PVRS stays the start elsewhere and the fallback.
 // Parameter layout: W1[6][64], b1[64], W2[64][64], b2[64], w3[64], b3.
 // ---------------------------------------------------------------------------
 constexpr int MLP_NIN = 6, MLP_NH = 64;
@@ -468,10 +469,11 @@ struct RSInfo {
 
 // Godunov state at x/t = 0 of conserved data QL | QR, as conserved Q and
 // primitive W.  allow_vacuum: vacuum data are sampled and ST_VACUUM returned
-// with Q valid.  With a learned model (ph.guess == 2) non-trivial data start
-// Newton from the network's prediction; an input outside the training box, a
-// prediction out of range or not finite, or no convergence within
-// MLP_GUESS_MAX_ITER iterations falls back to PVRS (iterations add up).
+// with Q valid.  With a learned model (ph.guess == 2) strong data start Newton
+// from the network's prediction (or from p_TR for two rarefactions); an input
+// outside the training box, a prediction out of range or not finite, or no
+// convergence within MLP_GUESS_MAX_ITER iterations falls back to PVRS
+// (iterations add up).
 template <bool G75>
 static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double QR[3], bool allow_vacuum,
                                 double Q[3], Prim& W, int& iters, RSInfo* info = nullptr)
@@ -486,6 +488,17 @@ static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double
     if (info->has_x) {
       info->base = trrs<G75>(ph, L, R);
       info->has_x = info->base > 0.0 && isfinite(info->base);
+    }
+    // p_TR <= min(pL, pR): both waves are rarefactions and p_TR is p* itself
+    // (up to rounding); the network only serves data with a shock
+    const bool two_rare = info->has_x && info->base <= fmin(L.p, R.p);
+    info->has_x = info->has_x && !two_rare;
+    if (ph.guess == 2 && ph.mlp_w && two_rare) {
+      Phys pg = ph;
+      pg.max_iter = ph.max_iter < MLP_GUESS_MAX_ITER ? ph.max_iter : MLP_GUESS_MAX_ITER;
+      info->guess = 2;
+      st = star_pressure<G75>(pg, L, R, info->base, ps, us, iters);
+      if (st == ST_OK) info->guess = 1;
     }
     if (ph.guess == 2 && ph.mlp_w && info->has_x) {
       bool inbox = true;

@@ -115,9 +115,10 @@ def test_learned_guess_leaves_results_unchanged_and_saves_iterations(trained):
 
 def test_learned_guess_gain_per_strong_solve(trained):
     """What the trained network gains over the solver without it: Newton
-    iterations per strong-data Riemann problem, held-out interfaces of another
-    seed, from the PVRS start (the plain solver), the two-rarefaction start
-    (the network's base) and the learned start; p* itself is the same."""
+    iterations per strong-data Riemann problem with a shock (the problems the
+    network serves), held-out interfaces of another seed, from the PVRS start
+    (the plain solver), the two-rarefaction start (the network's base) and the
+    learned start; p* itself is the same."""
     from paper_2602_21911_gb300 import grprec, learned
     w, box, info, rec = trained
     prob, avg, lm, lp = I.batched(65536, seed=2604, domains=np.arange(1, 65536, 4))
@@ -142,7 +143,7 @@ def test_learned_guess_gain_per_strong_solve(trained):
         assert float(((res[g][0] - p0).abs() / p0).max()) < 1e-13
     m = {g: float(res[g][1].mean()) for g in res}
     frac = float(res[grprec.GRP_GUESS_MLP][2].double().mean())
-    print("\nNewton iterations per strong-data solve (%d held-out): PVRS %.3f  TRRS %.3f  learned %.3f "
+    print("\nNewton iterations per strong-data solve with a shock (%d held-out): PVRS %.3f  TRRS %.3f  learned %.3f "
           "(learned start used on %.1f%%)" % (n, m[0], m[1], m[2], 100 * frac))
     assert frac > 0.9
     assert m[grprec.GRP_GUESS_MLP] < m[grprec.GRP_GUESS_PVRS] - 0.5
