@@ -76,7 +76,7 @@ enum {
   GRP_STAT_FLUX_FB = 4,        /* interfaces whose time series was cut to its leading term */
   GRP_STAT_RS_CALLS = 5,       /* exact Riemann solves */
   GRP_STAT_LOW_ORDER = 6,      /* interfaces recomputed with the first-order Godunov flux */
-  GRP_STAT_GUESS_USED = 7,     /* Newton solves started by the learned guess (network, or p_TR for two rarefactions) */
+  GRP_STAT_GUESS_USED = 7,     /* Newton solves started from the network's prediction */
   GRP_STAT_GUESS_REJECTED = 8, /* learned guesses rejected (range / non-finite / stall) */
   GRP_NSTATS = 9
 };
@@ -205,23 +205,26 @@ int grp_set_graph(grp_ctx *ctx, int steps_per_graph);
  * states (rho,u,p)_L,R with rbar = sqrt(rhoL rhoR), pbar = sqrt(pL pR),
  * cbar = sqrt(gamma pbar / rbar), ubar = (uL+uR)/2:
  *   ln(rhoL/rbar), ln(rhoR/rbar), ln(pL/pbar), ln(pR/pbar), (uL-ubar)/cbar, (uR-ubar)/cbar
- * Output: y = ln(p* / p_TR), the correction of the two-rarefaction estimate
- * p_TR; the Newton start is p_TR e^y.  The network serves strong data with a
- * shock: |ln(pL/pR)| > 0.5 or |uR-uL|/cbar > 0.5, and p_TR > min(pL, pR).
- * Strong data with two rarefactions (p_TR <= min(pL, pR)) start at p_TR,
- * which is p* there; PVRS starts the rest.
+ * Output: v, the normalised correction of the two-rarefaction estimate p_TR:
+ * with the shock strength s = ln(p_TR / min(pL, pR)) the Newton start is
+ * p_TR exp(-0.005 s^3 v) (the correction vanishes like s^3; v is of order
+ * one).  Strong data, |ln(pL/pR)| > 0.5 or |uR-uL|/cbar > 0.5, with
+ * s >= 1e-3 start from the network; strong data with s < 1e-3 (two
+ * rarefactions, where p_TR is p*, or weaker shocks) start at p_TR; PVRS starts
+ * the rest.
  * Parameters (GRP_MLP_NPARAM floats): W1[6][64],
  * b1[64], W2[64][64], b2[64], w3[64], b3.
  *
  * grp_set_guess_model: load the weights and the input box (12 floats: lo[6],
  * hi[6]); used when grp_problem.guess == GRP_GUESS_MLP.  An input outside the
- * box, an output that is not finite or outside |y| <= ln 1e8, or no
+ * box, an output that is not finite or outside |v| <= 50, or no
  * convergence within 8 Newton iterations falls back to PVRS; the counters
  * GRP_STAT_GUESS_USED / GRP_STAT_GUESS_REJECTED record both.  Pointers host or
  * device (ptr_is_device); copied, not kept.  Synchronises.
  *
- * grp_set_harvest: record (6 inputs, ln(p* / p_TR), Newton iterations) of one
- * strong-data interface with a shock in 2^log2_stride, by a hash of (interface, step),
+ * grp_set_harvest: record (6 inputs, the target v = ln(p* / p_TR) /
+ * (-0.005 s^3), Newton iterations) of one network-served interface in
+ * 2^log2_stride, by a hash of (interface, step),
  * into the caller's device buffer records[capacity][8] during later steps;
  * *count (device, caller-zeroed) counts the offered records and may exceed
  * capacity (the excess is dropped).  records = NULL stops harvesting.
@@ -253,7 +256,9 @@ int grp_mlp_adam(float *weights, const float *grad, float *m, float *v, int step
  * independent pairs of conserved states, from the start `guess` (GRP_GUESS_*;
  * GRP_GUESS_MLP needs `weights` and `box` as for grp_set_guess_model, device
  * pointers, and serves strong data only, the rest starting from PVRS).
- * QL, QR: device, 3 planes of n doubles (rho, m, E).  Out (device): ps[n] the
+ * QL, QR: device, 3 planes of n doubles (rho, m, E).  p_start: NULL, or
+ * device [n] explicit Newton starts (then `guess` only picks the fallback,
+ * which is PVRS).  Out (device): ps[n] the
  * star pressure (0 unless status is 0), iters[n] the Newton iterations of all
  * attempts, status[n] 0 ok / 1 no convergence within newton_max_iter /
  * 2 vacuum data, used[n] (may be NULL) 1 where the learned guess started the
@@ -262,8 +267,8 @@ int grp_mlp_adam(float *weights, const float *grad, float *m, float *v, int step
  */
 int grp_riemann_batch(double gamma, int guess, double newton_rtol, int newton_max_iter,
                       const float *weights, const float *box, long long n, const double *QL,
-                      const double *QR, double *ps, int *iters, int *status, unsigned char *used,
-                      void *stream);
+                      const double *QR, const double *p_start, double *ps, int *iters, int *status,
+                      unsigned char *used, void *stream);
 
 /* Number of kernel launches this context has enqueued since grp_create. */
 long long grp_launch_count(const grp_ctx *ctx);

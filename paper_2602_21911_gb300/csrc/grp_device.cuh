@@ -395,17 +395,24 @@ static GRP_HD Prim sample_vacuum_zero(const Phys& ph, const Side& L, const Side&
 // ---------------------------------------------------------------------------
 // Learned Newton initial guess (FP32): a 6 -> 64 -> 64 -> 1 tanh network on
 // features invariant under the scaling and Galilean symmetries of the Riemann
-// problem, predicting the correction y = ln(p*/p_TR) of the two-rarefaction
-// estimate, so that the guess is p_TR e^y.  Used only for strong data with a
-// shock (p_TR > min(pL, pR)); strong data with two rarefactions start at p_TR,
-// which is exact there; PVRS stays the start elsewhere and the fallback.
+// problem, predicting the correction of the two-rarefaction estimate p_TR.
+// With the shock strength s = ln(p_TR / min(pL, pR)) the correction
+// ln(p*/p_TR) vanishes like s^3 (the Hugoniot and the isentrope agree to
+// second order), so the network predicts the normalised correction
+// v = ln(p*/p_TR) / (MLP_T_SCALE s^3), of order one at every strength, and the
+// guess is p_TR exp(MLP_T_SCALE s^3 v).  Only strong data use it: with
+// s >= MLP_S_MIN the network, below it (two rarefactions: s <= 0, p_TR is p*)
+// p_TR itself; PVRS starts the rest and is the fallback.
 // Parameter layout: W1[6][64], b1[64], W2[64][64], b2[64], w3[64], b3.
 // ---------------------------------------------------------------------------
 constexpr int MLP_NIN = 6, MLP_NH = 64;
 constexpr int MLP_NPARAM = MLP_NIN * MLP_NH + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NH + 1;
 constexpr int MLP_GUESS_MAX_ITER = 8;     // Newton from the learned guess gives up after this
 constexpr float MLP_GATE = 0.5f;          // |ln(pL/pR)| or |du|/cbar above this: strong data
-constexpr float MLP_YMAX = 18.420681f;    // |ln(p*/pbar)| <= ln 1e8
+constexpr double MLP_S_MIN = 1e-3;        // shock strength below which p_TR is the start
+constexpr double MLP_T_SCALE = -0.005;    // output scale: ln(p*/p_TR) = MLP_T_SCALE s^3 v
+constexpr float MLP_VMAX = 50.0f;         // |v| above this: prediction rejected
+constexpr double MLP_YMAX = 18.420681;    // |ln(p*/p_TR)| <= ln 1e8
 
 GRP_HD __forceinline__ float fast_tanh(float x)
 {
@@ -462,9 +469,10 @@ GRP_HD __forceinline__ float mlp_eval(const float* __restrict__ w, const float x
 struct RSInfo {
   double ps = 0.0, pbar = 0.0;   // star pressure; pbar of the features
   double base = 0.0;             // two-rarefaction estimate (the base of the learned correction)
+  double s3 = 0.0;               // cube of the shock strength ln(p_TR / min(pL, pR))
   float x[6];                    // features (valid when has_x)
-  bool has_x = false;
-  int guess = 0;                 // 0 not tried, 1 learned guess used, 2 learned guess rejected
+  bool has_x = false;            // strong data with a shock of strength >= MLP_S_MIN
+  int guess = 0;                 // 0 not tried, 1 network start used, 2 rejected, 3 p_TR start (two rarefactions)
 };
 
 // Godunov state at x/t = 0 of conserved data QL | QR, as conserved Q and
@@ -484,33 +492,33 @@ static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double
   int st = -1;
   iters = 0;
   if (ph.features && info) {
-    info->has_x = mlp_features(ph, L, R, info->x, info->pbar);
-    if (info->has_x) {
-      info->base = trrs<G75>(ph, L, R);
-      info->has_x = info->base > 0.0 && isfinite(info->base);
-    }
-    // p_TR <= min(pL, pR): both waves are rarefactions and p_TR is p* itself
-    // (up to rounding); the network only serves data with a shock
-    const bool two_rare = info->has_x && info->base <= fmin(L.p, R.p);
-    info->has_x = info->has_x && !two_rare;
-    if (ph.guess == 2 && ph.mlp_w && two_rare) {
-      Phys pg = ph;
-      pg.max_iter = ph.max_iter < MLP_GUESS_MAX_ITER ? ph.max_iter : MLP_GUESS_MAX_ITER;
+    const bool strong = mlp_features(ph, L, R, info->x, info->pbar);
+    const double base = strong ? trrs<G75>(ph, L, R) : 0.0;
+    const bool ok = strong && base > 0.0 && isfinite(base);
+    // shock strength s = ln(p_TR / min(pL, pR)); s <= 0: two rarefactions, and
+    // p_TR is p* up to rounding; s < MLP_S_MIN: |ln(p*/p_TR)| < 1e-11
+    const double sh = ok ? log(base / fmin(L.p, R.p)) : 0.0;
+    info->base = base;
+    info->s3 = sh * sh * sh;
+    info->has_x = ok && sh >= MLP_S_MIN;
+    if (ph.guess == 2 && ph.mlp_w && ok) {
+      double p0 = base;
+      bool go = true;
       info->guess = 2;
-      st = star_pressure<G75>(pg, L, R, info->base, ps, us, iters);
-      if (st == ST_OK) info->guess = 1;
-    }
-    if (ph.guess == 2 && ph.mlp_w && info->has_x) {
-      bool inbox = true;
+      if (info->has_x) {
+        bool inbox = true;
 #pragma unroll
-      for (int i = 0; i < 6; ++i) inbox = inbox && info->x[i] >= ph.mlp_box[i] && info->x[i] <= ph.mlp_box[6 + i];
-      const float y = inbox ? mlp_eval(ph.mlp_w, info->x) : 0.0f;
-      info->guess = 2;
-      if (inbox && y == y && fabsf(y) <= MLP_YMAX) {
+        for (int i = 0; i < 6; ++i) inbox = inbox && info->x[i] >= ph.mlp_box[i] && info->x[i] <= ph.mlp_box[6 + i];
+        const float v = inbox ? mlp_eval(ph.mlp_w, info->x) : 0.0f;
+        const double y = MLP_T_SCALE * info->s3 * (double)v;
+        go = inbox && v == v && fabsf(v) <= MLP_VMAX && fabs(y) <= MLP_YMAX;
+        p0 = base * exp(y);
+      }
+      if (go) {
         Phys pg = ph;
         pg.max_iter = ph.max_iter < MLP_GUESS_MAX_ITER ? ph.max_iter : MLP_GUESS_MAX_ITER;
-        st = star_pressure<G75>(pg, L, R, info->base * exp((double)y), ps, us, iters);
-        if (st == ST_OK) info->guess = 1;
+        st = star_pressure<G75>(pg, L, R, p0, ps, us, iters);
+        if (st == ST_OK) info->guess = info->has_x ? 1 : 3;   // 3: p_TR start, not a network start
       }
     }
   }

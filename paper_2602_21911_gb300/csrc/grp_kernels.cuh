@@ -285,7 +285,7 @@ __device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d,
           float* r = a.harvest + 8 * k;
 #pragma unroll
           for (int i = 0; i < 6; ++i) r[i] = info.x[i];
-          r[6] = (float)log(info.ps / info.base);
+          r[6] = (float)(log(info.ps / info.base) / (MLP_T_SCALE * info.s3));
           r[7] = (float)iters;
         }
       }

@@ -15,30 +15,48 @@ namespace {
 
 template <bool G75>
 __global__ void k_riemann_batch(Phys ph, long long n, const double* __restrict__ QL, const double* __restrict__ QR,
-                                double* __restrict__ ps, int* __restrict__ iters, int* __restrict__ status,
-                                unsigned char* __restrict__ used)
+                                const double* __restrict__ p_start, double* __restrict__ ps,
+                                int* __restrict__ iters, int* __restrict__ status, unsigned char* __restrict__ used)
 {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double l[3] = {QL[i], QL[n + i], QL[2 * n + i]};
   const double r[3] = {QR[i], QR[n + i], QR[2 * n + i]};
-  RSInfo info;
-  double Q[3];
-  Prim W;
-  int it = 0;
-  const int st = riemann_state<G75>(ph, l, r, true, Q, W, it, &info);
-  ps[i] = st == ST_OK ? info.ps : 0.0;
+  int st, it = 0;
+  double p = 0.0;
+  bool by_net = false;
+  if (p_start) {
+    // explicit start; PVRS when it fails
+    const Side L = make_side(ph, l), R = make_side(ph, r);
+    double us;
+    st = star_pressure<G75>(ph, L, R, p_start[i], p, us, it);
+    if (st == ST_NO_CONV) {
+      int it2 = 0;
+      Phys pv = ph;
+      pv.guess = 0;
+      st = star_pressure<G75>(pv, L, R, 0.0, p, us, it2);
+      it += it2;
+    }
+  } else {
+    RSInfo info;
+    double Q[3];
+    Prim W;
+    st = riemann_state<G75>(ph, l, r, true, Q, W, it, &info);
+    p = info.ps;
+    by_net = info.guess == 1;
+  }
+  ps[i] = st == ST_OK ? p : 0.0;
   iters[i] = it;
   status[i] = st;
-  if (used) used[i] = info.guess == 1 ? 1 : 0;
+  if (used) used[i] = by_net ? 1 : 0;
 }
 
 }  // namespace
 
 extern "C" int grp_riemann_batch(double gamma, int guess, double newton_rtol, int newton_max_iter,
                                  const float* weights, const float* box, long long n, const double* QL,
-                                 const double* QR, double* ps, int* iters, int* status, unsigned char* used,
-                                 void* stream)
+                                 const double* QR, const double* p_start, double* ps, int* iters, int* status,
+                                 unsigned char* used, void* stream)
 {
   if (!(gamma > 1.0 && isfinite(gamma)) || guess < GRP_GUESS_PVRS || guess > GRP_GUESS_MLP) return GRP_E_INVALID_ARG;
   if (!(newton_rtol > 0.0) || newton_max_iter < 2 || n < 0) return GRP_E_INVALID_ARG;
@@ -51,8 +69,8 @@ extern "C" int grp_riemann_batch(double gamma, int guess, double newton_rtol, in
   ph.features = guess == GRP_GUESS_MLP ? 1 : 0;
   const unsigned nb = (unsigned)((n + 127) / 128);
   if (gamma == 1.4)
-    k_riemann_batch<true><<<nb, 128, 0, (cudaStream_t)stream>>>(ph, n, QL, QR, ps, iters, status, used);
+    k_riemann_batch<true><<<nb, 128, 0, (cudaStream_t)stream>>>(ph, n, QL, QR, p_start, ps, iters, status, used);
   else
-    k_riemann_batch<false><<<nb, 128, 0, (cudaStream_t)stream>>>(ph, n, QL, QR, ps, iters, status, used);
+    k_riemann_batch<false><<<nb, 128, 0, (cudaStream_t)stream>>>(ph, n, QL, QR, p_start, ps, iters, status, used);
   return cudaGetLastError() == cudaSuccess ? GRP_OK : GRP_E_CUDA;
 }

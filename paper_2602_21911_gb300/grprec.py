@@ -80,7 +80,7 @@ def load(build_if_missing=True):
     L.grp_mlp_adam.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                ctypes.c_float, ctypes.c_float, _vp]
     L.grp_riemann_batch.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int, _vp, _vp,
-                                    ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+                                    ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.grp_set_graph.argtypes = [_vp, ctypes.c_int]
     L.grp_destroy.argtypes = [_vp]
     L.grp_destroy.restype = None
@@ -130,15 +130,18 @@ def grp_mlp_adam(weights, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps
 
 
 def grp_riemann_batch(QL, QR, ps, iters, status, used=None, gamma=1.4, guess=0, weights=None, box=None,
-                      newton_rtol=1e-12, newton_max_iter=50, stream=None):
+                      p_start=None, newton_rtol=1e-12, newton_max_iter=50, stream=None):
     """Star pressures of n independent Riemann problems.  QL, QR: device float64
-    [3, n] (rho, m, E); ps float64 [n], iters and status int32 [n], used uint8
-    [n] or None: device outputs."""
+    [3, n] (rho, m, E); p_start: None or device float64 [n] explicit starts;
+    ps float64 [n], iters and status int32 [n], used uint8 [n] or None: device
+    outputs."""
     n = int(QL.shape[-1])
     _check(load().grp_riemann_batch(float(gamma), int(guess), float(newton_rtol), int(newton_max_iter),
                                     _dev(weights, "weights") if weights is not None else None,
                                     _dev(box, "box") if box is not None else None, n,
-                                    _dev(QL, "QL"), _dev(QR, "QR"), _dev(ps, "ps"), _dev(iters, "iters"),
+                                    _dev(QL, "QL"), _dev(QR, "QR"),
+                                    _dev(p_start, "p_start") if p_start is not None else None,
+                                    _dev(ps, "ps"), _dev(iters, "iters"),
                                     _dev(status, "status"), _dev(used, "used") if used is not None else None,
                                     stream), "grp_riemann_batch")
 

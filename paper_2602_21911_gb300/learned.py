@@ -1,8 +1,10 @@
 """Learned Newton initial guess: harvest, training and loading (marshalling only).
 
 1. harvest: run the scheme with grp_set_harvest on; the flux kernel records the
-   network inputs and the converged FP64 correction ln(p*/p_TR) of the
-   two-rarefaction estimate at the strong-data interfaces.
+   network inputs and the converged FP64 target v = ln(p*/p_TR) / (-0.005 s^3)
+   (the correction of the two-rarefaction estimate p_TR, normalised by the cube
+   of the shock strength s = ln(p_TR / min(pL, pR))) at the interfaces the
+   network serves.
 2. train: mini-batch Adam on the mean-squared error, every batch through the
    library's FP32 kernels grp_mlp_loss_grad and grp_mlp_adam.
 3. load: grp_set_guess_model with the weights and the input box of the data.
@@ -20,7 +22,7 @@ NPARAM = grprec.GRP_MLP_NPARAM
 
 def harvest(runs, capacity=2_000_000, log2_stride=2, device=0):
     """runs: iterable of (prob, avg, lim_minus, lim_plus, n_steps).  Returns a
-    float32 device tensor [n, 8]: 6 inputs, ln(p*/p_TR), Newton iterations."""
+    float32 device tensor [n, 8]: 6 inputs, target v, Newton iterations."""
     import torch
     dev = torch.device("cuda", device)
     out = []
@@ -68,7 +70,7 @@ def input_box(x, margin=0.05):
     return torch.cat([lo - pad, hi + pad]).contiguous()
 
 
-def train(x, t, epochs=30, batch=4096, lr=2e-3, lr_end=1e-4, seed=0, weights=None, verbose=False):
+def train(x, t, epochs=800, batch=1024, lr=3e-3, lr_end=1e-5, seed=0, weights=None, verbose=False):
     """Mini-batch Adam, learning rate decayed geometrically from lr to lr_end.
     x: float32 device [n, 6]; t: float32 device [n].  Returns (weights, losses
     per epoch)."""
@@ -129,7 +131,7 @@ def states_from_features(x, gamma=1.4):
 
 def fit_from_records(records, val_fraction=0.1, seed=0, **kw):
     """Split harvested records, train, and report the validation RMS error of
-    ln(p*/p_TR) and the input box."""
+    the target v and the input box."""
     import torch
     n = records.shape[0]
     gen = torch.Generator(device=records.device).manual_seed(seed + 1)

@@ -68,23 +68,23 @@ def _batch_subset(k=150, step=311):
 def trained():
     from paper_2602_21911_gb300 import learned
     runs = []
-    prob, avg, lm, lp = I.batched(65536, seed=2603, domains=np.arange(0, 65536, 2))
-    runs.append((prob, avg, lm, lp, 300))
+    prob, avg, lm, lp = I.batched(65536, seed=2603)
+    runs.append((prob, avg, lm, lp, 500))
     prob, avg, lm, lp = I.sod(4096)
     runs.append((prob, avg, lm, lp, 400))
-    rec = learned.harvest(runs, capacity=600_000, log2_stride=0)
-    assert rec.shape[0] > 10_000
-    w, box, info = learned.fit_from_records(rec, epochs=200, batch=2048)
+    rec = learned.harvest(runs, capacity=2_000_000, log2_stride=0)
+    assert rec.shape[0] > 30_000
+    w, box, info = learned.fit_from_records(rec)
     return w, box, info, rec
 
 
 def test_training_learns_the_star_pressure(trained):
     w, box, info, rec = trained
     assert info["train_mse"][-1] < 0.5 * info["train_mse"][0]
-    # the correction of the two-rarefaction estimate is learned: held-out RMS
-    # error well below the RMS of the correction itself (what p_TR gets wrong)
+    # the normalised correction of the two-rarefaction estimate is learned:
+    # held-out RMS error well below its spread (what a constant gets wrong)
     t = rec[:, 6]
-    assert info["val_rms"] < 0.5 * float(torch.sqrt(torch.mean(t * t)).item())
+    assert info["val_rms"] < 0.1 * float(t.std().item())
 
 
 def test_learned_guess_leaves_results_unchanged_and_saves_iterations(trained):
@@ -113,12 +113,26 @@ def test_learned_guess_leaves_results_unchanged_and_saves_iterations(trained):
                  solver=_with_model(prob, w, box))
 
 
+def _trrs_host(QL, QR, gamma=1.4):
+    """Two-rarefaction star pressure and primitive states, computed with torch
+    on the device (a baseline of the test, independent of the library)."""
+    r = [QL[0], QR[0]]
+    u = [QL[1] / QL[0], QR[1] / QR[0]]
+    p = [(gamma - 1) * (Q[2] - 0.5 * Q[1] * Q[1] / Q[0]) for Q in (QL, QR)]
+    c = [torch.sqrt(gamma * p[k] / r[k]) for k in (0, 1)]
+    z = (gamma - 1) / (2 * gamma)
+    num = c[0] + c[1] - 0.5 * (gamma - 1) * (u[1] - u[0])
+    return (num / (c[0] * p[0] ** -z + c[1] * p[1] ** -z)) ** (1 / z), p
+
+
 def test_learned_guess_gain_per_strong_solve(trained):
     """What the trained network gains over the solver without it: Newton
     iterations per strong-data Riemann problem with a shock (the problems the
     network serves), held-out interfaces of another seed, from the PVRS start
-    (the plain solver), the two-rarefaction start (the network's base) and the
-    learned start; p* itself is the same."""
+    (the plain solver), the two-rarefaction start p_TR (the network's base),
+    p_TR with the best constant normalised correction (the mean training
+    target: everything but the learned dependence on the data), and the
+    learned start.  p* itself does not depend on the start."""
     from paper_2602_21911_gb300 import grprec, learned
     w, box, info, rec = trained
     prob, avg, lm, lp = I.batched(65536, seed=2604, domains=np.arange(1, 65536, 4))
@@ -126,28 +140,35 @@ def test_learned_guess_gain_per_strong_solve(trained):
     assert ev.shape[0] > 2000
     QL, QR = learned.states_from_features(ev[:, :6])
     n = QL.shape[1]
+    ptr, p = _trrs_host(QL, QR)
+    s3 = torch.log(ptr / torch.minimum(p[0], p[1])) ** 3
+    v_mean = float(rec[:, 6].double().mean().item())
+    starts = {"PVRS": (grprec.GRP_GUESS_PVRS, None), "TRRS": (grprec.GRP_GUESS_TRRS, None),
+              "TRRS+const": (grprec.GRP_GUESS_PVRS, ptr * torch.exp(-0.005 * s3 * v_mean)),
+              "learned": (grprec.GRP_GUESS_MLP, None)}
     res = {}
-    for g in (grprec.GRP_GUESS_PVRS, grprec.GRP_GUESS_TRRS, grprec.GRP_GUESS_MLP):
+    for name, (g, p0) in starts.items():
         ps = torch.empty(n, dtype=torch.float64, device="cuda")
         it = torch.empty(n, dtype=torch.int32, device="cuda")
         st = torch.empty(n, dtype=torch.int32, device="cuda")
-        used = torch.empty(n, dtype=torch.uint8, device="cuda")
+        used = torch.zeros(n, dtype=torch.uint8, device="cuda")
         mlp = g == grprec.GRP_GUESS_MLP
         grprec.grp_riemann_batch(QL, QR, ps, it, st, used, guess=g, weights=w if mlp else None,
-                                 box=box if mlp else None)
+                                 box=box if mlp else None, p_start=p0)
         assert int((st != 0).sum()) == 0
-        res[g] = (ps, it.double(), used)
-    p0 = res[grprec.GRP_GUESS_PVRS][0]
-    for g in res:
-        # p* does not depend on the start (converged, then one more iteration)
-        assert float(((res[g][0] - p0).abs() / p0).max()) < 1e-13
-    m = {g: float(res[g][1].mean()) for g in res}
-    frac = float(res[grprec.GRP_GUESS_MLP][2].double().mean())
-    print("\nNewton iterations per strong-data solve with a shock (%d held-out): PVRS %.3f  TRRS %.3f  learned %.3f "
-          "(learned start used on %.1f%%)" % (n, m[0], m[1], m[2], 100 * frac))
-    assert frac > 0.9
-    assert m[grprec.GRP_GUESS_MLP] < m[grprec.GRP_GUESS_PVRS] - 0.5
-    assert m[grprec.GRP_GUESS_MLP] < m[grprec.GRP_GUESS_TRRS]
+        res[name] = (ps, float(it.double().mean().item()), float(used.double().mean().item()))
+    p_ref = res["PVRS"][0]
+    for name in res:
+        # converged, then one more iteration: the same p* from every start
+        assert float(((res[name][0] - p_ref).abs() / p_ref).max()) < 1e-13
+    m = {name: res[name][1] for name in res}
+    print("\nNewton iterations per strong-data solve with a shock (%d held-out): " % n
+          + "  ".join("%s %.3f" % kv for kv in m.items())
+          + "  (network start used on %.1f%%)" % (100 * res["learned"][2]))
+    assert res["learned"][2] > 0.9
+    assert m["learned"] < m["PVRS"] - 1.5
+    assert m["learned"] < m["TRRS"] - 0.3
+    assert m["learned"] < m["TRRS+const"] - 0.1
 
 
 def _with_model(prob, w, box):
