@@ -8,6 +8,16 @@ every domain (the whole hot path: CFL reduction, reconstruction, GRP, update,
 repair, write-back).  The state (~0.8 GB) is larger than L2, so no flush is
 needed between steps.
 
+The headline value is the batched form with the learned Newton guess (network
+trained first, on interfaces harvested from another seed).  Beside it:
+  plain        the same domains advanced one domain per solver, direct kernel
+               launches, PVRS start: the method without batching and learning
+               (a bounded sample of domains);
+  batched_pvrs the batched form with the PVRS start (what the learned guess adds);
+  equal_error  the largest relative difference between the final states of the
+               three forms on the plain sample: the same scheme, so the same L1
+               error, up to round-off.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the CPU oracle (the only reference this build has) on a
@@ -53,6 +63,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--launch", default="tune", choices=["tune", "auto", "flat", "fused", "split"],
                     help="launch configuration: autotuned (default), library default, or forced")
+    ap.add_argument("--guess", default="learned", choices=["learned", "pvrs"])
+    ap.add_argument("--plain-domains", type=int, default=128, help="sample size of the plain form")
+    ap.add_argument("--plain-steps", type=int, default=60)
     return ap.parse_args()
 
 
@@ -134,6 +147,67 @@ def workload(args, rank):
     return prob, avg, lm, lp
 
 
+def train_guess(args, device):
+    """Harvest interfaces from another seed of the batch (and a shock tube),
+    train the network with the library's kernels; returns (weights, box, info)."""
+    from paper_2602_21911_gb300 import inputs as I, learned
+    t0 = time.perf_counter()
+    runs = [(*I.batched(args.domains, seed=2603, M=args.M), 500), (*I.sod(4096, M=args.M), 400)]
+    rec = learned.harvest(runs, capacity=2_000_000, log2_stride=0, device=device)
+    w, box, info = learned.fit_from_records(rec)
+    return w, box, {"records": int(rec.shape[0]), "val_rms": info["val_rms"],
+                    "target_std": float(rec[:, 6].std().item()), "seconds": time.perf_counter() - t0,
+                    "harvest": "batched seed 2603 x 500 steps + Sod 4096 x 400 steps"}
+
+
+def plain_arm(args, device, stream, w, box):
+    """The plain GPU form on an evenly spread sample of the domains: one
+    solver per domain, direct launches, PVRS start.  Also runs the sample
+    through the batched forms and returns the largest relative difference of
+    the final states (equal error)."""
+    import torch
+    from paper_2602_21911_gb300 import grprec, inputs as I
+    ids = np.unique(np.linspace(0, args.domains - 1, args.plain_domains).astype(np.int64))
+    prob, avg, lm, lp = I.batched(args.domains, seed=2602, M=args.M, domains=ids)
+    doms = I.split_domains(prob, avg, lm, lp)
+    solvers = []
+    for pj, aj, mj, qj in doms:
+        sj = grprec.Solver(pj, device=device, stream=stream.cuda_stream)
+        sj.set_launch(grprec.GRP_LAUNCH_FLAT)
+        sj.set_graph(0)
+        sj.set_initial(aj, mj, qj)
+        sj.step(3)
+        solvers.append(sj)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for sj in solvers:
+        sj.step(args.plain_steps)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    upd = float(prob["n_cells"].sum()) * args.plain_steps
+    plain_state = np.concatenate([sj.get_state()[0] for sj in solvers], axis=1)
+    for sj in solvers:
+        sj.close()
+    # the batched forms on the same sample, same number of steps
+    diffs = {}
+    forms = [("batched_pvrs", grprec.GRP_GUESS_PVRS)]
+    if w is not None:
+        forms.append(("batched_learned", grprec.GRP_GUESS_MLP))
+    for name, guess in forms:
+        sb = grprec.Solver(prob, device=device, stream=stream.cuda_stream, guess=guess)
+        if guess == grprec.GRP_GUESS_MLP:
+            sb.set_guess_model(w, box)
+        sb.set_initial(avg, lm, lp)
+        sb.step(3 + args.plain_steps)
+        a = sb.get_state()[0]
+        sb.close()
+        diffs[name] = float((np.abs(a - plain_state).max(axis=1) / np.abs(plain_state).max(axis=1)).max())
+    return {"value": upd / el, "unit": UNIT,
+            "sample": "%d domains evenly spread over the batch (%d cells) x %d steps, one solver per domain, "
+                      "flat kernels, direct launches, PVRS start" % (len(ids), int(prob["n_cells"].sum()),
+                                                                     args.plain_steps)}, diffs
+
+
 def cpu_baseline(args, steps=100, stride=4):
     """The oracle as it stands, OpenMP over domains, on a bounded sample."""
     import oracle as O
@@ -199,7 +273,15 @@ def main():
     prob, avg, lm, lp = workload(args, rank)
     peak = grprec.grp_probe_fp64_peak(local)
     stream = torch.cuda.Stream()
-    s = grprec.Solver(prob, device=local, stream=stream.cuda_stream)
+    learned = args.guess == "learned"
+    w = box = None
+    guess_info = None
+    if learned:
+        w, box, guess_info = train_guess(args, local)
+    s = grprec.Solver(prob, device=local, stream=stream.cuda_stream,
+                      guess=grprec.GRP_GUESS_MLP if learned else grprec.GRP_GUESS_PVRS)
+    if learned:
+        s.set_guess_model(w, box)
     if args.launch == "tune":
         from paper_2602_21911_gb300 import autotune
         s.set_launch(*autotune.tune(prob, avg, lm, lp, device=local, use_cache=False))
@@ -256,6 +338,29 @@ def main():
     st_e2e, _ = s.get_stats()
     upd_e2e = float((st_e2e[:, 0].astype(np.float64) * prob["n_cells"]).sum())
     nsteps_e2e = args.warmup + args.steps
+    guess_stats = {"network_starts": int(st_e2e[:, grprec.STAT_GUESS_USED].sum()),
+                   "rejected": int(st_e2e[:, grprec.STAT_GUESS_REJECTED].sum()),
+                   "riemann_solves": int(st_e2e[:, grprec.STAT_RS_CALLS].sum()),
+                   "newton_iterations": int(st_e2e[:, grprec.STAT_NEWTON_SUM].sum())}
+
+    # the batched form with the PVRS start, same launch configuration (ablation)
+    pv_value = None
+    if learned:
+        sp = grprec.Solver(prob, device=local, stream=stream.cuda_stream, guess=grprec.GRP_GUESS_PVRS)
+        sp.set_launch(launch["form"], launch["threads"], launch["cells_per_block"], launch["steps_per_launch"])
+        sp.set_initial(avg, lm, lp)
+        sp.step(args.warmup)
+        st0, _ = sp.get_stats()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        sp.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        st1, _ = sp.get_stats()
+        pv_upd = float(((st1[:, 0] - st0[:, 0]).astype(np.float64) * prob["n_cells"]).sum())
+        pv_value = pv_upd / (ev0.elapsed_time(ev1) * 1e-3)
+        sp.close()
+    plain, equal = plain_arm(args, local, stream, w, box) if rank == 0 else (None, None)
     h2d = 8 * (h_avg.numel() + h_lm.numel() + h_lp.numel())
     d2h = 8 * (o_avg.numel() + o_if.numel() + o_t.numel())
     if rank != 0:
@@ -264,7 +369,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": tmax / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "batched Euler: %d domains x log-uniform 4..512 cells, M=%d, CFL 0.9, "
-                                   "transmissive, guess PVRS" % (args.domains, args.M),
+                                   "transmissive, %s" % (args.domains, args.M,
+                                                         "learned p* guess" if learned else "PVRS p* guess"),
                        "seed": 2602, "cells": int(prob["n_cells"].sum()), "launch": launch,
                        "l2": "state larger than L2 (no flush needed)"},
             "e2e": {"value": upd_e2e / e2e_s, "unit": UNIT,
@@ -272,7 +378,12 @@ def main():
             "gpu_launches": launches, "clocks": clk.summary(),
             "dominant_kernel": {"ms_total": flux_ms, "launches": flux_n,
                                 "share_of_timed_region": flux_ms / ms if ms > 0 else None},
-            "frozen_domains": int((status != 0).sum())}
+            "frozen_domains": int((status != 0).sum()),
+            "plain": plain, "batched_pvrs": {"value": pv_value, "unit": UNIT} if pv_value else None,
+            "equal_error": {"max_rel_diff_vs_plain": equal,
+                            "note": "final averages of the plain sample vs the batched forms on the same "
+                                    "domains and steps"} if equal else None,
+            "learned_guess": dict(guess_info or {}, **guess_stats) if learned else None}
     if launch["form"] == grprec.GRP_LAUNCH_FUSED:
         flops = STEP_FLOPS_PER_UPDATE.get(("batched", args.M))
         kname = "k_batch<Euler,M=%d> (%d steps per launch)" % (args.M, launch["steps_per_launch"])

@@ -198,6 +198,22 @@ def batched(n_domains=65536, seed=2602, M=2, cfl=0.9, gamma=1.4, domains=None):
     return prob, np.concatenate(avgs, axis=1), np.concatenate(minus, axis=1), np.concatenate(plus, axis=1)
 
 
+def split_domains(prob, avg, lim_minus, lim_plus, which=None):
+    """The domains of a multi-domain problem as single-domain problems
+    (prob, avg, lim_minus, lim_plus), for the domain positions ``which``."""
+    co, io = cell_offsets(prob), iface_offsets(prob)
+    out = []
+    for j in (range(len(prob["n_cells"])) if which is None else which):
+        pj = dict(prob)
+        for k in ("n_cells", "x_left", "x_right", "bc"):
+            pj[k] = np.asarray(prob[k])[j:j + 1].copy()
+        c = slice(int(co[j]), int(co[j + 1]))
+        f = slice(int(io[j]), int(io[j + 1]))
+        out.append((pj, np.ascontiguousarray(avg[:, c]), np.ascontiguousarray(lim_minus[:, f]),
+                    np.ascontiguousarray(lim_plus[:, f])))
+    return out
+
+
 def n_ifaces(prob):
     return int(np.sum(prob["n_cells"] + (prob["bc"] == TRANSMISSIVE)))
 
