@@ -409,6 +409,7 @@ constexpr int MLP_NIN = 6, MLP_NH = 64;
 constexpr int MLP_NPARAM = MLP_NIN * MLP_NH + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NH + 1;
 constexpr int MLP_GUESS_MAX_ITER = 8;     // Newton from the learned guess gives up after this
 constexpr float MLP_GATE = 0.5f;          // |ln(pL/pR)| or |du|/cbar above this: strong data
+constexpr double MLP_GATE_EXP = 1.6487212707001282;   // e^MLP_GATE
 constexpr double MLP_S_MIN = 1e-3;        // shock strength below which p_TR is the start
 constexpr double MLP_T_SCALE = -0.005;    // output scale: ln(p*/p_TR) = MLP_T_SCALE s^3 v
 constexpr float MLP_VMAX = 50.0f;         // |v| above this: prediction rejected
@@ -425,10 +426,18 @@ GRP_HD __forceinline__ float fast_tanh(float x)
 #endif
 }
 
-// Features x[6] and pbar; returns false for trivial data (no guess needed).
+// Features x[6] and pbar; returns false for data that are not strong (no
+// network), decided first without transcendental functions:
+// |ln(pL/pR)| > g  <=>  pL/pR outside [e^-g, e^g], and
+// |du|/cbar > g    <=>  du^4 rhoL rhoR > g^4 gamma^2 pL pR.
 GRP_HD __forceinline__ bool mlp_features(const Phys& ph, const Side& L, const Side& R, float x[6], double& pbar)
 {
-  const float lp = logf((float)(L.p * R.ip));
+  const double pr = L.p * R.ip, dun = R.u - L.u, du2 = dun * dun;
+  const double g2 = (double)MLP_GATE * (double)MLP_GATE;
+  const bool strong = pr > MLP_GATE_EXP || pr * MLP_GATE_EXP < 1.0 ||
+                      du2 * du2 * (L.r * R.r) > g2 * g2 * ph.gamma * ph.gamma * (L.p * R.p);
+  if (!strong) return false;
+  const float lp = logf((float)pr);
   const float lr = logf((float)(L.r * R.ir));
   pbar = sqrt(L.p * R.p);
   const double cbar = sqrt(ph.gamma * pbar * sqrt(L.ir * R.ir));
@@ -436,10 +445,14 @@ GRP_HD __forceinline__ bool mlp_features(const Phys& ph, const Side& L, const Si
   x[0] = 0.5f * lr; x[1] = -0.5f * lr;
   x[2] = 0.5f * lp; x[3] = -0.5f * lp;
   x[4] = -0.5f * du; x[5] = 0.5f * du;
-  return fabsf(lp) > MLP_GATE || fabsf(du) > MLP_GATE;
+  return true;
 }
 
-GRP_HD __forceinline__ float mlp_eval(const float* __restrict__ w, const float x[6])
+// The hidden activations live in local memory (the loops over neurons are not
+// unrolled): the network runs on a few strong-data interfaces only, and 64
+// activations in registers would raise the register count of every flux
+// kernel that contains this path.
+GRP_HD inline float mlp_eval(const float* __restrict__ w, const float x[6])
 {
   const float* W1 = w;
   const float* b1 = W1 + MLP_NIN * MLP_NH;
@@ -448,7 +461,7 @@ GRP_HD __forceinline__ float mlp_eval(const float* __restrict__ w, const float x
   const float* w3 = b2 + MLP_NH;
   const float b3 = w3[MLP_NH];
   float h1[MLP_NH];
-#pragma unroll
+#pragma unroll 1
   for (int j = 0; j < MLP_NH; ++j) {
     float z = b1[j];
 #pragma unroll
@@ -456,10 +469,10 @@ GRP_HD __forceinline__ float mlp_eval(const float* __restrict__ w, const float x
     h1[j] = fast_tanh(z);
   }
   float y = b3;
-#pragma unroll 4
+#pragma unroll 1
   for (int k = 0; k < MLP_NH; ++k) {
     float z = b2[k];
-#pragma unroll
+#pragma unroll 4
     for (int j = 0; j < MLP_NH; ++j) z = fmaf(h1[j], W2[j * MLP_NH + k], z);
     y = fmaf(fast_tanh(z), w3[k], y);
   }
@@ -474,6 +487,52 @@ struct RSInfo {
   bool has_x = false;            // strong data with a shock of strength >= MLP_S_MIN
   int guess = 0;                 // 0 not tried, 1 network start used, 2 rejected, 3 p_TR start (two rarefactions)
 };
+
+// The learned-guess path of riemann_state: features, the two-rarefaction base
+// and, for data with a shock, the network; Newton from that start.  Returns
+// the solver status, or -1 when no learned start was tried.  Kept out of line
+// so that its registers do not count against the flux kernels, which take
+// this path on a few strong-data interfaces only.
+template <bool G75>
+#ifdef __CUDA_ARCH__
+__device__ __noinline__
+#else
+inline
+#endif
+int learned_start(const Phys& ph, const Side& L, const Side& R, RSInfo& info, double& ps, double& us, int& iters)
+{
+  int st = -1;
+  const bool strong = mlp_features(ph, L, R, info.x, info.pbar);
+  const double base = strong ? trrs<G75>(ph, L, R) : 0.0;
+  const bool ok = strong && base > 0.0 && isfinite(base);
+  // shock strength s = ln(p_TR / min(pL, pR)); s <= 0: two rarefactions, and
+  // p_TR is p* up to rounding; s < MLP_S_MIN: |ln(p*/p_TR)| < 1e-11
+  const double sh = ok ? log(base / fmin(L.p, R.p)) : 0.0;
+  info.base = base;
+  info.s3 = sh * sh * sh;
+  info.has_x = ok && sh >= MLP_S_MIN;
+  if (ph.guess == 2 && ph.mlp_w && ok) {
+    double p0 = base;
+    bool go = true;
+    info.guess = 2;
+    if (info.has_x) {
+      bool inbox = true;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) inbox = inbox && info.x[i] >= ph.mlp_box[i] && info.x[i] <= ph.mlp_box[6 + i];
+      const float v = inbox ? mlp_eval(ph.mlp_w, info.x) : 0.0f;
+      const double y = MLP_T_SCALE * info.s3 * (double)v;
+      go = inbox && v == v && fabsf(v) <= MLP_VMAX && fabs(y) <= MLP_YMAX;
+      p0 = base * exp(y);
+    }
+    if (go) {
+      Phys pg = ph;
+      pg.max_iter = ph.max_iter < MLP_GUESS_MAX_ITER ? ph.max_iter : MLP_GUESS_MAX_ITER;
+      st = star_pressure<G75>(pg, L, R, p0, ps, us, iters);
+      if (st == ST_OK) info.guess = info.has_x ? 1 : 3;   // 3: p_TR start, not a network start
+    }
+  }
+  return st;
+}
 
 // Godunov state at x/t = 0 of conserved data QL | QR, as conserved Q and
 // primitive W.  allow_vacuum: vacuum data are sampled and ST_VACUUM returned
@@ -491,37 +550,7 @@ static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double
   double ps = 0.0, us = 0.0;
   int st = -1;
   iters = 0;
-  if (ph.features && info) {
-    const bool strong = mlp_features(ph, L, R, info->x, info->pbar);
-    const double base = strong ? trrs<G75>(ph, L, R) : 0.0;
-    const bool ok = strong && base > 0.0 && isfinite(base);
-    // shock strength s = ln(p_TR / min(pL, pR)); s <= 0: two rarefactions, and
-    // p_TR is p* up to rounding; s < MLP_S_MIN: |ln(p*/p_TR)| < 1e-11
-    const double sh = ok ? log(base / fmin(L.p, R.p)) : 0.0;
-    info->base = base;
-    info->s3 = sh * sh * sh;
-    info->has_x = ok && sh >= MLP_S_MIN;
-    if (ph.guess == 2 && ph.mlp_w && ok) {
-      double p0 = base;
-      bool go = true;
-      info->guess = 2;
-      if (info->has_x) {
-        bool inbox = true;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) inbox = inbox && info->x[i] >= ph.mlp_box[i] && info->x[i] <= ph.mlp_box[6 + i];
-        const float v = inbox ? mlp_eval(ph.mlp_w, info->x) : 0.0f;
-        const double y = MLP_T_SCALE * info->s3 * (double)v;
-        go = inbox && v == v && fabsf(v) <= MLP_VMAX && fabs(y) <= MLP_YMAX;
-        p0 = base * exp(y);
-      }
-      if (go) {
-        Phys pg = ph;
-        pg.max_iter = ph.max_iter < MLP_GUESS_MAX_ITER ? ph.max_iter : MLP_GUESS_MAX_ITER;
-        st = star_pressure<G75>(pg, L, R, p0, ps, us, iters);
-        if (st == ST_OK) info->guess = info->has_x ? 1 : 3;   // 3: p_TR start, not a network start
-      }
-    }
-  }
+  if (ph.features && info) st = learned_start<G75>(ph, L, R, *info, ps, us, iters);
   if (st != ST_OK && st != ST_VACUUM) {
     int it2 = 0;
     Phys pv = ph;
