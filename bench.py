@@ -284,7 +284,7 @@ def main():
         s.set_guess_model(w, box)
     if args.launch == "tune":
         from paper_2602_21911_gb300 import autotune
-        s.set_launch(*autotune.tune(prob, avg, lm, lp, device=local, use_cache=False))
+        autotune.tune(prob, avg, lm, lp, device=local, use_cache=False, solver=s)
     elif args.launch == "flat":
         s.set_launch(grprec.GRP_LAUNCH_FLAT)
     elif args.launch == "fused":

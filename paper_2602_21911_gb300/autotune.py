@@ -62,31 +62,54 @@ def _load():
         return {}
 
 
-def tune(prob, avg, lim_minus, lim_plus, device=0, steps=16, use_cache=True, verbose=False):
-    """Best (mode, threads, cells_per_block, steps_per_launch) for this problem."""
-    key = gpu_name(device) + "|" + signature(prob)
+def _time(s, avg, lim_minus, lim_plus, cfg, warm, steps):
+    s.set_launch(*cfg)
+    s.set_initial(avg, lim_minus, lim_plus)
+    s.step(warm)                               # warm-up (graph capture, first-launch set-up)
+    s.get_stats()
+    t0 = time.perf_counter()
+    s.step(steps)
+    s.get_stats()                              # synchronises
+    return (time.perf_counter() - t0) / steps
+
+
+def tune(prob, avg, lim_minus, lim_plus, device=0, warm=16, steps=32, finalists=3, use_cache=True,
+         verbose=False, solver=None):
+    """Best (mode, threads, cells_per_block, steps_per_launch) for this problem.
+    Every candidate runs `warm` steps, then `steps` timed steps, from the
+    initial data; the `finalists` fastest run again for 2 x `steps` and the
+    fastest of that round wins.  ``solver``: tune on this Solver (its guess
+    model and settings) instead of a new one; its launch configuration is left
+    at the winner and its state must be set again by the caller."""
+    key = gpu_name(device) + "|" + signature(prob) + ("|guess%d" % int(prob.get("guess", 0)))
     cache = _load() if use_cache else {}
     if key in cache:
-        return tuple(cache[key]["config"])
-    s = grprec.Solver(prob, device=device)
+        best = tuple(cache[key]["config"])
+        if solver is not None:
+            solver.set_launch(*best)
+        return best
+    s = solver or grprec.Solver(prob, device=device)
     results = []
     for cfg in candidates(prob):
-        s.set_launch(*cfg)
-        s.set_initial(avg, lim_minus, lim_plus)
-        s.step(max(cfg[3], 2))                 # warm-up (and first-launch set-up)
-        s.get_stats()
-        t0 = time.perf_counter()
-        s.step(steps)
-        s.get_stats()                          # synchronises
-        dt = time.perf_counter() - t0
+        dt = _time(s, avg, lim_minus, lim_plus, cfg, warm, steps)
         results.append((dt, cfg))
         if verbose:
-            print("autotune %-28s %8.3f ms/step" % (cfg, 1e3 * dt / steps))
-    s.close()
-    best = min(results)[1]
+            print("autotune %-28s %8.3f ms/step" % (cfg, 1e3 * dt))
+    results.sort()
+    final = []
+    for dt0, cfg in results[:finalists]:
+        dt = _time(s, avg, lim_minus, lim_plus, cfg, warm, 2 * steps)
+        final.append((dt, cfg))
+        if verbose:
+            print("autotune final %-22s %8.3f ms/step" % (cfg, 1e3 * dt))
+    best_dt, best = min(final)
+    if solver is None:
+        s.close()
+    else:
+        solver.set_launch(*best)
     if use_cache:
         cache = _load()
-        cache[key] = {"config": list(best), "ms_per_step": 1e3 * min(results)[0] / steps}
+        cache[key] = {"config": list(best), "ms_per_step": 1e3 * best_dt}
         try:
             os.makedirs(os.path.dirname(CACHE), exist_ok=True)
             with open(CACHE + ".tmp", "w") as f:

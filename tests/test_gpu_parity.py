@@ -249,3 +249,14 @@ def test_kernel_timing_through_graphs():
         assert n == 32 and ms > 0
         res[graph] = ms / n
     assert 0.5 < res[16] / res[0] < 2.0
+
+
+def test_autotuner_picks_a_candidate_and_leaves_results_unchanged():
+    from paper_2602_21911_gb300 import autotune, grprec
+    prob, avg, lm, lp = I.batched(domains=np.arange(0, 65536, 97)[:600])
+    s = grprec.Solver(prob)
+    best = autotune.tune(prob, avg, lm, lp, warm=2, steps=4, use_cache=False, solver=s)
+    assert best in autotune.candidates(prob)
+    L = s.get_launch()
+    assert (L["form"], L["threads"], L["cells_per_block"], L["steps_per_launch"]) == best
+    check_parity(prob, avg, lm, lp, 20, DISC_TOL, solver=s)
