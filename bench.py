@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--launch", default="tune", choices=["tune", "auto", "flat", "fused", "split"],
                     help="launch configuration: autotuned (default), library default, or forced")
     ap.add_argument("--guess", default="learned", choices=["learned", "pvrs"])
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="N > 1: a batch per rank (weak) or one batch split across the ranks (strong)")
     ap.add_argument("--plain-domains", type=int, default=128, help="sample size of the plain form")
     ap.add_argument("--plain-steps", type=int, default=60)
     return ap.parse_args()
@@ -141,10 +143,15 @@ def profiled_traffic(cells, kname):
     return float(kv["dram_bytes_per_launch"]) * cells / float(kv["cells_per_launch"])
 
 
-def workload(args, rank):
-    from paper_2602_21911_gb300 import inputs as I
-    prob, avg, lm, lp = I.batched(args.domains, seed=2602 + rank, M=args.M)
-    return prob, avg, lm, lp
+def workload(args, rank, world):
+    """Weak scaling: every rank advances its own batch (seed 2602 + rank).
+    Strong scaling: the ranks split one batch (seed 2602) by longest-first
+    balancing of the cell counts."""
+    from paper_2602_21911_gb300 import dist as D, inputs as I
+    if args.scaling == "strong" and world > 1:
+        part = D.lpt_partition(I.batched_params(args.domains, 2602)["n"], world)[rank]
+        return I.batched(args.domains, seed=2602, M=args.M, domains=part)
+    return I.batched(args.domains, seed=2602 + rank, M=args.M)
 
 
 def train_guess(args, device):
@@ -270,7 +277,7 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     from paper_2602_21911_gb300 import grprec
-    prob, avg, lm, lp = workload(args, rank)
+    prob, avg, lm, lp = workload(args, rank, world)
     peak = grprec.grp_probe_fp64_peak(local)
     stream = torch.cuda.Stream()
     learned = args.guess == "learned"
@@ -313,13 +320,8 @@ def main():
     launches = s.launch_count() - launches0
     stats1, status = s.get_stats()
     upd = float(((stats1[:, 0] - stats0[:, 0]).astype(np.float64) * prob["n_cells"]).sum())
-    tmax = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, upd], device="cuda", dtype=torch.float64)
-        mx = t.clone(); dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
-        sm = t.clone(); dist.all_reduce(sm[1:], op=dist.ReduceOp.SUM)
-        tmax, upd = float(mx[0]), float(sm[1])
+    from paper_2602_21911_gb300 import dist as D
+    tmax, upd = D.reduce_time_and_work(ms, upd, device="cuda")
     value = upd / (tmax * 1e-3)
 
     # end to end through the public API with pinned host buffers
@@ -330,6 +332,8 @@ def main():
     o_if = torch.empty((s.C, s.nif), dtype=torch.float64).pin_memory()
     o_t = torch.empty(s.D, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     t0 = time.perf_counter()
     s.set_initial(h_avg, h_lm, h_lp)
     s.step(args.warmup + args.steps)
@@ -337,6 +341,8 @@ def main():
     e2e_s = time.perf_counter() - t0
     st_e2e, _ = s.get_stats()
     upd_e2e = float((st_e2e[:, 0].astype(np.float64) * prob["n_cells"]).sum())
+    e2e_ms, upd_e2e = D.reduce_time_and_work(1e3 * e2e_s, upd_e2e, device="cuda")
+    e2e_s = 1e-3 * e2e_ms
     nsteps_e2e = args.warmup + args.steps
     guess_stats = {"network_starts": int(st_e2e[:, grprec.STAT_GUESS_USED].sum()),
                    "rejected": int(st_e2e[:, grprec.STAT_GUESS_REJECTED].sum()),
@@ -358,7 +364,8 @@ def main():
         torch.cuda.synchronize()
         st1, _ = sp.get_stats()
         pv_upd = float(((st1[:, 0] - st0[:, 0]).astype(np.float64) * prob["n_cells"]).sum())
-        pv_value = pv_upd / (ev0.elapsed_time(ev1) * 1e-3)
+        pv_ms, pv_upd = D.reduce_time_and_work(ev0.elapsed_time(ev1), pv_upd, device="cuda")
+        pv_value = pv_upd / (pv_ms * 1e-3)
         sp.close()
     plain, equal = plain_arm(args, local, stream, w, box) if rank == 0 else (None, None)
     h2d = 8 * (h_avg.numel() + h_lm.numel() + h_lp.numel())
@@ -367,7 +374,7 @@ def main():
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tmax / max(args.steps, 1), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": args.scaling, "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "batched Euler: %d domains x log-uniform 4..512 cells, M=%d, CFL 0.9, "
                                    "transmissive, %s" % (args.domains, args.M,
                                                          "learned p* guess" if learned else "PVRS p* guess"),

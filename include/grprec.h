@@ -251,7 +251,7 @@ int grp_mlp_adam(float *weights, const float *grad, float *m, float *v, int step
 
 /*
  * Leading-term Riemann problems in bulk: the exact ideal-gas solver of the
- * flux kernel (Toro-Titarev GRP, Section 2.2: Newton on the star pressure to a
+ * flux kernel (Toro-Titarev GRP, Section 2: Newton on the star pressure to a
  * relative change below newton_rtol, then one more iteration) applied to n
  * independent pairs of conserved states, from the start `guess` (GRP_GUESS_*;
  * GRP_GUESS_MLP needs `weights` and `box` as for grp_set_guess_model, device

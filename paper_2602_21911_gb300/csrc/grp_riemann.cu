@@ -1,6 +1,6 @@
 // grp_riemann_batch: independent leading-term Riemann problems of the ideal
 // gas solved in bulk with the solver of the flux kernel (exact solver of
-// Section 2.2: Newton on the star pressure, relative change below rtol plus
+// Section 2: Newton on the star pressure, relative change below rtol plus
 // one more iteration), from a chosen Newton start.  It serves users who need
 // the exact solver alone, and measures what each start costs in iterations.
 #include <cuda_runtime.h>
