@@ -36,6 +36,7 @@ struct grp_ctx {
   int *nstep = nullptr, *status = nullptr;
   unsigned long long* smax_bits = nullptr;
   int *bad = nullptr, *inad = nullptr, *fail = nullptr, *any_bad = nullptr;
+  int *tlist0 = nullptr, *tlist1 = nullptr, *ilist = nullptr, *lcount = nullptr;   // repair work lists
   unsigned long long* stats = nullptr;
   double* scratch_norm = nullptr;
   float *mlp = nullptr, *mlp_norm = nullptr;     // learned guess: weights, input box (library-owned)
@@ -111,7 +112,8 @@ void free_all(grp_ctx* c)
   c->ev_pending.clear();
   void* ptrs[] = {c->cell_off, c->if_off, c->cell_dom, c->if_dom, c->dx, c->bc, c->avg[0], c->avg[1],
                   c->ifc[0], c->ifc[1], c->flux, c->low, c->troubled, c->t, c->dt_prev, c->nstep,
-                  c->status, c->smax_bits, c->bad, c->inad, c->fail, c->any_bad, c->stats,
+                  c->status, c->smax_bits, c->bad, c->inad, c->fail, c->any_bad, c->tlist0, c->tlist1,
+                  c->ilist, c->lcount, c->stats,
                   c->scratch_norm, c->mlp, c->mlp_norm, c->grp};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -152,6 +154,10 @@ StepArgs make_args(const grp_ctx* c, double t_end)
   a.inad = c->inad;
   a.fail = c->fail;
   a.any_bad = c->any_bad;
+  a.tlist[0] = c->tlist0;
+  a.tlist[1] = c->tlist1;
+  a.ilist = c->ilist;
+  a.lcount = c->lcount;
   a.stats = c->stats;
   a.ph.mlp_w = c->mlp;
   a.ph.mlp_box = c->mlp_norm;
@@ -316,10 +322,11 @@ int enqueue_step(grp_ctx* c, double t_end)
   if (euler) {
     k_update<SYS_EULER><<<blocks(c->ncell, 256), 256, 0, s>>>(a, -1);
     c->launches++;
+    // repair rounds over the compacted lists of troubled cells and repaired interfaces
     for (int r = 0; r < MAX_REPAIR; ++r) {
-      if (c->p.gamma == 1.4) k_repair_flux<true><<<blocks(c->nif, 128), 128, 0, s>>>(a, r);
-      else k_repair_flux<false><<<blocks(c->nif, 128), 128, 0, s>>>(a, r);
-      k_update<SYS_EULER><<<blocks(c->ncell, 256), 256, 0, s>>>(a, r);
+      if (c->p.gamma == 1.4) k_repair_list<true><<<LIST_BLOCKS, LIST_THREADS, 0, s>>>(a, r);
+      else k_repair_list<false><<<LIST_BLOCKS, LIST_THREADS, 0, s>>>(a, r);
+      k_update_list<SYS_EULER><<<LIST_BLOCKS, LIST_THREADS, 0, s>>>(a, r);
       c->launches += 2;
     }
   } else {
@@ -425,6 +432,7 @@ int grp_create(grp_ctx** out, const grp_problem* p)
   AL(flux, C * c->nif) AL(low, c->nif) AL(troubled, c->ncell) AL(t, D) AL(dt_prev, D) AL(nstep, D)
   AL(status, D) AL(smax_bits, D) AL(bad, (MAX_REPAIR + 1) * D) AL(inad, D) AL(fail, D)
   AL(any_bad, MAX_REPAIR + 1) AL(stats, (long long)NSTATS * D) AL(scratch_norm, 3 * D)
+  AL(tlist0, c->ncell) AL(tlist1, c->ncell) AL(ilist, c->nif) AL(lcount, 2 * (MAX_REPAIR + 1))
 #undef AL
   struct Cp { void* dst; const void* src; size_t n; } cps[] = {
       {c->cell_off, c->h_cell_off.data(), sizeof(long long) * (D + 1)},

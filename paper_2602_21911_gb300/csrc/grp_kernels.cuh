@@ -3,9 +3,10 @@
 // One step is a short fixed sequence of launches on the context's stream:
 //   k_smax         per cell   S_max of every domain (warp max + atomicMax)
 //   k_flux<M>      per iface  GRPrec traces -> GRP -> flux, new interface data
-//   k_update       per cell   candidate averages, admissibility flags
-//   k_repair_flux  per iface  (only troubled domains) first-order fluxes
-//   k_repair_upd   per cell   (only troubled domains) candidates again
+//   k_update       per cell   candidate averages, detection flags, list of troubled cells
+//   k_repair_list  per listed troubled cell: first-order fluxes on its interfaces
+//   k_update_list  per listed repaired interface: candidates of its cells again
+//                  (the last two MAX_REPAIR times, on fixed grids)
 //   k_finish       per domain time, step count, status, buffer bookkeeping
 // Every kernel derives dt from the same per-domain words with the same
 // expression, so no extra launch is needed to publish it.
@@ -51,6 +52,12 @@ struct StepArgs {
   int* inad;                         // [D] number of inadmissible candidate averages
   int* fail;                         // [D] non-zero: solver failure code this step
   int* any_bad;                      // [MAX_REPAIR+1] any domain troubled after pass p
+  // repair work lists of the flat form (compacted: the rounds touch only the
+  // troubled cells and their interfaces)
+  int* tlist[2];                     // [ncell] troubled cells after pass p-1, in tlist[p & 1]
+  int* ilist;                        // [nif] interfaces repaired in the current round
+  int* lcount;                       // [2 (MAX_REPAIR+1)]: troubled cells after pass p-1 at [p];
+                                     //   interfaces repaired in round r at [MAX_REPAIR + 1 + r]
   unsigned long long* stats;         // [D][NSTATS]
   // harvest of (features, ln(p*/pbar), iterations) records, may be null
   float* harvest;                    // [harvest_cap][8]
@@ -148,6 +155,7 @@ static __global__ void k_smax(StepArgs a)
 {
   const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (blockIdx.x == 0 && threadIdx.x <= MAX_REPAIR) a.any_bad[threadIdx.x] = 0;
+  if (blockIdx.x == 0 && threadIdx.x < 2 * (MAX_REPAIR + 1) && a.lcount) a.lcount[threadIdx.x] = 0;
   const bool valid = gi < a.ncell;
   if (valid && gi == a.cell_off[a.cell_dom[gi]]) reset_domain_words(a, a.cell_dom[gi]);
   if (a.sys != SYS_EULER) return;                  // uniform
@@ -413,13 +421,114 @@ __global__ void k_update(StepArgs a, int pass)
   if (pass >= 0 && a.any_bad[pass] == 0) return;
   if (gi >= a.ncell) return;
   const int d = a.cell_dom[gi];
-  if (update_one<SYS>(a, gi, d, pass) & 1) a.any_bad[pass + 1] = 1;
+  const bool bad = update_one<SYS>(a, gi, d, pass) & 1;
+  if (bad) a.any_bad[pass + 1] = 1;
+  if (pass < 0 && a.lcount) {
+    // warp-aggregated append of the troubled cells to the first work list
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, bad);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      int base = 0;
+      if (lane_id() == leader) base = atomicAdd(a.lcount, __popc(m));
+      base = __shfl_sync(act, base, leader);
+      if (bad) a.tlist[0][base + __popc(m & ((1u << lane_id()) - 1u))] = (int)gi;
+    }
+  }
+}
+
+// Grid-stride helpers of the work-list kernels (their grids are fixed, so a
+// captured graph serves every step).
+constexpr int LIST_BLOCKS = 4 * 152, LIST_THREADS = 128;
+
+// First-order Godunov flux at the domain-local interface j (round `pass`),
+// unless the interface is already low; appends it to the round's interface list.
+template <bool G75>
+__device__ __forceinline__ void repair_iface(const StepArgs& a, int pass, int d, long long c0, long long i0, int N,
+                                             int bc, int j)
+{
+  const long long gj = i0 + j;
+  if (a.low[gj]) return;
+  double F[3], Q0[3];
+  int iters = 0;
+  const int rs = first_order<G75>(a, c0, N, bc, j, F, Q0, iters);
+  unsigned long long* S = a.stats + (long long)d * NSTATS;
+  atomicAdd(S + S_NEWTON_SUM, (unsigned long long)iters);
+  atomicMax(S + S_NEWTON_MAX, (unsigned long long)iters);
+  atomicAdd(S + S_RS_CALLS, 1ull);
+  atomicAdd(S + S_LOW, 1ull);
+  if (rs != ST_OK) { atomicExch(a.fail + d, rs); return; }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    a.flux[c * a.nif + gj] = F[c];
+    a.ifc_new[c * a.nif + gj] = Q0[c];
+  }
+  a.low[gj] = (unsigned char)(2 + pass);
+  a.ilist[atomicAdd(a.lcount + MAX_REPAIR + 1 + pass, 1)] = (int)gj;
+}
+
+// Round `pass` of the repair from the list of troubled cells: each troubled
+// cell repairs its right interface, and its left one unless the left cell is
+// troubled too (that cell repairs it as its right interface, or did so in an
+// earlier round); interfaces repaired before are skipped.
+template <bool G75>
+__global__ void __launch_bounds__(LIST_THREADS) k_repair_list(StepArgs a, int pass)
+{
+  const int n = a.lcount[pass];
+  const int* L = a.tlist[pass & 1];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const long long gi = L[k];
+    const int d = a.cell_dom[gi];
+    const long long c0 = a.cell_off[d], i0 = a.if_off[d];
+    const int N = (int)(a.cell_off[d + 1] - c0);
+    const int bc = a.bc[d];
+    const int i = (int)(gi - c0);
+    const int jr = bc == 0 ? (i == N - 1 ? 0 : i + 1) : i + 1;
+    const int il = bc == 0 ? (i == 0 ? N - 1 : i - 1) : i - 1;      // -1: the ghost
+    repair_iface<G75>(a, pass, d, c0, i0, N, bc, jr);
+    if (il < 0 || !a.troubled[c0 + il]) repair_iface<G75>(a, pass, d, c0, i0, N, bc, i);
+  }
+}
+
+// Re-update after round `pass` from the list of repaired interfaces.  The
+// cells next to interface j are its right cell (whose left interface is j)
+// and its left cell; the left cell is left to its own left interface when
+// that was repaired in this round too, so every cell is updated once.
+// Troubled results go to the next round's cell list.
+template <int SYS>
+__global__ void __launch_bounds__(LIST_THREADS) k_update_list(StepArgs a, int pass)
+{
+  const int n = a.lcount[MAX_REPAIR + 1 + pass];
+  const unsigned char mark = (unsigned char)(2 + pass);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const long long gj = a.ilist[k];
+    const int d = a.if_dom[gj];
+    const long long c0 = a.cell_off[d], i0 = a.if_off[d];
+    const int N = (int)(a.cell_off[d + 1] - c0);
+    const int bc = a.bc[d];
+    const int j = (int)(gj - i0);
+    int cl, cr;
+    if (bc == 0) { cl = j == 0 ? N - 1 : j - 1; cr = j; }
+    else { cl = j - 1; cr = j == N ? -1 : j; }
+    int cells[2], nc = 0;
+    if (cr >= 0) cells[nc++] = cr;
+    if (cl >= 0 && a.low[i0 + cl] != mark) cells[nc++] = cl;
+    for (int q = 0; q < nc; ++q) {
+      const long long gi = c0 + cells[q];
+      if (update_one<SYS>(a, gi, d, pass) & 1) {
+        a.any_bad[pass + 1] = 1;
+        if (pass + 1 <= MAX_REPAIR) a.tlist[(pass + 1) & 1][atomicAdd(a.lcount + pass + 1, 1)] = (int)gi;
+      }
+    }
+  }
 }
 
 // ------------------------------------------------------------------ repair
 // Interfaces of troubled cells (inadmissible, or outside the relaxed discrete
 // maximum principle) take the first-order Godunov flux (a-posteriori,
-// MOOD-like, bounded to MAX_REPAIR rounds).
+// MOOD-like, bounded to MAX_REPAIR rounds).  repair_one is the sweep form of
+// the block-local kernels (k_batch, k_post); the flat form runs the rounds
+// from work lists (k_repair_list, k_update_list).
 template <bool G75>
 static __device__ __forceinline__ void repair_one(const StepArgs& a, int pass, long long gj, int d, unsigned st[3])
 {
@@ -446,24 +555,6 @@ static __device__ __forceinline__ void repair_one(const StepArgs& a, int pass, l
     a.ifc_new[c * a.nif + gj] = Q0[c];
   }
   a.low[gj] = (unsigned char)(2 + pass);
-}
-
-template <bool G75>
-__global__ void __launch_bounds__(128) k_repair_flux(StepArgs a, int pass)
-{
-  if (a.any_bad[pass] == 0) return;          // uniform over the grid
-  const long long gj = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned st[3] = {0u, 0u, 0u};
-  int d = -1;
-  if (gj < a.nif) {
-    d = a.if_dom[gj];
-    repair_one<G75>(a, pass, gj, d, st);
-  }
-  __syncwarp();
-  warp_stat_add(a.stats, d, S_NEWTON_SUM, st[0]);
-  warp_stat_max(a.stats, d, S_NEWTON_MAX, st[0]);
-  warp_stat_add(a.stats, d, S_RS_CALLS, st[1]);
-  warp_stat_add(a.stats, d, S_LOW, st[1]);
 }
 
 // ------------------------------------------------------------------ finish

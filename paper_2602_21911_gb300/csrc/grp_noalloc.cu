@@ -30,7 +30,10 @@ constexpr size_t OFF_LOW = align256(OFF_FLUX + sizeof(double) * 3 * NA_IFACES);
 constexpr size_t OFF_TROUBLED = align256(OFF_LOW + NA_IFACES);
 constexpr size_t OFF_CELL_DOM = align256(OFF_TROUBLED + NA_CELLS);
 constexpr size_t OFF_IF_DOM = align256(OFF_CELL_DOM + sizeof(int) * NA_CELLS);
-constexpr size_t OFF_WORDS = align256(OFF_IF_DOM + sizeof(int) * NA_IFACES);
+constexpr size_t OFF_TLIST0 = align256(OFF_IF_DOM + sizeof(int) * NA_IFACES);
+constexpr size_t OFF_TLIST1 = align256(OFF_TLIST0 + sizeof(int) * NA_CELLS);
+constexpr size_t OFF_ILIST = align256(OFF_TLIST1 + sizeof(int) * NA_CELLS);
+constexpr size_t OFF_WORDS = align256(OFF_ILIST + sizeof(int) * NA_IFACES);
 
 // per-domain words of the single domain, in one struct
 struct Words {
@@ -40,6 +43,7 @@ struct Words {
   unsigned long long stats[NSTATS];
   int nstep, status, fail;
   int bad[MAX_REPAIR + 1], inad, any_bad[MAX_REPAIR + 1];
+  int lcount[2 * (MAX_REPAIR + 1)];
   unsigned char bc;
 };
 constexpr size_t SCRATCH_BYTES = align256(OFF_WORDS + sizeof(Words));
@@ -67,6 +71,7 @@ __global__ void k_noalloc_setup(unsigned char* base, int N, int nif, double dx, 
     for (int k = 0; k < NSTATS; ++k) w->stats[k] = 0ull;
     w->nstep = 0; w->status = 0; w->fail = 0;
     for (int p = 0; p <= MAX_REPAIR; ++p) { w->bad[p] = 0; w->any_bad[p] = 0; }
+    for (int p = 0; p < 2 * (MAX_REPAIR + 1); ++p) w->lcount[p] = 0;
     w->inad = 0;
     w->bc = (unsigned char)bc;
   }
@@ -134,6 +139,8 @@ extern "C" int grp_step_noalloc(int system, double lambda, double gamma, int M, 
   a.t = &w->t; a.dt_prev = &w->dt_prev; a.nstep = &w->nstep; a.status = &w->status;
   a.smax_bits = &w->smax_bits;
   a.bad = w->bad; a.inad = &w->inad; a.fail = &w->fail; a.any_bad = w->any_bad;
+  a.tlist[0] = (int*)(base + OFF_TLIST0); a.tlist[1] = (int*)(base + OFF_TLIST1);
+  a.ilist = (int*)(base + OFF_ILIST); a.lcount = w->lcount;
   a.stats = w->stats;
   a.harvest = nullptr; a.harvest_count = nullptr; a.harvest_cap = 0; a.harvest_log2_stride = 0;
 
@@ -144,9 +151,9 @@ extern "C" int grp_step_noalloc(int system, double lambda, double gamma, int M, 
   if (euler) {
     k_update<SYS_EULER><<<nblk(N, 256), 256, 0, s>>>(a, -1);
     for (int r = 0; r < MAX_REPAIR; ++r) {
-      if (gamma == 1.4) k_repair_flux<true><<<nblk(nif, 128), 128, 0, s>>>(a, r);
-      else k_repair_flux<false><<<nblk(nif, 128), 128, 0, s>>>(a, r);
-      k_update<SYS_EULER><<<nblk(N, 256), 256, 0, s>>>(a, r);
+      if (gamma == 1.4) k_repair_list<true><<<LIST_BLOCKS, LIST_THREADS, 0, s>>>(a, r);
+      else k_repair_list<false><<<LIST_BLOCKS, LIST_THREADS, 0, s>>>(a, r);
+      k_update_list<SYS_EULER><<<LIST_BLOCKS, LIST_THREADS, 0, s>>>(a, r);
     }
   } else {
     k_update<SYS_ADV><<<nblk(N, 256), 256, 0, s>>>(a, -1);
