@@ -31,6 +31,7 @@ struct grp_ctx {
   double* avg[2] = {nullptr, nullptr};
   double* ifc[2] = {nullptr, nullptr};
   double* flux = nullptr;
+  double* pold = nullptr;        // pressure of the current averages (S_max pass)
   unsigned char *low = nullptr, *troubled = nullptr;
   double *t = nullptr, *dt_prev = nullptr;
   int *nstep = nullptr, *status = nullptr;
@@ -111,7 +112,7 @@ void free_all(grp_ctx* c)
   c->ev_free.clear();
   c->ev_pending.clear();
   void* ptrs[] = {c->cell_off, c->if_off, c->cell_dom, c->if_dom, c->dx, c->bc, c->avg[0], c->avg[1],
-                  c->ifc[0], c->ifc[1], c->flux, c->low, c->troubled, c->t, c->dt_prev, c->nstep,
+                  c->ifc[0], c->ifc[1], c->flux, c->pold, c->low, c->troubled, c->t, c->dt_prev, c->nstep,
                   c->status, c->smax_bits, c->bad, c->inad, c->fail, c->any_bad, c->tlist0, c->tlist1,
                   c->ilist, c->lcount, c->stats,
                   c->scratch_norm, c->mlp, c->mlp_norm, c->grp};
@@ -143,6 +144,7 @@ StepArgs make_args(const grp_ctx* c, double t_end)
   a.ifc = c->ifc[c->cur];
   a.ifc_new = c->ifc[c->cur ^ 1];
   a.flux = c->flux;
+  a.pold = c->pold;
   a.low = c->low;
   a.troubled = c->troubled;
   a.t = c->t;
@@ -429,7 +431,7 @@ int grp_create(grp_ctx** out, const grp_problem* p)
   }
   AL(cell_off, D + 1) AL(if_off, D + 1) AL(cell_dom, c->ncell) AL(if_dom, c->nif) AL(dx, D) AL(bc, D)
   AL(avg[0], C * c->ncell) AL(avg[1], C * c->ncell) AL(ifc[0], C * c->nif) AL(ifc[1], C * c->nif)
-  AL(flux, C * c->nif) AL(low, c->nif) AL(troubled, c->ncell) AL(t, D) AL(dt_prev, D) AL(nstep, D)
+  AL(flux, C * c->nif) AL(pold, c->ncell) AL(low, c->nif) AL(troubled, c->ncell) AL(t, D) AL(dt_prev, D) AL(nstep, D)
   AL(status, D) AL(smax_bits, D) AL(bad, (MAX_REPAIR + 1) * D) AL(inad, D) AL(fail, D)
   AL(any_bad, MAX_REPAIR + 1) AL(stats, (long long)NSTATS * D) AL(scratch_norm, 3 * D)
   AL(tlist0, c->ncell) AL(tlist1, c->ncell) AL(ilist, c->nif) AL(lcount, 2 * (MAX_REPAIR + 1))

@@ -40,6 +40,7 @@ struct StepArgs {
   const double* ifc;                 // current interface data [C][nif]
   double* ifc_new;                   // next interface data    [C][nif]
   double* flux;                      // scratch [C][nif]
+  double* pold;                      // [ncell] pressure of the current averages, written with S_max
   unsigned char* low;                // [nif] 0 high order; 1 first order (flux kernel); 2+r repaired in round r
   unsigned char* troubled;           // [ncell] 0 ok; 1 outside the relaxed DMP; 2 inadmissible
   // per-domain words
@@ -132,6 +133,7 @@ __device__ __forceinline__ void smax_cell(const StepArgs& a, long long gi, bool 
     const double r = a.avg[gi], m = a.avg[a.ncell + gi], E = a.avg[2 * a.ncell + gi];
     const double u = __ddiv_rn(m, r);
     const double p = __dmul_rn(g - 1.0, __dadd_rn(E, -__dmul_rn(__dmul_rn(0.5, m), u)));
+    a.pold[gi] = p;                                // for the discrete maximum principle of the update
     double sp = __dadd_rn(fabs(u), __dsqrt_rn(__ddiv_rn(__dmul_rn(g, p), r)));
     if (!(sp >= 0.0)) sp = 0.0;
     bits = (unsigned long long)__double_as_longlong(sp);
@@ -399,10 +401,11 @@ __device__ __forceinline__ int update_one(const StepArgs& a, long long gi, int d
     double lo0 = 0.0, hi0 = 0.0, lo1 = 0.0, hi1 = 0.0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
+      // old density and pressure (the pressure as reduced with S_max)
       const long long q = c0 + nb[k];
-      const Prim w = to_prim(g, a.avg[q], a.avg[a.ncell + q], a.avg[2 * a.ncell + q]);
-      lo0 = k == 0 ? w.r : fmin(lo0, w.r); hi0 = k == 0 ? w.r : fmax(hi0, w.r);
-      lo1 = k == 0 ? w.p : fmin(lo1, w.p); hi1 = k == 0 ? w.p : fmax(hi1, w.p);
+      const double r = a.avg[q], pr = a.pold[q];
+      lo0 = k == 0 ? r : fmin(lo0, r); hi0 = k == 0 ? r : fmax(hi0, r);
+      lo1 = k == 0 ? pr : fmin(lo1, pr); hi1 = k == 0 ? pr : fmax(hi1, pr);
     }
     const Prim wc = to_prim(g, Q[0], Q[1], Q[2]);
     const double d0 = DMP_REL * fmax(fabs(lo0), fabs(hi0)), d1 = DMP_REL * fmax(fabs(lo1), fabs(hi1));
