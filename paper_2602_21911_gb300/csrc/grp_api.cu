@@ -32,6 +32,7 @@ struct grp_ctx {
   double* ifc[2] = {nullptr, nullptr};
   double* flux = nullptr;
   double* pold = nullptr;        // pressure of the current averages (S_max pass)
+  DomStep* ds = nullptr;         // per-domain time step of the current step
   unsigned char *low = nullptr, *troubled = nullptr;
   double *t = nullptr, *dt_prev = nullptr;
   int *nstep = nullptr, *status = nullptr;
@@ -112,7 +113,7 @@ void free_all(grp_ctx* c)
   c->ev_free.clear();
   c->ev_pending.clear();
   void* ptrs[] = {c->cell_off, c->if_off, c->cell_dom, c->if_dom, c->dx, c->bc, c->avg[0], c->avg[1],
-                  c->ifc[0], c->ifc[1], c->flux, c->pold, c->low, c->troubled, c->t, c->dt_prev, c->nstep,
+                  c->ifc[0], c->ifc[1], c->flux, c->pold, c->ds, c->low, c->troubled, c->t, c->dt_prev, c->nstep,
                   c->status, c->smax_bits, c->bad, c->inad, c->fail, c->any_bad, c->tlist0, c->tlist1,
                   c->ilist, c->lcount, c->stats,
                   c->scratch_norm, c->mlp, c->mlp_norm, c->grp};
@@ -145,6 +146,7 @@ StepArgs make_args(const grp_ctx* c, double t_end)
   a.ifc_new = c->ifc[c->cur ^ 1];
   a.flux = c->flux;
   a.pold = c->pold;
+  a.ds = c->ds;
   a.low = c->low;
   a.troubled = c->troubled;
   a.t = c->t;
@@ -270,7 +272,8 @@ int enqueue_split(grp_ctx* c, double t_end)
   cudaStream_t s = c->stream;
   if (!c->smax_ready) {
     k_smax<<<blocks(c->ncell, 256), 256, 0, s>>>(a);
-    c->launches++;
+    k_dt<<<blocks(c->D, 128), 128, 0, s>>>(a);
+    c->launches += 2;
     c->smax_ready = true;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -306,6 +309,8 @@ int enqueue_step(grp_ctx* c, double t_end)
     k_smax<<<blocks(c->ncell, 256), 256, 0, s>>>(a);
     c->launches++;
   }
+  k_dt<<<blocks(c->D, 128), 128, 0, s>>>(a);
+  c->launches++;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing) {
     for (cudaEvent_t* e : {&e0, &e1}) {
@@ -431,7 +436,7 @@ int grp_create(grp_ctx** out, const grp_problem* p)
   }
   AL(cell_off, D + 1) AL(if_off, D + 1) AL(cell_dom, c->ncell) AL(if_dom, c->nif) AL(dx, D) AL(bc, D)
   AL(avg[0], C * c->ncell) AL(avg[1], C * c->ncell) AL(ifc[0], C * c->nif) AL(ifc[1], C * c->nif)
-  AL(flux, C * c->nif) AL(pold, c->ncell) AL(low, c->nif) AL(troubled, c->ncell) AL(t, D) AL(dt_prev, D) AL(nstep, D)
+  AL(flux, C * c->nif) AL(pold, c->ncell) AL(ds, D) AL(low, c->nif) AL(troubled, c->ncell) AL(t, D) AL(dt_prev, D) AL(nstep, D)
   AL(status, D) AL(smax_bits, D) AL(bad, (MAX_REPAIR + 1) * D) AL(inad, D) AL(fail, D)
   AL(any_bad, MAX_REPAIR + 1) AL(stats, (long long)NSTATS * D) AL(scratch_norm, 3 * D)
   AL(tlist0, c->ncell) AL(tlist1, c->ncell) AL(ilist, c->nif) AL(lcount, 2 * (MAX_REPAIR + 1))

@@ -21,6 +21,12 @@ enum { S_STEPS = 0, S_NEWTON_SUM, S_NEWTON_MAX, S_RECON_FB, S_FLUX_FB, S_RS_CALL
 constexpr int MAX_REPAIR = 4;   // rounds of the a-posteriori first-order repair
 constexpr double DMP_REL = 1e-2; // relaxation of the discrete maximum principle
 
+// This step's time step of one domain, computed once per step after S_max.
+struct DomStep {
+  double dt, nu, dt_cfl;             // dt (clipped at t_end), dt / dx, the CFL dt kept for dt_hold
+  int active, last;                  // the domain steps; this step reaches t_end
+};
+
 struct StepArgs {
   int sys, M, C;
   Phys ph;
@@ -41,6 +47,7 @@ struct StepArgs {
   double* ifc_new;                   // next interface data    [C][nif]
   double* flux;                      // scratch [C][nif]
   double* pold;                      // [ncell] pressure of the current averages, written with S_max
+  DomStep* ds;                       // [D] this step's time step of every domain (k_dt or in-block)
   unsigned char* low;                // [nif] 0 high order; 1 first order (flux kernel); 2+r repaired in round r
   unsigned char* troubled;           // [ncell] 0 ok; 1 outside the relaxed DMP; 2 inadmissible
   // per-domain words
@@ -89,22 +96,44 @@ __device__ __forceinline__ void warp_stat_max(unsigned long long* stats, int d, 
 
 // Time-step rule (Section 4.1): dt = C dx / S_max, recomputed every dt_hold
 // steps, the last step clipped to t_end.  false: the domain does not move.
+// Time step of domain d from its words (S_max complete): one division.
+__device__ __forceinline__ void compute_domain_step(const StepArgs& a, int d)
+{
+  DomStep r{0.0, 0.0, 0.0, 0, 0};
+  const double t = a.t[d];
+  if (a.status[d] == ST_OK && t < a.t_end) {
+    const double dtp = a.dt_prev[d];
+    double dt_cfl;
+    if (a.nstep[d] % a.dt_hold == 0 || !(dtp > 0.0)) {
+      const double smax = a.sys == SYS_ADV ? fabs(a.ph.lambda) : __longlong_as_double((long long)a.smax_bits[d]);
+      dt_cfl = __ddiv_rn(__dmul_rn(a.cfl, a.dx[d]), smax);
+    } else {
+      dt_cfl = dtp;
+    }
+    double dt = dt_cfl;
+    if (__dadd_rn(t, dt) >= a.t_end) { dt = __dadd_rn(a.t_end, -t); r.last = 1; }
+    r.dt = dt;
+    r.dt_cfl = dt_cfl;
+    r.nu = __ddiv_rn(dt, a.dx[d]);
+    r.active = 1;
+  }
+  a.ds[d] = r;
+}
+
+// The step's time step of domain d; false when the domain does not step.
 __device__ __forceinline__ bool domain_dt(const StepArgs& a, int d, double& dt, double& dt_cfl, bool& last)
 {
-  if (a.status[d] != ST_OK) return false;
-  const double t = a.t[d];
-  if (!(t < a.t_end)) return false;
-  const double dtp = a.dt_prev[d];
-  if (a.nstep[d] % a.dt_hold == 0 || !(dtp > 0.0)) {
-    const double smax = a.sys == SYS_ADV ? fabs(a.ph.lambda) : __longlong_as_double((long long)a.smax_bits[d]);
-    dt_cfl = __ddiv_rn(__dmul_rn(a.cfl, a.dx[d]), smax);
-  } else {
-    dt_cfl = dtp;
-  }
-  dt = dt_cfl;
-  last = false;
-  if (__dadd_rn(t, dt) >= a.t_end) { dt = __dadd_rn(a.t_end, -t); last = true; }
-  return true;
+  const DomStep& r = a.ds[d];
+  dt = r.dt;
+  dt_cfl = r.dt_cfl;
+  last = r.last != 0;
+  return r.active != 0;
+}
+
+static __global__ void k_dt(StepArgs a)
+{
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d < a.n_domains) compute_domain_step(a, d);
 }
 
 // Neighbour cells of cell i (domain-local) under the domain's boundary rule:
@@ -235,7 +264,7 @@ __device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d,
     return;
   }
   a.low[gj] = 0;
-  const double nu = dt / a.dx[d];
+  const double nu = a.ds[d].nu;
 
   // cells on both sides (transmissive ends: a ghost with the boundary average)
   int cl, cr;
@@ -383,7 +412,7 @@ __device__ __forceinline__ int update_one(const StepArgs& a, long long gi, int d
     }
     return 0;
   }
-  const double r = dt / a.dx[d];
+  const double r = a.ds[d].nu;
   double Q[3];
 #pragma unroll
   for (int c = 0; c < C; ++c) {
@@ -447,17 +476,17 @@ __global__ void k_update(StepArgs a, int pass)
 // captured graph serves every step).
 constexpr int LIST_BLOCKS = 4 * 152, LIST_THREADS = 128;
 
-// First-order Godunov flux at the domain-local interface j (round `pass`),
-// unless the interface is already low; appends it to the round's interface list.
+// First-order Godunov flux at interface gj (round `pass`); appends it to the
+// round's interface list.
 template <bool G75>
-__device__ __forceinline__ void repair_iface(const StepArgs& a, int pass, int d, long long c0, long long i0, int N,
-                                             int bc, int j)
+__device__ __forceinline__ void repair_iface(const StepArgs& a, int pass, long long gj)
 {
-  const long long gj = i0 + j;
-  if (a.low[gj]) return;
+  const int d = a.if_dom[gj];
+  const long long c0 = a.cell_off[d], i0 = a.if_off[d];
+  const int N = (int)(a.cell_off[d + 1] - c0);
   double F[3], Q0[3];
   int iters = 0;
-  const int rs = first_order<G75>(a, c0, N, bc, j, F, Q0, iters);
+  const int rs = first_order<G75>(a, c0, N, a.bc[d], (int)(gj - i0), F, Q0, iters);
   unsigned long long* S = a.stats + (long long)d * NSTATS;
   atomicAdd(S + S_NEWTON_SUM, (unsigned long long)iters);
   atomicMax(S + S_NEWTON_MAX, (unsigned long long)iters);
@@ -474,25 +503,38 @@ __device__ __forceinline__ void repair_iface(const StepArgs& a, int pass, int d,
 }
 
 // Round `pass` of the repair from the list of troubled cells: each troubled
-// cell repairs its right interface, and its left one unless the left cell is
-// troubled too (that cell repairs it as its right interface, or did so in an
-// earlier round); interfaces repaired before are skipped.
+// cell names its right interface, and its left one unless the left cell is
+// troubled too (that cell names it as its right interface, or repaired it in
+// an earlier round); interfaces repaired before are skipped.  A block first
+// gathers the named interfaces of its slice of the list in shared memory and
+// then solves them one per thread, so the warps running Riemann problems are
+// full (on this GPU a divergent FP64 instruction costs as much as a full one).
 template <bool G75>
 __global__ void __launch_bounds__(LIST_THREADS) k_repair_list(StepArgs a, int pass)
 {
+  __shared__ long long q[2 * LIST_THREADS];
+  __shared__ int qn;
   const int n = a.lcount[pass];
   const int* L = a.tlist[pass & 1];
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const long long gi = L[k];
-    const int d = a.cell_dom[gi];
-    const long long c0 = a.cell_off[d], i0 = a.if_off[d];
-    const int N = (int)(a.cell_off[d + 1] - c0);
-    const int bc = a.bc[d];
-    const int i = (int)(gi - c0);
-    const int jr = bc == 0 ? (i == N - 1 ? 0 : i + 1) : i + 1;
-    const int il = bc == 0 ? (i == 0 ? N - 1 : i - 1) : i - 1;      // -1: the ghost
-    repair_iface<G75>(a, pass, d, c0, i0, N, bc, jr);
-    if (il < 0 || !a.troubled[c0 + il]) repair_iface<G75>(a, pass, d, c0, i0, N, bc, i);
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {   // uniform per block
+    if (threadIdx.x == 0) qn = 0;
+    __syncthreads();
+    const int k = base + threadIdx.x;
+    if (k < n) {
+      const long long gi = L[k];
+      const int d = a.cell_dom[gi];
+      const long long c0 = a.cell_off[d], i0 = a.if_off[d];
+      const int N = (int)(a.cell_off[d + 1] - c0);
+      const int bc = a.bc[d];
+      const int i = (int)(gi - c0);
+      const int jr = bc == 0 ? (i == N - 1 ? 0 : i + 1) : i + 1;
+      const int il = bc == 0 ? (i == 0 ? N - 1 : i - 1) : i - 1;      // -1: the ghost
+      if (!a.low[i0 + jr]) q[atomicAdd(&qn, 1)] = i0 + jr;
+      if ((il < 0 || !a.troubled[c0 + il]) && !a.low[i0 + i] && i != jr) q[atomicAdd(&qn, 1)] = i0 + i;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < qn; e += blockDim.x) repair_iface<G75>(a, pass, q[e]);
+    __syncthreads();
   }
 }
 
@@ -615,6 +657,8 @@ __global__ void __launch_bounds__(256, 2) k_batch(StepArgs a, const int* __restr
     if (SYS == SYS_EULER)
       for (long long base = cb; base < ce; base += bt) smax_cell(w, base + tid, base + tid < ce);
     __syncthreads();
+    for (int d = d0 + tid; d < d1; d += bt) compute_domain_step(w, d);
+    __syncthreads();
     for (long long base = ib; base < ie; base += bt) {
       const long long gj = base + tid;
       unsigned st[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
@@ -716,11 +760,12 @@ __global__ void __launch_bounds__(256) k_post(StepArgs a, const int* __restrict_
     reset_domain_words(a, d);
   }
   __syncthreads();
-  if (SYS == SYS_EULER) {
-    StepArgs n = a;                                   // S_max of the state just written
-    n.avg = a.avg_new;
+  StepArgs n = a;                                     // the state just written
+  n.avg = a.avg_new;
+  if (SYS == SYS_EULER)
     for (long long base = cb; base < ce; base += bt) smax_cell(n, base + tid, base + tid < ce);
-  }
+  __syncthreads();
+  for (int d = d0 + tid; d < d1; d += bt) compute_domain_step(n, d);   // next step's dt
 }
 
 // ------------------------------------------------------------------ init

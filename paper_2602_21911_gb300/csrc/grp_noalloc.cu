@@ -34,7 +34,8 @@ constexpr size_t OFF_TLIST0 = align256(OFF_IF_DOM + sizeof(int) * NA_IFACES);
 constexpr size_t OFF_TLIST1 = align256(OFF_TLIST0 + sizeof(int) * NA_CELLS);
 constexpr size_t OFF_ILIST = align256(OFF_TLIST1 + sizeof(int) * NA_CELLS);
 constexpr size_t OFF_POLD = align256(OFF_ILIST + sizeof(int) * NA_IFACES);
-constexpr size_t OFF_WORDS = align256(OFF_POLD + sizeof(double) * NA_CELLS);
+constexpr size_t OFF_DS = align256(OFF_POLD + sizeof(double) * NA_CELLS);
+constexpr size_t OFF_WORDS = align256(OFF_DS + sizeof(DomStep));
 
 // per-domain words of the single domain, in one struct
 struct Words {
@@ -137,6 +138,7 @@ extern "C" int grp_step_noalloc(int system, double lambda, double gamma, int M, 
   a.avg = avg_in; a.avg_new = avg_out; a.ifc = iface_in; a.ifc_new = iface_out;
   a.flux = (double*)(base + OFF_FLUX);
   a.pold = (double*)(base + OFF_POLD);
+  a.ds = (DomStep*)(base + OFF_DS);
   a.low = base + OFF_LOW; a.troubled = base + OFF_TROUBLED;
   a.t = &w->t; a.dt_prev = &w->dt_prev; a.nstep = &w->nstep; a.status = &w->status;
   a.smax_bits = &w->smax_bits;
@@ -149,6 +151,7 @@ extern "C" int grp_step_noalloc(int system, double lambda, double gamma, int M, 
   // the flat step sequence of grp_step
   const bool euler = system == GRP_EULER_IDEAL;
   if (euler) k_smax<<<nblk(N, 256), 256, 0, s>>>(a);
+  k_dt<<<1, 32, 0, s>>>(a);
   if (flux_dispatch(a, s) != cudaSuccess) return GRP_E_CUDA;
   if (euler) {
     k_update<SYS_EULER><<<nblk(N, 256), 256, 0, s>>>(a, -1);
