@@ -171,6 +171,25 @@ GRP_HD __forceinline__ double rcp_newton_step(double y)
   return fma(r, e, r);
 }
 
+// 1/y for a positive normal y, correct to about an ulp: the hardware
+// reciprocal approximation (rcp.approx.ftz.f64, about 2^-22 relative) and two
+// Newton steps r <- r + r (1 - y r), each squaring the relative error.  Half
+// the FP64 instructions of a correctly rounded division; used where the result
+// feeds further arithmetic, not a comparison with the oracle's rounding.
+GRP_HD __forceinline__ double rcp64(double y)
+{
+#ifdef __CUDA_ARCH__
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(y));
+  double e = fma(-y, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-y, r, 1.0);
+  return fma(r, e, r);
+#else
+  return 1.0 / y;
+#endif
+}
+
 // x^(-1/7) for x > 0: FP32 seed 2^(-log2(x)/7), then two FP64 Newton steps on
 // w^-7 = x, w <- w (8 - x w^7)/7, each squaring the relative error
 // (2^-21 -> 2^-40 -> rounding).  Outside the FP32 normal range: pow.
@@ -218,7 +237,7 @@ GRP_HD __forceinline__ Side make_side(const Phys& ph, const double Q[3])
   s.c = c2 * s.ic;
   s.sA = ph.sqrt_c2_gp1 * tr;
   s.B = ph.gm1_gp1 * s.p;
-  s.ip = 1.0 / s.p;
+  s.ip = rcp64(s.p);
   s.k = ph.c2_gm1 * s.c;
   s.d = s.ir * s.ic;
   return s;
@@ -426,18 +445,21 @@ GRP_HD __forceinline__ float fast_tanh(float x)
 #endif
 }
 
-// Features x[6] and pbar; returns false for data that are not strong (no
-// network), decided first without transcendental functions:
+// Strong data, decided without transcendental functions:
 // |ln(pL/pR)| > g  <=>  pL/pR outside [e^-g, e^g], and
 // |du|/cbar > g    <=>  du^4 rhoL rhoR > g^4 gamma^2 pL pR.
-GRP_HD __forceinline__ bool mlp_features(const Phys& ph, const Side& L, const Side& R, float x[6], double& pbar)
+GRP_HD __forceinline__ bool strong_data(const Phys& ph, const Side& L, const Side& R)
 {
   const double pr = L.p * R.ip, dun = R.u - L.u, du2 = dun * dun;
   const double g2 = (double)MLP_GATE * (double)MLP_GATE;
-  const bool strong = pr > MLP_GATE_EXP || pr * MLP_GATE_EXP < 1.0 ||
-                      du2 * du2 * (L.r * R.r) > g2 * g2 * ph.gamma * ph.gamma * (L.p * R.p);
-  if (!strong) return false;
-  const float lp = logf((float)pr);
+  return pr > MLP_GATE_EXP || pr * MLP_GATE_EXP < 1.0 ||
+         du2 * du2 * (L.r * R.r) > g2 * g2 * ph.gamma * ph.gamma * (L.p * R.p);
+}
+
+// Features x[6] and pbar of strong data.
+GRP_HD __forceinline__ void mlp_features(const Phys& ph, const Side& L, const Side& R, float x[6], double& pbar)
+{
+  const float lp = logf((float)(L.p * R.ip));
   const float lr = logf((float)(L.r * R.ir));
   pbar = sqrt(L.p * R.p);
   const double cbar = sqrt(ph.gamma * pbar * sqrt(L.ir * R.ir));
@@ -445,7 +467,6 @@ GRP_HD __forceinline__ bool mlp_features(const Phys& ph, const Side& L, const Si
   x[0] = 0.5f * lr; x[1] = -0.5f * lr;
   x[2] = 0.5f * lp; x[3] = -0.5f * lp;
   x[4] = -0.5f * du; x[5] = 0.5f * du;
-  return true;
 }
 
 // The hidden activations live in local memory (the loops over neurons are not
@@ -488,8 +509,9 @@ struct RSInfo {
   int guess = 0;                 // 0 not tried, 1 network start used, 2 rejected, 3 p_TR start (two rarefactions)
 };
 
-// The learned-guess path of riemann_state: features, the two-rarefaction base
-// and, for data with a shock, the network; Newton from that start.  Returns
+// The learned-guess path of riemann_state for strong data: features, the
+// two-rarefaction base and, for data with a shock, the network; Newton from
+// that start.  Returns
 // the solver status, or -1 when no learned start was tried.  Kept out of line
 // so that its registers do not count against the flux kernels, which take
 // this path on a few strong-data interfaces only.
@@ -502,9 +524,9 @@ inline
 int learned_start(const Phys& ph, const Side& L, const Side& R, RSInfo& info, double& ps, double& us, int& iters)
 {
   int st = -1;
-  const bool strong = mlp_features(ph, L, R, info.x, info.pbar);
-  const double base = strong ? trrs<G75>(ph, L, R) : 0.0;
-  const bool ok = strong && base > 0.0 && isfinite(base);
+  mlp_features(ph, L, R, info.x, info.pbar);
+  const double base = trrs<G75>(ph, L, R);
+  const bool ok = base > 0.0 && isfinite(base);
   // shock strength s = ln(p_TR / min(pL, pR)); s <= 0: two rarefactions, and
   // p_TR is p* up to rounding; s < MLP_S_MIN: |ln(p*/p_TR)| < 1e-11
   const double sh = ok ? log(base / fmin(L.p, R.p)) : 0.0;
@@ -550,7 +572,8 @@ static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double
   double ps = 0.0, us = 0.0;
   int st = -1;
   iters = 0;
-  if (ph.features && info) st = learned_start<G75>(ph, L, R, *info, ps, us, iters);
+  // the learned-guess path (out of line) only for strong data
+  if (ph.features && info && strong_data(ph, L, R)) st = learned_start<G75>(ph, L, R, *info, ps, us, iters);
   if (st != ST_OK && st != ST_VACUUM) {
     int it2 = 0;
     Phys pv = ph;
@@ -586,7 +609,7 @@ struct Eig {
 GRP_HD __forceinline__ Eig make_eig(const Phys& ph, const double Q0[3], Prim w)
 {
   Eig e;
-  const double ir = 1.0 / w.r;
+  const double ir = rcp64(w.r);
   e.u = w.u;
   const double c2 = ph.gamma * w.p * ir;
   e.ic = rsqrt(c2);
@@ -640,7 +663,7 @@ GRP_HD __forceinline__ void ck_euler(double g, double rho[Tri<M>::N], double m[T
 {
   using T = Tri<M>;
   double u[T::N], mu[T::N], Ep[T::N], F1[T::N], F2[T::N];
-  const double irho = 1.0 / rho[0];
+  const double irho = rcp64(rho[0]);
   const double gm1 = g - 1.0;
 #pragma unroll
   for (int b = 0; b < M; ++b) {
@@ -786,7 +809,7 @@ GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[
       for (int k = M - 1; k >= 0; --k) v = v * Tn + s[c][k];
       Qg[al][c] = v;
     }
-    ug[al] = Qg[al][1] / Qg[al][0];
+    ug[al] = Qg[al][1] * rcp64(Qg[al][0]);        // a non-positive density fails the test below
     pg[al] = (g - 1.0) * (Qg[al][2] - 0.5 * Qg[al][1] * ug[al]);
     ok = ok && Qg[al][0] > 0.0 && pg[al] > 0.0;
   }
