@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--domains", type=int, default=65536)
     ap.add_argument("--M", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other", action="store_true", help="skip the single-domain workloads")
     ap.add_argument("--launch", default="tune", choices=["tune", "auto", "flat", "fused", "split"],
                     help="launch configuration: autotuned (default), library default, or forced")
     ap.add_argument("--guess", default="learned", choices=["learned", "pvrs"])
@@ -213,6 +214,66 @@ def plain_arm(args, device, stream, w, box):
             "sample": "%d domains evenly spread over the batch (%d cells) x %d steps, one solver per domain, "
                       "flat kernels, direct launches, PVRS start" % (len(ids), int(prob["n_cells"].sum()),
                                                                      args.plain_steps)}, diffs
+
+
+def other_workloads(local, stream):
+    """Throughput of the single-domain configurations (context beside the
+    batched headline): the smooth Euler density wave at N = 8192 for M = 1..4
+    (plain single-domain path; launch-latency bound at this size), its L1
+    density error at t = 1 for M = 2, the shock tube at 2^22 cells (M = 2), and
+    the advection sine at N = 100 (M = 2) to t = 1."""
+    import torch
+    from paper_2602_21911_gb300 import grprec, inputs as I
+    out = {}
+
+    def timed(s, n):
+        s.step(8)
+        s.get_stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    for M in (1, 2, 3, 4):
+        prob, avg, lm, lp = I.euler_wave(8192, M)
+        s = grprec.Solver(prob, device=local, stream=stream.cuda_stream)
+        s.set_initial(avg, lm, lp)
+        ms = timed(s, 256)
+        out["euler_wave_N8192_M%d" % M] = {"cell_updates_per_s": 8192 / (ms * 1e-3), "ms_per_step": ms}
+        if M == 2:
+            s.set_initial(avg, lm, lp)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.advance_to(1.0)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            l1, _, _ = s.error_norms(np.ascontiguousarray(I.euler_wave_exact(8192, 1.0)[0]))
+            stats, _ = s.get_stats()
+            out["euler_wave_N8192_M2"].update({"t_end": 1.0, "steps": int(stats[0, 0]),
+                                               "seconds_to_t_end": e0.elapsed_time(e1) * 1e-3,
+                                               "l1_rho": float(l1[0])})
+        s.close()
+    prob, avg, lm, lp = I.sod(1 << 22, M=2)
+    s = grprec.Solver(prob, device=local, stream=stream.cuda_stream)
+    s.set_initial(avg, lm, lp)
+    ms = timed(s, 64)
+    out["sod_N4194304_M2"] = {"cell_updates_per_s": (1 << 22) / (ms * 1e-3), "ms_per_step": ms,
+                              "window": "steps 9..72 of t_end = 0.2"}
+    s.close()
+    prob, avg, lm, lp = I.advection_sine(100, M=2)
+    s = grprec.Solver(prob, device=local, stream=stream.cuda_stream)
+    s.set_initial(avg, lm, lp)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.advance_to(1.0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    l1, _, _ = s.error_norms(np.ascontiguousarray(I.advection_sine_exact(100, 1.0)[0]))
+    out["advection_sine_N100_M2"] = {"seconds_to_t_end": e0.elapsed_time(e1) * 1e-3, "l1": float(l1[0])}
+    s.close()
+    return out
 
 
 def cpu_baseline(args, steps=100, stride=4):
@@ -409,6 +470,8 @@ def main():
                             "kernel": kname,
                             "peak_source": "measured FP64 FMA-chain probe (grp_probe_fp64_peak), this GPU",
                             "flops_per_cell_update": flops}
+    if not args.no_other:
+        line["workloads"] = other_workloads(local, stream)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line))
