@@ -48,6 +48,7 @@ enum { GRP_ADVECTION = 0, GRP_EULER_IDEAL = 1 };                 /* system (Sect
 enum { GRP_BC_PERIODIC = 0, GRP_BC_TRANSMISSIVE = 1 };            /* per-domain boundary */
 enum { GRP_GUESS_PVRS = 0, GRP_GUESS_TRRS = 1, GRP_GUESS_MLP = 2 };/* Newton initial guess for p* */
 enum { GRP_LAUNCH_AUTO = 0, GRP_LAUNCH_FLAT = 1, GRP_LAUNCH_FUSED = 2, GRP_LAUNCH_SPLIT = 3 }; /* grp_set_launch */
+enum { GRP_RECON_GRPREC = 0, GRP_RECON_GRPRECNL = 1 };            /* reconstruction (Sections 3.1, 3.3-3.4) */
 
 /* return codes */
 enum {
@@ -98,6 +99,11 @@ typedef struct {
   int dt_hold;           /* recompute dt every dt_hold steps; 1 = the paper's rule */
   int device;            /* CUDA device ordinal */
   void *stream;          /* cudaStream_t to order work on (NULL = default stream) */
+  int recon;             /* GRP_RECON_GRPREC: linear GRPrec, component-wise in conserved variables
+                            (Section 3.1); GRP_RECON_GRPRECNL: the nonlinear convex combination
+                            of Sections 3.3-3.4 (weights r = 4, eps = 1e-14, lambda_C = 1e9), in
+                            characteristic variables of the cell average for the Euler equations
+                            (Section 3.1).  grp_step_noalloc always uses GRPrec. */
 } grp_problem;
 
 /*

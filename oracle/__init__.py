@@ -17,6 +17,7 @@ import numpy as np
 from . import build as _build
 
 ADVECTION, EULER = 0, 1
+RECON_GRPREC, RECON_GRPRECNL = 0, 1
 PERIODIC, TRANSMISSIVE = 0, 1
 GUESS_PVRS, GUESS_TRRS, GUESS_GIVEN = 0, 1, 2
 OK, NEWTON_NO_CONV, VACUUM, NONPHYSICAL = 0, 1, 2, 3
@@ -51,6 +52,12 @@ def lib():
                              ctypes.c_double, ctypes.c_int, _I, _D, _D, _I, ctypes.c_double,
                              ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _I, _D, _I,
                              ctypes.c_int, ctypes.c_double, _L, _D, ctypes.c_int]
+        L.or_run_ex.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_double, ctypes.c_int, _I, _D, _D, _I, ctypes.c_double,
+                                ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _I, _D, _I,
+                                ctypes.c_int, ctypes.c_double, _L, _D, ctypes.c_int]
+        L.or_recon_nl.argtypes = [ctypes.c_int, _D, ctypes.c_double, _D, _D]
+        L.or_char_basis.argtypes = [ctypes.c_double, _D, _D, _D]
         _lib = L
     return _lib
 
@@ -65,6 +72,25 @@ def _ip(a):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def recon_nl(M, d7, dx):
+    """GRPrecNL monomial coefficients and the weights (beta_L, beta_C, beta_R)
+    (Sections 3.3-3.4); d7 = (q_{i-1}, q_i, q_{i+1}, g_{i-3/2}, g_{i-1/2},
+    g_{i+1/2}, g_{i+3/2})."""
+    d7 = _f64(d7)
+    coef, beta = np.zeros(5), np.zeros(3)
+    if lib().or_recon_nl(M, _dp(d7), float(dx), _dp(coef), _dp(beta)) != 0:
+        raise ValueError("bad degree")
+    return coef[:M + 1], beta
+
+
+def char_basis(gamma, Q):
+    """(R, L): right eigenvectors (columns) of the Euler flux Jacobian at Q and L = R^-1."""
+    Q = _f64(Q)
+    R, L = np.zeros(9), np.zeros(9)
+    lib().or_char_basis(float(gamma), _dp(Q), _dp(R), _dp(L))
+    return R.reshape(3, 3), L.reshape(3, 3)
 
 
 def recon(M, qbar, g):
@@ -148,7 +174,7 @@ def run(prob, state, n_steps, t_end=np.inf, dt_fixed=None, n_threads=1):
     """Advance ``state`` in place by n_steps or to t_end (Section 2 update).
 
     ``prob`` keys: system, lam, gamma, M, cfl, n_cells, x_left, x_right, bc,
-    newton_rtol, newton_max_iter, guess, dt_hold.
+    newton_rtol, newton_max_iter, guess, dt_hold, recon (optional).
     """
     n_cells = np.ascontiguousarray(prob["n_cells"], dtype=np.int32)
     xl = _f64(prob["x_left"])
@@ -158,8 +184,8 @@ def run(prob, state, n_steps, t_end=np.inf, dt_fixed=None, n_threads=1):
     if dt_fixed is not None:
         dtf = _f64(dt_fixed)
         assert len(dtf) >= n_steps
-    rc = lib().or_run(prob["system"], prob.get("lam", 1.0), prob.get("gamma", 1.4), prob["M"],
-                      prob["cfl"], len(n_cells), _ip(n_cells), _dp(xl), _dp(xr), _ip(bc),
+    rc = lib().or_run_ex(prob["system"], prob.get("lam", 1.0), prob.get("gamma", 1.4), prob["M"],
+                      prob.get("recon", RECON_GRPREC), prob["cfl"], len(n_cells), _ip(n_cells), _dp(xl), _dp(xr), _ip(bc),
                       prob.get("newton_rtol", 1e-12), prob.get("newton_max_iter", 50),
                       prob.get("guess", GUESS_PVRS), prob.get("dt_hold", 1),
                       _dp(state.avg), _dp(state.iface), _dp(state.t), _ip(state.nstep),

@@ -192,6 +192,138 @@ int or_recon(int M, const double *qbar, const double *g, double *coef)
   return 0;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Sections 3.3-3.4, GRPrecNL: p_i = beta_L p_L + beta_C p_C + beta_R p_R,    */
+/* beta_k = omega_k / sum omega, omega_k = lambda_k / (eps + OI_k)^r with     */
+/* r = 4, eps = 1e-14, lambda_L = lambda_R = 1, lambda_C = 1e9; p_C is the    */
+/* linear GRPrec polynomial, p_L and p_R the one-sided polynomials of the     */
+/* paragraphs for each degree (every one conserves cell i):                  */
+/*   degree 1: p_L interpolates g_{i-1/2}; p_R interpolates g_{i+1/2}         */
+/*   degree 2: p_L conserves cell i-1, interpolates g_{i+1/2};               */
+/*             p_R conserves cell i+1, interpolates g_{i-1/2}                */
+/*   degree 3: both conserve cells i-1, i+1; p_L interpolates g_{i-1/2},     */
+/*             p_R interpolates g_{i+1/2}                                     */
+/*   degree 4: both conserve cells i-1, i+1; p_L interpolates g_{i-1/2} and  */
+/*             g_{i-3/2}, p_R interpolates g_{i+1/2} and g_{i+3/2}           */
+/* OI_k = sum_{l=1..M} int_cell (d^l p_k/dx^l)^2 dx^{2l} dx, which in xi is   */
+/* dx * sum_l int_{-1/2}^{1/2} (d^l p_k/dxi^l)^2 dxi (READING: the printed     */
+/* weight dx^{2l} with the measure dx, taken literally).                      */
+/* Data order: d7 = {q_{i-1}, q_i, q_{i+1}, g_{i-3/2}, g_{i-1/2}, g_{i+1/2},  */
+/* g_{i+3/2}}.                                                                */
+/* ------------------------------------------------------------------------- */
+#define OR_NL_R 4
+#define OR_NL_EPS 1e-14
+#define OR_NL_LAMBDA_C 1e9
+
+static int side_system(int M, int side, const double *d7, double *coef)
+{
+  double A[(MAXM + 1) * (MAXM + 1)], x[MAXM + 1];
+  int n = 0;
+  const double h = 0.5, h3 = 1.5;
+#define ROW_AVG(a, b, v) do { row_average_d(M, a, b, A + n * (M + 1)); x[n++] = (v); } while (0)
+#define ROW_PT(z, v) do { row_point_d(M, z, A + n * (M + 1)); x[n++] = (v); } while (0)
+  ROW_AVG(-h, h, d7[1]);                                   /* cell i */
+  if (M == 1) {
+    if (side == 0) ROW_PT(-h, d7[4]); else ROW_PT(h, d7[5]);
+  } else if (M == 2) {
+    if (side == 0) { ROW_AVG(-h3, -h, d7[0]); ROW_PT(h, d7[5]); }
+    else { ROW_AVG(h, h3, d7[2]); ROW_PT(-h, d7[4]); }
+  } else {
+    ROW_AVG(-h3, -h, d7[0]);
+    ROW_AVG(h, h3, d7[2]);
+    if (side == 0) { ROW_PT(-h, d7[4]); if (M == 4) ROW_PT(-h3, d7[3]); }
+    else { ROW_PT(h, d7[5]); if (M == 4) ROW_PT(h3, d7[6]); }
+  }
+#undef ROW_AVG
+#undef ROW_PT
+  if (n != M + 1) return -1;
+  if (solve_dense_d(n, A, x) != 0) return -1;
+  for (int k = 0; k <= MAXM; ++k) coef[k] = k <= M ? x[k] : 0;
+  return 0;
+}
+
+/* p_L, p_R are linear in the 7 data: operator columns from unit data, per M */
+static double side_op[2][MAXM + 1][MAXM + 1][7];
+static int side_op_ready[MAXM + 1];
+
+static void nl_side_apply(int M, int side, const real *d7, real *coef)
+{
+  if (!side_op_ready[M]) {
+    for (int sd = 0; sd < 2; ++sd)
+      for (int j = 0; j < 7; ++j) {
+        double unit[7] = { 0, 0, 0, 0, 0, 0, 0 }, cf[MAXM + 1];
+        unit[j] = 1;
+        side_system(M, sd, unit, cf);
+        for (int k = 0; k <= MAXM; ++k) side_op[sd][M][k][j] = cf[k];
+      }
+    side_op_ready[M] = 1;
+  }
+  for (int k = 0; k <= MAXM; ++k) {
+    real s = 0;
+    for (int j = 0; j < 7; ++j)
+      if (side_op[side][M][k][j] != 0) s = s + side_op[side][M][k][j] * d7[j];
+    coef[k] = k <= M ? s : (real)0;
+  }
+}
+
+/* dx * sum_{l=1..M} int_{-1/2}^{1/2} (p^{(l)}(xi))^2 dxi, by exact monomial integration */
+static real oscillation_indicator(int M, const real *coef, real dx)
+{
+  real total = 0;
+  for (int l = 1; l <= M; ++l) {
+    real d[MAXM + 1];                          /* d^l/dxi^l in monomials */
+    int nd = M - l;
+    for (int k = 0; k <= nd; ++k) {
+      real fall = 1;
+      for (int r = 0; r < l; ++r) fall = fall * (k + l - r);
+      d[k] = coef[k + l] * fall;
+    }
+    for (int a = 0; a <= nd; ++a)
+      for (int b = 0; b <= nd; ++b) {
+        int e = a + b;
+        if (e % 2) continue;                   /* odd powers integrate to zero */
+        double mono = 2.0 * pow(0.5, e + 1) / (e + 1);
+        total = total + d[a] * d[b] * mono;
+      }
+  }
+  return dx * total;
+}
+
+/* GRPrecNL polynomial of one scalar component; beta (may be NULL) gets the weights L, C, R */
+static void recon_nl(int M, const real *d7, real dx, real *coef, real *beta)
+{
+  real pk[3][MAXM + 1];
+  real d5[5] = { d7[0], d7[1], d7[2], d7[4], d7[5] };
+  nl_side_apply(M, 0, d7, pk[0]);
+  recon_apply(M, d5, pk[1]);
+  nl_side_apply(M, 1, d7, pk[2]);
+  const double lam[3] = { 1.0, OR_NL_LAMBDA_C, 1.0 };
+  real om[3], sum = 0;
+  for (int k = 0; k < 3; ++k) {
+    real b = OR_NL_EPS + oscillation_indicator(M, pk[k], dx);
+    real b2 = b * b;
+    om[k] = lam[k] / (b2 * b2);                /* r = 4 */
+    sum = sum + om[k];
+  }
+  for (int q = 0; q <= MAXM; ++q) coef[q] = 0;
+  for (int k = 0; k < 3; ++k) {
+    real w = om[k] / sum;
+    if (beta) beta[k] = w;
+    for (int q = 0; q <= M; ++q) coef[q] = coef[q] + w * pk[k][q];
+  }
+}
+
+int or_recon_nl(int M, const double *d7, double dx, double *coef, double *beta)
+{
+  if (M < 1 || M > MAXM) return -1;
+  real d[7], cf[MAXM + 1], bt[3];
+  for (int j = 0; j < 7; ++j) d[j] = d7[j];
+  recon_nl(M, d, dx, cf, bt);
+  for (int k = 0; k <= MAXM; ++k) coef[k] = (double)cf[k];
+  if (beta) for (int k = 0; k < 3; ++k) beta[k] = (double)bt[k];
+  return 0;
+}
+
 /* k-th xi-derivative of the polynomial at xi0 */
 static real poly_deriv(int M, const real *coef, int k, real xi0)
 {
@@ -238,6 +370,38 @@ static int euler_admissible(real gamma, const real *Q)
   if (!(Q[0] > 0)) return 0;
   cons_to_prim(gamma, Q, W);
   return W[2] > 0;
+}
+
+/* Characteristic variables of the Euler equations at state Q (Section 3.1:
+ * systems are reconstructed in characteristic variables): right eigenvectors
+ * of the flux Jacobian as the columns of R (textbook form, eigenvalues u - c,
+ * u, u + c), and L = R^{-1} by the adjugate. */
+static void char_basis(real gamma, const real *Q, real R[3][3], real L[3][3])
+{
+  real W[3];
+  cons_to_prim(gamma, Q, W);
+  real u = W[1], c = sqrt(gamma * W[2] / W[0]), H = (Q[2] + W[2]) / W[0];
+  R[0][0] = 1;         R[0][1] = 1;             R[0][2] = 1;
+  R[1][0] = u - c;     R[1][1] = u;             R[1][2] = u + c;
+  R[2][0] = H - u * c; R[2][1] = 0.5 * u * u;   R[2][2] = H + u * c;
+  real cof[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int k = 0; k < 3; ++k) {
+      int r1 = (r + 1) % 3, r2 = (r + 2) % 3, k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+      cof[r][k] = R[r1][k1] * R[r2][k2] - R[r1][k2] * R[r2][k1];
+    }
+  real det = R[0][0] * cof[0][0] + R[0][1] * cof[0][1] + R[0][2] * cof[0][2];
+  for (int r = 0; r < 3; ++r)
+    for (int k = 0; k < 3; ++k) L[r][k] = cof[k][r] / det;
+}
+
+int or_char_basis(double gamma, const double *Q, double *R, double *L)
+{
+  real q[3] = { Q[0], Q[1], Q[2] }, r[3][3], l[3][3];
+  char_basis(gamma, q, r, l);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) { R[a * 3 + b] = (double)r[a][b]; L[a * 3 + b] = (double)l[a][b]; }
+  return 0;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -659,6 +823,7 @@ int or_init_iface(int system, double lambda, double gamma, int n_ifaces,
 typedef struct {
   int system; real lambda, gamma; int M; real cfl;
   real rtol; int max_iter; int guess_kind; int dt_hold;
+  int recon;                  /* OR_RECON_GRPREC or OR_RECON_GRPRECNL */
 } params;
 
 /* Time-step rule (Section 4.1): dt = C dx / S_max, S_max over the cell averages.
@@ -748,10 +913,42 @@ static int step_domain(const params *P, int N, int bc, real dx, real dt, real *a
     if (bc == OR_BC_PERIODIC) { im = (im + N) % N; ip = ip % N; }
     else { if (im < 0) im = 0; if (ip > N - 1) ip = N - 1; }  /* ghost = copy */
     int jl = i, jr = (bc == OR_BC_PERIODIC) ? (i + 1) % N : i + 1;
-    for (int c = 0; c < C; ++c) {
-      real data[5] = { avg[c * cstride + im], avg[c * cstride + i], avg[c * cstride + ip],
-                       iface[c * istride + jl], iface[c * istride + jr] };
-      recon_apply(M, data, coef + (i * C + c) * (MAXM + 1));
+    if (P->recon == OR_RECON_GRPRECNL) {
+      /* the two further interfaces of degree 4 (READING: outside a
+       * transmissive end the ghost state is the boundary cell's average,
+       * on its interfaces too) */
+      int jll = i - 1, jrr = i + 2;
+      if (bc == OR_BC_PERIODIC) { jll = (jll + N) % N; jrr = jrr % N; }
+      real d7[MAXC][7];
+      for (int c = 0; c < C; ++c) {
+        d7[c][0] = avg[c * cstride + im];
+        d7[c][1] = avg[c * cstride + i];
+        d7[c][2] = avg[c * cstride + ip];
+        d7[c][3] = jll < 0 ? avg[c * cstride + 0] : iface[c * istride + jll];
+        d7[c][4] = iface[c * istride + jl];
+        d7[c][5] = iface[c * istride + jr];
+        d7[c][6] = (bc != OR_BC_PERIODIC && jrr > N) ? avg[c * cstride + N - 1] : iface[c * istride + jrr];
+      }
+      if (P->system == OR_EULER) {
+        /* characteristic variables of the cell average (Section 3.1) */
+        real Qi[3] = { avg[i], avg[cstride + i], avg[2 * cstride + i] }, Rm[3][3], Lm[3][3];
+        char_basis(P->gamma, Qi, Rm, Lm);
+        real w7[3][7], cw[3][MAXM + 1];
+        for (int k = 0; k < 3; ++k)
+          for (int j = 0; j < 7; ++j) w7[k][j] = Lm[k][0] * d7[0][j] + Lm[k][1] * d7[1][j] + Lm[k][2] * d7[2][j];
+        for (int k = 0; k < 3; ++k) recon_nl(M, w7[k], dx, cw[k], 0);
+        for (int c = 0; c < 3; ++c)
+          for (int q = 0; q <= MAXM; ++q)
+            coef[(i * C + c) * (MAXM + 1) + q] = Rm[c][0] * cw[0][q] + Rm[c][1] * cw[1][q] + Rm[c][2] * cw[2][q];
+      } else {
+        recon_nl(M, d7[0], dx, coef + i * (MAXM + 1), 0);
+      }
+    } else {
+      for (int c = 0; c < C; ++c) {
+        real data[5] = { avg[c * cstride + im], avg[c * cstride + i], avg[c * cstride + ip],
+                         iface[c * istride + jl], iface[c * istride + jr] };
+        recon_apply(M, data, coef + (i * C + c) * (MAXM + 1));
+      }
     }
     if (P->system == OR_EULER) {   /* READING: inadmissible trace -> degree 0 */
       int ok = 1;
@@ -861,10 +1058,22 @@ int or_run(int system, double lambda, double gamma, int M, double cfl,
            double *avg, double *iface, double *t, int *nstep, double *dt_prev, int *status,
            int n_steps, double t_end, long long *stats, const double *dt_fixed, int n_threads)
 {
+  return or_run_ex(system, lambda, gamma, M, OR_RECON_GRPREC, cfl, n_domains, n_cells, x_left, x_right, bc,
+                   newton_rtol, newton_max_iter, guess_kind, dt_hold, avg, iface, t, nstep, dt_prev, status,
+                   n_steps, t_end, stats, dt_fixed, n_threads);
+}
+
+int or_run_ex(int system, double lambda, double gamma, int M, int recon, double cfl,
+              int n_domains, const int *n_cells, const double *x_left, const double *x_right,
+              const int *bc, double newton_rtol, int newton_max_iter, int guess_kind, int dt_hold,
+              double *avg, double *iface, double *t, int *nstep, double *dt_prev, int *status,
+              int n_steps, double t_end, long long *stats, const double *dt_fixed, int n_threads)
+{
   params P;
   P.system = system; P.lambda = lambda; P.gamma = gamma; P.M = M; P.cfl = cfl;
   P.rtol = newton_rtol; P.max_iter = newton_max_iter; P.guess_kind = guess_kind;
   P.dt_hold = dt_hold < 1 ? 1 : dt_hold;
+  P.recon = recon;
   if (M < 1 || M > MAXM) return -1;
   const int C = system == OR_EULER ? 3 : 1;
   long *coff = (long *)malloc(sizeof(long) * (n_domains + 1));

@@ -25,6 +25,7 @@ extern "C" {
 enum { OR_ADVECTION = 0, OR_EULER = 1 };
 enum { OR_BC_PERIODIC = 0, OR_BC_TRANSMISSIVE = 1 };
 enum { OR_GUESS_PVRS = 0, OR_GUESS_TRRS = 1, OR_GUESS_GIVEN = 2 };
+enum { OR_RECON_GRPREC = 0, OR_RECON_GRPRECNL = 1 };
 enum {
   OR_OK = 0,
   OR_NEWTON_NO_CONV = 1,
@@ -46,6 +47,17 @@ enum {
 /* Section 3.1: GRPrec polynomial of degree M on cell i, monomial coefficients
  * in xi = (x - x_i)/dx.  qbar = {q_{i-1}, q_i, q_{i+1}}, g = {g_{i-1/2}, g_{i+1/2}}. */
 int or_recon(int M, const double *qbar, const double *g, double *coef);
+
+/* Sections 3.3-3.4: GRPrecNL polynomial of degree M (monomial coefficients in
+ * xi) from d7 = {q_{i-1}, q_i, q_{i+1}, g_{i-3/2}, g_{i-1/2}, g_{i+1/2},
+ * g_{i+3/2}} and the cell width dx; beta (3 values, may be NULL) receives the
+ * nonlinear weights of the left, central and right polynomials. */
+int or_recon_nl(int M, const double *d7, double dx, double *coef, double *beta);
+
+/* Characteristic variables of the Euler equations at conserved state Q:
+ * R (row-major 3x3, right eigenvectors as columns, eigenvalues u-c, u, u+c)
+ * and L = R^{-1}. */
+int or_char_basis(double gamma, const double *Q, double *R, double *L);
 
 /* Exact Riemann solver for the ideal-gas Euler equations (primitive states). */
 int or_star_pressure(double gamma, const double *WL, const double *WR, int guess_kind,
@@ -74,6 +86,15 @@ int or_run(int system, double lambda, double gamma, int M, double cfl,
            const int *bc, double newton_rtol, int newton_max_iter, int guess_kind, int dt_hold,
            double *avg, double *iface, double *t, int *nstep, double *dt_prev, int *status,
            int n_steps, double t_end, long long *stats, const double *dt_fixed, int n_threads);
+
+/* or_run with the reconstruction chosen: OR_RECON_GRPREC (Section 3.1, conserved
+ * variables) or OR_RECON_GRPRECNL (Sections 3.3-3.4, characteristic variables
+ * for the Euler equations). */
+int or_run_ex(int system, double lambda, double gamma, int M, int recon, double cfl,
+              int n_domains, const int *n_cells, const double *x_left, const double *x_right,
+              const int *bc, double newton_rtol, int newton_max_iter, int guess_kind, int dt_hold,
+              double *avg, double *iface, double *t, int *nstep, double *dt_prev, int *status,
+              int n_steps, double t_end, long long *stats, const double *dt_fixed, int n_threads);
 
 #ifdef __cplusplus
 }

@@ -126,6 +126,7 @@ StepArgs make_args(const grp_ctx* c, double t_end)
   StepArgs a;
   a.sys = c->p.system;
   a.M = c->p.M;
+  a.recon = c->p.recon;
   a.C = c->C;
   a.ph = make_phys(c->p.lambda, c->p.gamma, c->p.newton_rtol, c->p.newton_max_iter, c->p.guess);
   a.cfl = c->p.cfl;
@@ -185,24 +186,26 @@ cudaError_t record(const grp_ctx* c, cudaEvent_t e)
 
 cudaError_t launch_flux(const StepArgs& a, cudaStream_t s)
 {
-  if (a.sys == SYS_ADV) return launch_flux_adv(a, s);
+  const bool nl = a.recon == GRP_RECON_GRPRECNL;
+  if (a.sys == SYS_ADV) return nl ? launch_flux_adv_nl(a, s) : launch_flux_adv(a, s);
   switch (a.M) {
-    case 1: return launch_flux_euler_m1(a, s);
-    case 2: return launch_flux_euler_m2(a, s);
-    case 3: return launch_flux_euler_m3(a, s);
-    case 4: return launch_flux_euler_m4(a, s);
+    case 1: return nl ? launch_flux_euler_m1_nl(a, s) : launch_flux_euler_m1(a, s);
+    case 2: return nl ? launch_flux_euler_m2_nl(a, s) : launch_flux_euler_m2(a, s);
+    case 3: return nl ? launch_flux_euler_m3_nl(a, s) : launch_flux_euler_m3(a, s);
+    case 4: return nl ? launch_flux_euler_m4_nl(a, s) : launch_flux_euler_m4(a, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s)
 {
-  if (L.a.sys == SYS_ADV) return launch_batch_adv(L, s);
+  const bool nl = L.a.recon == GRP_RECON_GRPRECNL;
+  if (L.a.sys == SYS_ADV) return nl ? launch_batch_adv_nl(L, s) : launch_batch_adv(L, s);
   switch (L.a.M) {
-    case 1: return launch_batch_euler_m1(L, s);
-    case 2: return launch_batch_euler_m2(L, s);
-    case 3: return launch_batch_euler_m3(L, s);
-    case 4: return launch_batch_euler_m4(L, s);
+    case 1: return nl ? launch_batch_euler_m1_nl(L, s) : launch_batch_euler_m1(L, s);
+    case 2: return nl ? launch_batch_euler_m2_nl(L, s) : launch_batch_euler_m2(L, s);
+    case 3: return nl ? launch_batch_euler_m3_nl(L, s) : launch_batch_euler_m3(L, s);
+    case 4: return nl ? launch_batch_euler_m4_nl(L, s) : launch_batch_euler_m4(L, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -396,6 +399,7 @@ int grp_create(grp_ctx** out, const grp_problem* p)
   if (!(p->newton_rtol > 0.0) || p->newton_max_iter < 2) return GRP_E_INVALID_ARG;
   if (p->guess < GRP_GUESS_PVRS || p->guess > GRP_GUESS_MLP) return GRP_E_INVALID_ARG;
   if (p->dt_hold < 1) return GRP_E_INVALID_ARG;
+  if (p->recon != GRP_RECON_GRPREC && p->recon != GRP_RECON_GRPRECNL) return GRP_E_INVALID_ARG;
   grp_ctx* c = new grp_ctx();
   c->p = *p;
   c->p.n_cells = nullptr; c->p.x_left = nullptr; c->p.x_right = nullptr; c->p.bc = nullptr;

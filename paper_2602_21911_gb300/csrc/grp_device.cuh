@@ -87,6 +87,92 @@ GRP_HD __forceinline__ void grprec_coeffs(double qm, double q0, double qp, doubl
   }
 }
 
+// ---------------------------------------------------------------------------
+// Sections 3.3-3.4, GRPrecNL: the convex combination beta_L p_L + beta_C p_C
+// + beta_R p_R of the one-sided polynomials and the linear GRPrec one, with
+// beta_k = omega_k / sum omega, omega_k = lambda_k / (eps + OI_k)^4,
+// eps = 1e-14, lambda_L = lambda_R = 1, lambda_C = 1e9, and
+// OI_k = dx * sum_{l<=M} int_{-1/2}^{1/2} (d^l p_k / dxi^l)^2 dxi (the printed
+// indicator, dx^{2l} with the measure dx).  Data
+// d = {q_{i-1}, q_i, q_{i+1}, g_{i-3/2}, g_{i-1/2}, g_{i+1/2}, g_{i+3/2}}.
+// One-sided polynomials in the zero-mean basis (all conserve cell i):
+//   degree 1: p_L through g_{i-1/2}, p_R through g_{i+1/2};
+//   degree 2: p_L conserves cell i-1 and passes through g_{i+1/2}, p_R
+//             conserves cell i+1 and passes through g_{i-1/2};
+//   degree 3: both conserve cells i-1, i+1; p_L through g_{i-1/2}, p_R
+//             through g_{i+1/2};
+//   degree 4: both conserve cells i-1, i+1; p_L through g_{i-1/2}, g_{i-3/2},
+//             p_R through g_{i+1/2}, g_{i+3/2}.
+// The closed forms solve those square systems in the zero-mean basis.
+// ---------------------------------------------------------------------------
+constexpr double NL_EPS = 1e-14, NL_LAMBDA_C = 1e9;
+
+template <int M>
+GRP_HD __forceinline__ void nl_sides(const double d[7], double bl[5], double br[5])
+{
+  const double qm = d[0], q0 = d[1], qp = d[2], gmm = d[3], gm = d[4], gp = d[5], gpp = d[6];
+  bl[0] = br[0] = q0;
+  bl[1] = bl[2] = bl[3] = bl[4] = br[1] = br[2] = br[3] = br[4] = 0.0;
+  if (M == 1) {
+    bl[1] = 2.0 * (q0 - gm);
+    br[1] = 2.0 * (gp - q0);
+  } else if (M == 2) {
+    bl[1] = 1.5 * gp - 1.25 * q0 - 0.25 * qm;
+    bl[2] = 1.5 * gp - 2.25 * q0 + 0.75 * qm;
+    br[1] = -1.5 * gm + 1.25 * q0 + 0.25 * qp;
+    br[2] = 1.5 * gm - 2.25 * q0 + 0.75 * qp;
+  } else if (M == 3) {
+    bl[1] = -2.5 * gm + (25.0 / 12.0) * q0 + (1.0 / 3.0) * qm + (1.0 / 12.0) * qp;
+    bl[2] = 0.5 * (qm + qp) - q0;
+    bl[3] = 2.0 * gm - (5.0 / 3.0) * q0 - (2.0 / 3.0) * qm + (1.0 / 3.0) * qp;
+    br[1] = 2.5 * gp - (25.0 / 12.0) * q0 - (1.0 / 12.0) * qm - (1.0 / 3.0) * qp;
+    br[2] = bl[2];
+    br[3] = -2.0 * gp + (5.0 / 3.0) * q0 - (1.0 / 3.0) * qm + (2.0 / 3.0) * qp;
+  } else {
+    bl[1] = -3.75 * gm - (5.0 / 12.0) * gmm + (95.0 / 36.0) * q0 + (109.0 / 72.0) * qm + (1.0 / 72.0) * qp;
+    bl[2] = -3.75 * gm - 1.25 * gmm + (2.0 / 3.0) * q0 + (97.0 / 24.0) * qm + (7.0 / 24.0) * qp;
+    bl[3] = 3.0 * gm + (1.0 / 3.0) * gmm - (19.0 / 9.0) * q0 - (29.0 / 18.0) * qm + (7.0 / 18.0) * qp;
+    bl[4] = 2.5 * gm + (5.0 / 6.0) * gmm - (10.0 / 9.0) * q0 - (85.0 / 36.0) * qm + (5.0 / 36.0) * qp;
+    br[1] = 3.75 * gp + (5.0 / 12.0) * gpp - (95.0 / 36.0) * q0 - (1.0 / 72.0) * qm - (109.0 / 72.0) * qp;
+    br[2] = -3.75 * gp - 1.25 * gpp + (2.0 / 3.0) * q0 + (7.0 / 24.0) * qm + (97.0 / 24.0) * qp;
+    br[3] = -3.0 * gp - (1.0 / 3.0) * gpp + (19.0 / 9.0) * q0 - (7.0 / 18.0) * qm + (29.0 / 18.0) * qp;
+    br[4] = 2.5 * gp + (5.0 / 6.0) * gpp - (10.0 / 9.0) * q0 + (5.0 / 36.0) * qm - (85.0 / 36.0) * qp;
+  }
+}
+
+// sum_{l<=M} int_{-1/2}^{1/2} (p^{(l)})^2 dxi for p with zero-mean coefficients b
+template <int M>
+GRP_HD __forceinline__ double nl_indicator(const double b[5])
+{
+  double s = b[1] * b[1];
+  if (M >= 2) s += (13.0 / 3.0) * b[2] * b[2];
+  if (M >= 3) s += 0.5 * b[1] * b[3] + (3129.0 / 80.0) * b[3] * b[3];
+  if (M >= 4) s += (21.0 / 5.0) * b[2] * b[4] + (87617.0 / 140.0) * b[4] * b[4];
+  return s;
+}
+
+// GRPrecNL coefficients b (zero-mean basis) of one scalar component
+template <int M>
+GRP_HD __forceinline__ void grprec_nl_coeffs(const double d[7], double dx, double b[5])
+{
+  double p[3][5];
+  nl_sides<M>(d, p[0], p[2]);
+  grprec_coeffs<M>(d[0], d[1], d[2], d[4], d[5], p[1]);
+  const double lam[3] = {1.0, NL_LAMBDA_C, 1.0};
+  double om[3], sum = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double o = NL_EPS + dx * nl_indicator<M>(p[k]);
+    const double o2 = o * o;
+    om[k] = lam[k] / (o2 * o2);
+    sum += om[k];
+  }
+  const double is = 1.0 / sum;
+  b[0] = d[1];
+#pragma unroll
+  for (int q = 1; q <= 4; ++q) b[q] = q <= M ? (om[0] * p[0][q] + om[1] * p[1][q] + om[2] * p[2][q]) * is : 0.0;
+}
+
 // Taylor coefficients at the right edge (side = +1) or left edge (side = -1).
 template <int M>
 GRP_HD __forceinline__ void edge_taylor(const double b[5], double side, double t[M + 1])
@@ -631,6 +717,14 @@ GRP_HD __forceinline__ void char_proj(const Eig& e, const double D[3], double w[
   w[2] = 0.5 * ((e.b2 - uc) * D[0] - (e.b1 * e.u - e.ic) * D[1] + e.b1 * D[2]);
 }
 
+// characteristic amplitudes w back to conserved variables: D = sum_j w_j r_j
+GRP_HD __forceinline__ void char_back(const Eig& e, const double w[3], double D[3])
+{
+  D[0] = w[0] + w[1] + w[2];
+  D[1] = (e.u - e.c) * w[0] + e.u * w[1] + (e.u + e.c) * w[2];
+  D[2] = (e.H - e.u * e.c) * w[0] + 0.5 * e.u * e.u * w[1] + (e.H + e.u * e.c) * w[2];
+}
+
 GRP_HD __forceinline__ void deriv_rp(const Eig& e, const double DL[3], const double DR[3], double D[3])
 {
   double wl[3], wr[3], w[3];
@@ -639,9 +733,7 @@ GRP_HD __forceinline__ void deriv_rp(const Eig& e, const double DL[3], const dou
 #pragma unroll
   for (int j = 0; j < 3; ++j)
     w[j] = e.lam[j] > e.tie ? wl[j] : (e.lam[j] < -e.tie ? wr[j] : 0.5 * (wl[j] + wr[j]));
-  D[0] = w[0] + w[1] + w[2];
-  D[1] = (e.u - e.c) * w[0] + e.u * w[1] + (e.u + e.c) * w[2];
-  D[2] = (e.H - e.u * e.c) * w[0] + 0.5 * e.u * e.u * w[1] + (e.H + e.u * e.c) * w[2];
+  char_back(e, w, D);
 }
 
 // ---------------------------------------------------------------------------

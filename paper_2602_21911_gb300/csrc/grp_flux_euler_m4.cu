@@ -1,23 +1,7 @@
-// Flux and persistent batched kernels of the Euler equations, M = 4
-// (gamma = 7/5 fast path and generic gamma).
-#include "grp_kernels.cuh"
-#include "grp_launch.h"
+// Flux and persistent batched kernels of the Euler equations, M = 4, GRPrec
+// reconstruction (gamma = 7/5 fast path and generic gamma).
+#include "grp_flux_inst.cuh"
 
 namespace grp {
-cudaError_t launch_flux_euler_m4(const StepArgs& a, cudaStream_t s)
-{
-  const unsigned g = (unsigned)((a.nif + 127) / 128);
-  if (a.ph.gamma == 1.4) k_flux<SYS_EULER, 4, true><<<g, 128, 0, s>>>(a);
-  else k_flux<SYS_EULER, 4, false><<<g, 128, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_batch_euler_m4(const BatchLaunch& L, cudaStream_t s)
-{
-  if (L.a.ph.gamma == 1.4)
-    k_batch<SYS_EULER, 4, true><<<L.blocks, L.threads, 0, s>>>(L.a, L.grp, L.nsteps, L.parity, L.A0, L.A1, L.I0, L.I1);
-  else
-    k_batch<SYS_EULER, 4, false><<<L.blocks, L.threads, 0, s>>>(L.a, L.grp, L.nsteps, L.parity, L.A0, L.A1, L.I0, L.I1);
-  return cudaGetLastError();
-}
+GRP_DEFINE_EULER_LAUNCHERS(4, false, m4)
 }  // namespace grp

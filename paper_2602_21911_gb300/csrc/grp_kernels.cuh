@@ -29,6 +29,7 @@ struct DomStep {
 
 struct StepArgs {
   int sys, M, C;
+  int recon;                         // 0 GRPrec (Section 3.1), 1 GRPrecNL (Sections 3.3-3.4)
   Phys ph;
   double cfl, t_end;
   int dt_hold;
@@ -197,19 +198,68 @@ static __global__ void k_smax(StepArgs a)
 // Taylor coefficients (scaled) of cell `cell`'s reconstruction at its right
 // (side = +1) or left (side = -1) edge, component c; with the degree-0
 // fallback when the cell's traces are inadmissible (Euler).
-template <int SYS, int M>
+// NL: GRPrecNL, in characteristic variables of the cell average for the
+// Euler equations (Section 3.1: systems are reconstructed in characteristic
+// variables; linear GRPrec commutes with that projection and runs on the
+// conserved variables directly).
+template <int SYS, int M, bool NL>
 __device__ __forceinline__ void cell_coeffs(const StepArgs& a, long long c0, long long i0, int N, int bc, int i,
                                             double b[3][5], bool& fallback)
 {
   int im, ip;
   nbr(i, N, bc, im, ip);
   const int jl = i, jr = (bc == 0) ? (i == N - 1 ? 0 : i + 1) : i + 1;
+  constexpr int C = SYS == SYS_EULER ? 3 : 1;
+  if (!NL) {
 #pragma unroll
-  for (int c = 0; c < (SYS == SYS_EULER ? 3 : 1); ++c) {
-    const double* A = a.avg + c * a.ncell + c0;
-    const double* G = a.ifc + c * a.nif + i0;
-    const double qm = (M >= 3) ? A[im] : 0.0, qp = (M >= 3) ? A[ip] : 0.0;
-    grprec_coeffs<M>(qm, A[i], qp, G[jl], G[jr], b[c]);
+    for (int c = 0; c < C; ++c) {
+      const double* A = a.avg + c * a.ncell + c0;
+      const double* G = a.ifc + c * a.nif + i0;
+      const double qm = (M >= 3) ? A[im] : 0.0, qp = (M >= 3) ? A[ip] : 0.0;
+      grprec_coeffs<M>(qm, A[i], qp, G[jl], G[jr], b[c]);
+    }
+  } else {
+    // the further interfaces i-3/2, i+3/2; outside a transmissive end the
+    // ghost state (the boundary cell's average) holds on its interfaces too
+    const int jll = bc == 0 ? (i == 0 ? N - 1 : i - 1) : i - 1;
+    const int jrr = bc == 0 ? (jr == N - 1 ? 0 : jr + 1) : i + 2;
+    double d[C][7];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const double* A = a.avg + c * a.ncell + c0;
+      const double* G = a.ifc + c * a.nif + i0;
+      d[c][0] = A[im]; d[c][1] = A[i]; d[c][2] = A[ip];
+      d[c][3] = jll < 0 ? A[0] : G[jll];
+      d[c][4] = G[jl]; d[c][5] = G[jr];
+      d[c][6] = (bc != 0 && jrr > N) ? A[N - 1] : G[jrr];
+    }
+    const double dx = a.dx[(int)a.cell_dom[c0 + i]];
+    if (SYS == SYS_EULER) {
+      const double Qi[3] = {d[0][1], d[1][1], d[2][1]};
+      const Eig e = make_eig(a.ph, Qi, to_prim(a.ph.gamma, Qi[0], Qi[1], Qi[2]));
+      double w[3][7];
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        const double D[3] = {d[0][j], d[1][j], d[2][j]};
+        double v[3];
+        char_proj(e, D, v);
+        w[0][j] = v[0]; w[1][j] = v[1]; w[2][j] = v[2];
+      }
+      double bw[3][5];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) grprec_nl_coeffs<M>(w[k], dx, bw[k]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) b[c][0] = d[c][1];
+#pragma unroll
+      for (int q = 1; q <= 4; ++q) {
+        const double v[3] = {bw[0][q], bw[1][q], bw[2][q]};
+        double D[3];
+        char_back(e, v, D);
+        b[0][q] = D[0]; b[1][q] = D[1]; b[2][q] = D[2];
+      }
+    } else {
+      grprec_nl_coeffs<M>(d[0], dx, b[0]);
+    }
   }
   fallback = false;
   if (SYS == SYS_EULER) {
@@ -248,7 +298,7 @@ static __device__ int first_order(const StepArgs& a, long long c0, int N, int bc
 }
 
 // ------------------------------------------------------------------ k_flux
-template <int SYS, int M, bool G75>
+template <int SYS, int M, bool G75, bool NL>
 __device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d, unsigned st[8])
 {
   const long long i0 = a.if_off[d], c0 = a.cell_off[d];
@@ -275,7 +325,7 @@ __device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d,
   if (cl >= 0) {
     double b[3][5];
     bool fb;
-    cell_coeffs<SYS, M>(a, c0, i0, N, bc, cl, b, fb);
+    cell_coeffs<SYS, M, NL>(a, c0, i0, N, bc, cl, b, fb);
     st[5] = fb ? 1u : 0u;                      // counted once per cell: at its right interface
 #pragma unroll
     for (int c = 0; c < C; ++c) edge_taylor<M>(b[c], 1.0, tL[c]);
@@ -290,7 +340,7 @@ __device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d,
   if (cr >= 0) {
     double b[3][5];
     bool fb;
-    cell_coeffs<SYS, M>(a, c0, i0, N, bc, cr, b, fb);
+    cell_coeffs<SYS, M, NL>(a, c0, i0, N, bc, cr, b, fb);
 #pragma unroll
     for (int c = 0; c < C; ++c) edge_taylor<M>(b[c], -1.0, tR[c]);
   } else {
@@ -354,7 +404,7 @@ __device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d,
 // At least 3 blocks of 128 per SM: that lets the compiler keep about 130
 // registers per thread, which measured 11 % faster on the batched workload
 // than the ~108 it picks for 128-thread blocks without the bound.
-template <int SYS, int M, bool G75>
+template <int SYS, int M, bool G75, bool NL>
 __global__ void __launch_bounds__(128, 3) k_flux(StepArgs a)
 {
   const long long gj = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -364,7 +414,7 @@ __global__ void __launch_bounds__(128, 3) k_flux(StepArgs a)
   int d = -1;
   if (gj < a.nif) {
     d = a.if_dom[gj];
-    flux_one<SYS, M, G75>(a, gj, d, st);
+    flux_one<SYS, M, G75, NL>(a, gj, d, st);
   }
   __syncwarp();
   if (SYS == SYS_EULER) {
@@ -635,7 +685,7 @@ static __global__ void k_finish(StepArgs a)
 // step (reset, S_max, GRP fluxes, update, repair rounds, bookkeeping) is local
 // to the block, separated by __syncthreads, so one launch covers nsteps steps.
 // Buffers alternate per step starting from `parity` (0: A0/I0 current).
-template <int SYS, int M, bool G75>
+template <int SYS, int M, bool G75, bool NL>
 __global__ void __launch_bounds__(256, 2) k_batch(StepArgs a, const int* __restrict__ grp, int nsteps, int parity,
                                                double* A0, double* A1, double* I0, double* I1)
 {
@@ -665,7 +715,7 @@ __global__ void __launch_bounds__(256, 2) k_batch(StepArgs a, const int* __restr
       int d = -1;
       if (gj < ie) {
         d = a.if_dom[gj];
-        flux_one<SYS, M, G75>(w, gj, d, st);
+        flux_one<SYS, M, G75, NL>(w, gj, d, st);
       }
       __syncwarp();
       if (SYS == SYS_EULER) {

@@ -1,5 +1,6 @@
 // Host-side launchers of the templated kernels (one translation unit per
-// system and degree, so the heavy FP64 instantiations compile in parallel).
+// system, degree and reconstruction, so the heavy FP64 instantiations compile
+// in parallel).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -16,6 +17,16 @@ struct BatchLaunch {
 };
 
 cudaError_t launch_flux_adv(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_flux_adv_nl(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_batch_adv_nl(const BatchLaunch& L, cudaStream_t s);
+cudaError_t launch_flux_euler_m1_nl(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_flux_euler_m2_nl(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_flux_euler_m3_nl(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_flux_euler_m4_nl(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_batch_euler_m1_nl(const BatchLaunch& L, cudaStream_t s);
+cudaError_t launch_batch_euler_m2_nl(const BatchLaunch& L, cudaStream_t s);
+cudaError_t launch_batch_euler_m3_nl(const BatchLaunch& L, cudaStream_t s);
+cudaError_t launch_batch_euler_m4_nl(const BatchLaunch& L, cudaStream_t s);
 cudaError_t launch_flux_euler_m1(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_flux_euler_m2(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_flux_euler_m3(const StepArgs& a, cudaStream_t s);

@@ -129,6 +129,7 @@ extern "C" int grp_step_noalloc(int system, double lambda, double gamma, int M, 
 
   StepArgs a;
   a.sys = system; a.M = M; a.C = system == GRP_EULER_IDEAL ? 3 : 1;
+  a.recon = GRP_RECON_GRPREC;
   a.ph = make_phys(lambda, gamma, 1e-12, 50, 0);
   a.cfl = cfl; a.t_end = t_end; a.dt_hold = 1;
   a.n_domains = 1; a.ncell = N; a.nif = nif;

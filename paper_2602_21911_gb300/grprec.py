@@ -31,7 +31,7 @@ class grp_problem(ctypes.Structure):
                 ("x_right", ctypes.POINTER(ctypes.c_double)), ("bc", ctypes.POINTER(ctypes.c_int)),
                 ("newton_rtol", ctypes.c_double), ("newton_max_iter", ctypes.c_int),
                 ("guess", ctypes.c_int), ("dt_hold", ctypes.c_int), ("device", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("recon", ctypes.c_int)]
 
 
 class GrpError(RuntimeError):
@@ -98,6 +98,7 @@ def grp_probe_fp64_peak(device=0):
 
 
 GRP_NOALLOC_MAX_CELLS = 65536
+GRP_RECON_GRPREC, GRP_RECON_GRPRECNL = 0, 1
 GRP_MLP_NPARAM = 4673
 
 
@@ -216,6 +217,7 @@ class Solver:
         p.dt_hold = int(prob.get("dt_hold", 1) if dt_hold is None else dt_hold)
         p.device = int(device)
         p.stream = stream
+        p.recon = int(prob.get("recon", GRP_RECON_GRPREC))
         self.prob = prob
         self.C = 3 if p.system == GRP_EULER_IDEAL else 1
         self.D = p.n_domains

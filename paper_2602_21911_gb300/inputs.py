@@ -84,6 +84,66 @@ def advection_sin4_exact(N, t):
 
 
 # --------------------------------------------------------------------------
+# The paper's discontinuous advection tests on periodic [-1, 1] (Section 4.2):
+# the square wave (1 on [-0.3, 0.3]) and the Jiang-Shu multi-wave profile.
+# Averages by Gauss-Legendre quadrature on the smooth pieces of each cell;
+# interface data are the one-sided limits.
+# --------------------------------------------------------------------------
+def _square(x):
+    return np.where((x >= -0.3) & (x <= 0.3), 1.0, 0.0)
+
+
+def _multiwave(x):
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    m = (x >= -0.8) & (x <= -0.6)
+    out[m] = np.exp(-math.log(2.0) * (x[m] + 0.7) ** 2 / 0.0009)
+    m = (x >= -0.4) & (x <= -0.2)
+    out[m] = 1.0
+    m = (x >= 0.0) & (x <= 0.2)
+    out[m] = 1.0 - np.abs(10.0 * x[m] - 1.0)
+    m = (x >= 0.4) & (x <= 0.6)
+    out[m] = np.sqrt(np.maximum(1.0 - 100.0 * (x[m] - 0.5) ** 2, 0.0))
+    return out
+
+
+def _piecewise_avg(f, breaks, xl, xr, n_gauss=16):
+    """Cell averages of f, integrating each smooth piece separately."""
+    xs, ws = np.polynomial.legendre.leggauss(n_gauss)
+    out = np.zeros(len(xl))
+    for i, (a, b) in enumerate(zip(xl, xr)):
+        pts = [a] + [p for p in breaks if a < p < b] + [b]
+        acc = 0.0
+        for u, v in zip(pts[:-1], pts[1:]):
+            acc += 0.5 * (v - u) * np.dot(ws, f(0.5 * (v - u) * xs + 0.5 * (u + v)))
+        out[i] = acc / (b - a)
+    return out
+
+
+def _advection_profile(N, M, f, breaks, cfl):
+    e, dx = _edges(-1.0, 1.0, N)
+    avg = _piecewise_avg(f, breaks, e[:-1], e[1:])[None, :]
+    eps = 1e-13
+    minus = f(e[:-1] - eps)[None, :]            # left limits
+    plus = f(e[:-1] + eps)[None, :]             # right limits
+    prob = _problem(ADVECTION, M, cfl, [N], [-1.0], [1.0], [PERIODIC])
+    return prob, avg, minus, plus
+
+
+def advection_square(N, M=2, cfl=0.9):
+    return _advection_profile(N, M, _square, [-0.3, 0.3], cfl)
+
+
+def advection_multiwave(N, M=2, cfl=0.9):
+    return _advection_profile(N, M, _multiwave, [-0.8, -0.6, -0.4, -0.2, 0.0, 0.1, 0.2, 0.4, 0.6], cfl)
+
+
+def euler_123(N, M=2, cfl=0.9, gamma=1.4):
+    """The 123 problem (Section 4.3): (1, -2, 0.4) | (1, 2, 0.4) at x = 0.5."""
+    return riemann_problem(N, (1.0, -2.0, 0.4), (1.0, 2.0, 0.4), M=M, cfl=cfl, xc=0.5, gamma=gamma)
+
+
+# --------------------------------------------------------------------------
 # Euler smooth density wave on periodic [0, 1]: rho = 1 + A sin(2 pi (x - t)),
 # u = 1, p = p0; exact solution is the translated wave.
 # --------------------------------------------------------------------------
