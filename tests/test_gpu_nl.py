@@ -1,0 +1,66 @@
+"""GPU GRPrecNL (Sections 3.3-3.4) against the oracle: smooth and
+discontinuous advection, the Euler density wave, the shock tube, the 123
+problem, transmissive ghost handling at degree 4, and every launch form on a
+batch of domains."""
+import numpy as np
+import pytest
+
+from paper_2602_21911_gb300 import inputs as I
+
+from parity import DISC_TOL, SMOOTH_TOL, check_parity
+
+pytestmark = pytest.mark.gpu
+
+NL = 1
+
+
+def _nl(prob):
+    return dict(prob, recon=NL)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+def test_advection_sine(M):
+    prob, avg, lm, lp = I.advection_sine(80, M=M)
+    check_parity(_nl(prob), avg, lm, lp, 10 ** 6, SMOOTH_TOL, t_end=1.0)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+def test_square_wave(M):
+    prob, avg, lm, lp = I.advection_square(50, M=M)
+    check_parity(_nl(prob), avg, lm, lp, 10 ** 6, DISC_TOL, t_end=4.0)
+
+
+def test_multiwave_many_periods():
+    prob, avg, lm, lp = I.advection_multiwave(100, M=2)
+    check_parity(_nl(prob), avg, lm, lp, 10 ** 6, DISC_TOL, t_end=20.0)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+def test_euler_wave(M):
+    prob, avg, lm, lp = I.euler_wave(64, M)
+    check_parity(_nl(prob), avg, lm, lp, 10 ** 6, SMOOTH_TOL, t_end=1.0)
+
+
+def test_euler_wave_transmissive_degree4_ghosts():
+    prob, avg, lm, lp = I.euler_wave(77, 4, bc=I.TRANSMISSIVE)
+    check_parity(_nl(prob), avg, lm, lp, 60, SMOOTH_TOL)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+def test_sod(M):
+    prob, avg, lm, lp = I.sod(200, M=M, xc=0.3)
+    check_parity(_nl(prob), avg, lm, lp, 10 ** 6, DISC_TOL, t_end=0.2)
+
+
+def test_123_problem():
+    prob, avg, lm, lp = I.euler_123(200, M=2)
+    check_parity(_nl(prob), avg, lm, lp, 10 ** 6, DISC_TOL, t_end=0.15)
+
+
+@pytest.mark.parametrize("form", [1, 2, 3])
+def test_batched_forms(form):
+    from paper_2602_21911_gb300 import grprec
+    prob, avg, lm, lp = I.batched(domains=np.arange(0, 65536, 331)[:150])
+    s = grprec.Solver(_nl(prob))
+    s.set_launch(form, 256, 2048, 4)
+    check_parity(_nl(prob), avg, lm, lp, 30, DISC_TOL, solver=s)
