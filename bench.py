@@ -217,11 +217,12 @@ def plain_arm(args, device, stream, w, box):
 
 
 def other_workloads(local, stream):
-    """Throughput of the single-domain configurations (context beside the
-    batched headline): the smooth Euler density wave at N = 8192 for M = 1..4
-    (plain single-domain path; launch-latency bound at this size), its L1
-    density error at t = 1 for M = 2, the shock tube at 2^22 cells (M = 2), and
-    the advection sine at N = 100 (M = 2) to t = 1."""
+    """Throughput of the other configurations (context beside the batched
+    headline): the smooth Euler density wave at N = 8192 for M = 1..4 (plain
+    single-domain path; launch-latency bound at this size), its L1 density
+    error at t = 1 for M = 2, the shock tube at 2^22 cells (M = 2), the batch
+    and the shock tube with the GRPrecNL reconstruction, and the advection sine
+    at N = 100 (M = 2) to t = 1."""
     import torch
     from paper_2602_21911_gb300 import grprec, inputs as I
     out = {}
@@ -261,6 +262,22 @@ def other_workloads(local, stream):
     ms = timed(s, 64)
     out["sod_N4194304_M2"] = {"cell_updates_per_s": (1 << 22) / (ms * 1e-3), "ms_per_step": ms,
                               "window": "steps 9..72 of t_end = 0.2"}
+    s.close()
+    # GRPrecNL (Sections 3.3-3.4): the batch and the shock tube
+    prob, avg, lm, lp = I.batched(65536, seed=2602, M=2)
+    s = grprec.Solver(dict(prob, recon=grprec.GRP_RECON_GRPRECNL), device=local, stream=stream.cuda_stream)
+    s.set_launch(grprec.GRP_LAUNCH_FLAT)
+    s.set_initial(avg, lm, lp)
+    ms = timed(s, 32)
+    cells = int(prob["n_cells"].sum())
+    out["batched_grprecnl_M2"] = {"cell_updates_per_s": cells / (ms * 1e-3), "ms_per_step": ms,
+                                  "launch": "flat", "window": "steps 9..40"}
+    s.close()
+    prob, avg, lm, lp = I.sod(1 << 22, M=2)
+    s = grprec.Solver(dict(prob, recon=grprec.GRP_RECON_GRPRECNL), device=local, stream=stream.cuda_stream)
+    s.set_initial(avg, lm, lp)
+    ms = timed(s, 32)
+    out["sod_N4194304_M2_grprecnl"] = {"cell_updates_per_s": (1 << 22) / (ms * 1e-3), "ms_per_step": ms}
     s.close()
     prob, avg, lm, lp = I.advection_sine(100, M=2)
     s = grprec.Solver(prob, device=local, stream=stream.cuda_stream)
