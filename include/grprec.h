@@ -49,6 +49,7 @@ enum { GRP_BC_PERIODIC = 0, GRP_BC_TRANSMISSIVE = 1 };            /* per-domain 
 enum { GRP_GUESS_PVRS = 0, GRP_GUESS_TRRS = 1, GRP_GUESS_MLP = 2 };/* Newton initial guess for p* */
 enum { GRP_LAUNCH_AUTO = 0, GRP_LAUNCH_FLAT = 1, GRP_LAUNCH_FUSED = 2, GRP_LAUNCH_SPLIT = 3 }; /* grp_set_launch */
 enum { GRP_RECON_GRPREC = 0, GRP_RECON_GRPRECNL = 1 };            /* reconstruction (Sections 3.1, 3.3-3.4) */
+enum { GRP_SOLVER_TT = 0, GRP_SOLVER_DET = 1 };                   /* GRP solver (Section 2, Section 4.1) */
 
 /* return codes */
 enum {
@@ -104,6 +105,14 @@ typedef struct {
                             of Sections 3.3-3.4 (weights r = 4, eps = 1e-14, lambda_C = 1e9), in
                             characteristic variables of the cell average for the Euler equations
                             (Section 3.1).  grp_step_noalloc always uses GRPrec. */
+  int solver;            /* GRP_SOLVER_TT: Toro-Titarev (exact leading Riemann problem, derivative
+                            Riemann problems, Cauchy-Kovalevskaya series, Gauss quadrature);
+                            GRP_SOLVER_DET: the solver of the paper's computations (Section 4.1), a
+                            space-time Galerkin predictor per cell (degree M in space and time, M+1
+                            Gauss-Legendre nodes, Picard iteration to 1e-13) and exact Riemann
+                            problems of the evolved edge values at the M+1 time nodes (flux) and at
+                            the end of the step (interface datum).  DET runs the FLAT launch form
+                            whatever grp_set_launch asks; grp_step_noalloc always uses TT. */
 } grp_problem;
 
 /*

@@ -18,6 +18,7 @@ from . import build as _build
 
 ADVECTION, EULER = 0, 1
 RECON_GRPREC, RECON_GRPRECNL = 0, 1
+SOLVER_TT, SOLVER_DET = 0, 1
 PERIODIC, TRANSMISSIVE = 0, 1
 GUESS_PVRS, GUESS_TRRS, GUESS_GIVEN = 0, 1, 2
 OK, NEWTON_NO_CONV, VACUUM, NONPHYSICAL = 0, 1, 2, 3
@@ -56,6 +57,10 @@ def lib():
                                 ctypes.c_double, ctypes.c_int, _I, _D, _D, _I, ctypes.c_double,
                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _I, _D, _I,
                                 ctypes.c_int, ctypes.c_double, _L, _D, ctypes.c_int]
+        L.or_run_solver.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_double, ctypes.c_int, _I, _D, _D, _I,
+                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _I,
+                                    _D, _I, ctypes.c_int, ctypes.c_double, _L, _D, ctypes.c_int]
         L.or_recon_nl.argtypes = [ctypes.c_int, _D, ctypes.c_double, _D, _D]
         L.or_char_basis.argtypes = [ctypes.c_double, _D, _D, _D]
         _lib = L
@@ -174,7 +179,7 @@ def run(prob, state, n_steps, t_end=np.inf, dt_fixed=None, n_threads=1):
     """Advance ``state`` in place by n_steps or to t_end (Section 2 update).
 
     ``prob`` keys: system, lam, gamma, M, cfl, n_cells, x_left, x_right, bc,
-    newton_rtol, newton_max_iter, guess, dt_hold, recon (optional).
+    newton_rtol, newton_max_iter, guess, dt_hold, recon and solver (optional).
     """
     n_cells = np.ascontiguousarray(prob["n_cells"], dtype=np.int32)
     xl = _f64(prob["x_left"])
@@ -184,8 +189,8 @@ def run(prob, state, n_steps, t_end=np.inf, dt_fixed=None, n_threads=1):
     if dt_fixed is not None:
         dtf = _f64(dt_fixed)
         assert len(dtf) >= n_steps
-    rc = lib().or_run_ex(prob["system"], prob.get("lam", 1.0), prob.get("gamma", 1.4), prob["M"],
-                      prob.get("recon", RECON_GRPREC), prob["cfl"], len(n_cells), _ip(n_cells), _dp(xl), _dp(xr), _ip(bc),
+    rc = lib().or_run_solver(prob["system"], prob.get("lam", 1.0), prob.get("gamma", 1.4), prob["M"],
+                      prob.get("recon", RECON_GRPREC), prob.get("solver", SOLVER_TT), prob["cfl"], len(n_cells), _ip(n_cells), _dp(xl), _dp(xr), _ip(bc),
                       prob.get("newton_rtol", 1e-12), prob.get("newton_max_iter", 50),
                       prob.get("guess", GUESS_PVRS), prob.get("dt_hold", 1),
                       _dp(state.avg), _dp(state.iface), _dp(state.t), _ip(state.nstep),

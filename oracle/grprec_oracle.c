@@ -818,12 +818,180 @@ int or_init_iface(int system, double lambda, double gamma, int n_ifaces,
 }
 
 /* ------------------------------------------------------------------------- */
+/* The DET GRP solver (the solver of the paper's computations; Section 2 and  */
+/* Section 4.1): in each cell a local space-time Galerkin predictor evolves   */
+/* the reconstruction over [t^n, t^n + dt]; at each interface classical       */
+/* Riemann problems of the two evolved edge values at the time integration   */
+/* points give the flux, and the one at the end of the step the interface    */
+/* datum.  READING: the predictor is the standard locally implicit one: a     */
+/* tensor-product nodal basis of degree M in space and time on M+1 Gauss-     */
+/* Legendre points, the time derivative integrated by parts with upwinding   */
+/* from the reconstruction at t^n, nodal quadrature, solved by Picard        */
+/* iteration until the largest update is below 1e-13 of the largest nodal    */
+/* value (at most 64 iterations).  The Riemann problems are solved exactly   */
+/* (this build's solver) for the flux and for the interface datum; the        */
+/* paper's two-rarefaction estimate for the Euler interface data is not       */
+/* taken.  Time points: the M+1 predictor nodes.                              */
+/* ------------------------------------------------------------------------- */
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+#define DET_N (MAXM + 1)
+typedef struct {
+  int n;
+  double x[DET_N], w[DET_N];            /* Gauss-Legendre nodes and weights on [0, 1] */
+  double D[DET_N][DET_N];               /* D[k][a] = phi_a'(x_k) */
+  double e0[DET_N], e1[DET_N];          /* phi_a(0), phi_a(1) */
+  double Tinv[DET_N][DET_N];            /* inverse of T_lb = phi_l(1) phi_b(1) - w_b phi_l'(x_b) */
+} det_basis;
+
+static det_basis det_tab[MAXM + 1];
+static int det_ready[MAXM + 1];
+
+static void gauss_legendre01(int n, double *x, double *w)
+{
+  for (int k = 0; k < n; ++k) {
+    double z = cos(M_PI * (k + 0.75) / (n + 0.5)), pp = 0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1, p1 = z;
+      for (int j = 2; j <= n; ++j) { double p2 = ((2 * j - 1) * z * p1 - (j - 1) * p0) / j; p0 = p1; p1 = p2; }
+      if (n == 1) { p1 = z; p0 = 1; }
+      pp = n * (z * p1 - p0) / (z * z - 1);
+      double dz = p1 / pp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[n - 1 - k] = 0.5 * (z + 1);
+    w[n - 1 - k] = 1.0 / ((1 - z * z) * pp * pp);       /* 2/((1-z^2)P'^2) on [-1,1], halved */
+  }
+}
+
+static double lagrange(int n, const double *x, int a, double s)
+{
+  double v = 1;
+  for (int j = 0; j < n; ++j) if (j != a) v *= (s - x[j]) / (x[a] - x[j]);
+  return v;
+}
+
+static double lagrange_d(int n, const double *x, int a, double s)
+{
+  double tot = 0;
+  for (int m = 0; m < n; ++m) {
+    if (m == a) continue;
+    double v = 1 / (x[a] - x[m]);
+    for (int j = 0; j < n; ++j) if (j != a && j != m) v *= (s - x[j]) / (x[a] - x[j]);
+    tot += v;
+  }
+  return tot;
+}
+
+static const det_basis *det_basis_for(int M)
+{
+  if (!det_ready[M]) {
+    det_basis *B = &det_tab[M];
+    int n = M + 1;
+    B->n = n;
+    gauss_legendre01(n, B->x, B->w);
+    for (int a = 0; a < n; ++a) {
+      B->e0[a] = lagrange(n, B->x, a, 0.0);
+      B->e1[a] = lagrange(n, B->x, a, 1.0);
+      for (int k = 0; k < n; ++k) B->D[k][a] = lagrange_d(n, B->x, a, B->x[k]);
+    }
+    for (int col = 0; col < n; ++col) {
+      double T[DET_N * DET_N], e[DET_N];
+      for (int l = 0; l < n; ++l) {
+        for (int b = 0; b < n; ++b) T[l * n + b] = B->e1[l] * B->e1[b] - B->w[b] * B->D[b][l];
+        e[l] = l == col ? 1 : 0;
+      }
+      solve_dense_d(n, T, e);
+      for (int l = 0; l < n; ++l) B->Tinv[l][col] = e[l];
+    }
+    det_ready[M] = 1;
+  }
+  return &det_tab[M];
+}
+
+static void phys_flux(int system, real lambda, real gamma, const real *Q, real *F)
+{
+  if (system == OR_ADVECTION) F[0] = lambda * Q[0];
+  else euler_flux(gamma, Q, F);
+}
+
+/* Predictor of one cell from its reconstruction (monomial coefficients in
+ * xi = s - 1/2 per component); nu = dt/dx.  Out: edge values at the time
+ * nodes and at the end of the step, ed[side][g][c] for g = 0..M (nodes) and
+ * g = M+1 (tau = 1), side 0 the left edge (s = 0), 1 the right edge.
+ * Returns 0, or -1 when a nodal state is inadmissible (Euler). */
+static int det_predict(int system, real lambda, real gamma, int M, real nu, const real *coef /* [C][MAXM+1] */,
+                       real ed[2][DET_N + 1][MAXC])
+{
+  const det_basis *B = det_basis_for(M);
+  const int n = B->n, C = system == OR_EULER ? 3 : 1;
+  real w[DET_N][MAXC], q[DET_N][DET_N][MAXC], f[DET_N][DET_N][MAXC];
+  for (int k = 0; k < n; ++k)
+    for (int c = 0; c < C; ++c) {
+      real xi = B->x[k] - 0.5, v = 0;
+      for (int j = M; j >= 0; --j) v = v * xi + coef[c * (MAXM + 1) + j];
+      w[k][c] = v;
+      for (int l = 0; l < n; ++l) q[k][l][c] = v;
+    }
+  for (int it = 0; it < 64; ++it) {
+    for (int k = 0; k < n; ++k)
+      for (int l = 0; l < n; ++l) {
+        if (system == OR_EULER && !euler_admissible(gamma, q[k][l])) return -1;
+        phys_flux(system, lambda, gamma, q[k][l], f[k][l]);
+      }
+    real diff = 0, scale = 0;
+    real qn[DET_N][DET_N][MAXC];
+    for (int k = 0; k < n; ++k)
+      for (int c = 0; c < C; ++c) {
+        real rhs[DET_N];
+        for (int l = 0; l < n; ++l) {
+          real df = 0;
+          for (int a = 0; a < n; ++a) df = df + B->D[k][a] * f[a][l][c];
+          rhs[l] = B->e0[l] * w[k][c] - nu * B->w[l] * df;
+        }
+        for (int l = 0; l < n; ++l) {
+          real v = 0;
+          for (int b = 0; b < n; ++b) v = v + B->Tinv[l][b] * rhs[b];
+          qn[k][l][c] = v;
+          real dv = fabs(v - q[k][l][c]);
+          if (dv > diff) diff = dv;
+          if (fabs(v) > scale) scale = fabs(v);
+        }
+      }
+    memcpy(q, qn, sizeof(q));
+    if (diff <= 1e-13 * scale) break;
+  }
+  if (system == OR_EULER)
+    for (int k = 0; k < n; ++k)
+      for (int l = 0; l < n; ++l)
+        if (!euler_admissible(gamma, q[k][l])) return -1;
+  for (int side = 0; side < 2; ++side) {
+    const double *ex = side ? B->e1 : B->e0;
+    for (int c = 0; c < C; ++c) {
+      for (int g = 0; g < n; ++g) {
+        real v = 0;
+        for (int a = 0; a < n; ++a) v = v + ex[a] * q[a][g][c];
+        ed[side][g][c] = v;
+      }
+      real v = 0;
+      for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) v = v + ex[a] * B->e1[b] * q[a][b][c];
+      ed[side][n][c] = v;
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* One step of one domain: FV update (eq. eq_finite_volume, Section 2).      */
 /* ------------------------------------------------------------------------- */
 typedef struct {
   int system; real lambda, gamma; int M; real cfl;
   real rtol; int max_iter; int guess_kind; int dt_hold;
   int recon;                  /* OR_RECON_GRPREC or OR_RECON_GRPRECNL */
+  int solver;                 /* OR_SOLVER_TT or OR_SOLVER_DET */
 } params;
 
 /* Time-step rule (Section 4.1): dt = C dx / S_max, S_max over the cell averages.
@@ -967,9 +1135,68 @@ static int step_domain(const params *P, int N, int bc, real dx, real dt, real *a
     }
   }
 
+  if (P->solver == OR_SOLVER_DET) {
+    /* predictor in every cell; a cell whose predictor meets an inadmissible
+     * state keeps its cell average, unevolved (READING, counted with the
+     * reconstruction fallbacks) */
+    const int n = M + 1;
+    real (*ed)[2][DET_N + 1][MAXC] = malloc(sizeof(*ed) * N);
+    real nu = dt / dx;
+    for (int i = 0; i < N; ++i) {
+      if (det_predict(P->system, P->lambda, P->gamma, M, nu, coef + i * C * (MAXM + 1), ed[i]) != 0) {
+        for (int side = 0; side < 2; ++side)
+          for (int g = 0; g <= n; ++g)
+            for (int c = 0; c < C; ++c) ed[i][side][g][c] = avg[c * cstride + i];
+        st[OR_ST_RECON_FB] += 1;
+      }
+    }
+    const det_basis *B = det_basis_for(M);
+    for (int j = 0; j < nif && status == OR_OK; ++j) {
+      int cl, cr;
+      if (bc == OR_BC_PERIODIC) { cl = (j - 1 + N) % N; cr = j; }
+      else { cl = j - 1; cr = j; }               /* -1 or N: the constant ghost */
+      int fo = 0;
+      real Fsum[3] = { 0, 0, 0 };
+      for (int g = 0; g <= n && !fo; ++g) {
+        real QL[3], QR[3], Q0[3], F[3];
+        for (int c = 0; c < C; ++c) {
+          QL[c] = cl < 0 ? avg[c * cstride + 0] : ed[cl][1][g][c];
+          QR[c] = cr > N - 1 ? avg[c * cstride + N - 1] : ed[cr][0][g][c];
+        }
+        if (P->system == OR_ADVECTION) {
+          Q0[0] = P->lambda > 0 ? QL[0] : (P->lambda < 0 ? QR[0] : 0.5 * (QL[0] + QR[0]));
+        } else {
+          int it = 0;
+          if (!euler_admissible(P->gamma, QL) || !euler_admissible(P->gamma, QR)) { fo = 1; break; }
+          int rs = riemann_state(P->gamma, QL, QR, P->guess_kind, 0, P->rtol, P->max_iter, 0, Q0, &it);
+          st[OR_ST_RS_CALLS] += 1;
+          st[OR_ST_NEWTON_SUM] += it;
+          if (it > st[OR_ST_NEWTON_MAX]) st[OR_ST_NEWTON_MAX] = it;
+          if (rs != OR_OK) { fo = 1; break; }
+        }
+        if (g < n) {
+          phys_flux(P->system, P->lambda, P->gamma, Q0, F);
+          for (int c = 0; c < C; ++c) Fsum[c] = Fsum[c] + B->w[g] * F[c];
+        } else {
+          for (int c = 0; c < C; ++c) gnew[j * C + c] = Q0[c];
+        }
+      }
+      if (fo) {
+        /* READING: an inadmissible evolved edge value or a Riemann problem
+         * without solution sends the interface to the first-order flux */
+        int s2 = first_order_interface(P, N, bc, j, avg, cstride, flux + j * C, gnew + j * C, st);
+        low[j] = 1;
+        if (s2 != OR_OK) status = s2;
+      } else {
+        for (int c = 0; c < C; ++c) flux[j * C + c] = Fsum[c];
+      }
+    }
+    free(ed);
+  }
+
   /* one GRP per interface.  READING (transmissive ends): the outside cell is a
    * ghost holding the boundary cell's average as a constant polynomial. */
-  for (int j = 0; j < nif && status == OR_OK; ++j) {
+  for (int j = 0; j < nif && status == OR_OK && P->solver != OR_SOLVER_DET; ++j) {
     int cl, cr;
     if (bc == OR_BC_PERIODIC) { cl = (j - 1 + N) % N; cr = j; }
     else { cl = j - 1; cr = j; }                  /* -1 or N: the ghost */
@@ -1069,7 +1296,19 @@ int or_run_ex(int system, double lambda, double gamma, int M, int recon, double 
               double *avg, double *iface, double *t, int *nstep, double *dt_prev, int *status,
               int n_steps, double t_end, long long *stats, const double *dt_fixed, int n_threads)
 {
+  return or_run_solver(system, lambda, gamma, M, recon, OR_SOLVER_TT, cfl, n_domains, n_cells, x_left, x_right,
+                       bc, newton_rtol, newton_max_iter, guess_kind, dt_hold, avg, iface, t, nstep, dt_prev,
+                       status, n_steps, t_end, stats, dt_fixed, n_threads);
+}
+
+int or_run_solver(int system, double lambda, double gamma, int M, int recon, int solver, double cfl,
+                  int n_domains, const int *n_cells, const double *x_left, const double *x_right,
+                  const int *bc, double newton_rtol, int newton_max_iter, int guess_kind, int dt_hold,
+                  double *avg, double *iface, double *t, int *nstep, double *dt_prev, int *status,
+                  int n_steps, double t_end, long long *stats, const double *dt_fixed, int n_threads)
+{
   params P;
+  P.solver = solver;
   P.system = system; P.lambda = lambda; P.gamma = gamma; P.M = M; P.cfl = cfl;
   P.rtol = newton_rtol; P.max_iter = newton_max_iter; P.guess_kind = guess_kind;
   P.dt_hold = dt_hold < 1 ? 1 : dt_hold;

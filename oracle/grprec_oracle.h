@@ -26,6 +26,7 @@ enum { OR_ADVECTION = 0, OR_EULER = 1 };
 enum { OR_BC_PERIODIC = 0, OR_BC_TRANSMISSIVE = 1 };
 enum { OR_GUESS_PVRS = 0, OR_GUESS_TRRS = 1, OR_GUESS_GIVEN = 2 };
 enum { OR_RECON_GRPREC = 0, OR_RECON_GRPRECNL = 1 };
+enum { OR_SOLVER_TT = 0, OR_SOLVER_DET = 1 };
 enum {
   OR_OK = 0,
   OR_NEWTON_NO_CONV = 1,
@@ -95,6 +96,16 @@ int or_run_ex(int system, double lambda, double gamma, int M, int recon, double 
               const int *bc, double newton_rtol, int newton_max_iter, int guess_kind, int dt_hold,
               double *avg, double *iface, double *t, int *nstep, double *dt_prev, int *status,
               int n_steps, double t_end, long long *stats, const double *dt_fixed, int n_threads);
+
+/* or_run_ex with the GRP solver chosen: OR_SOLVER_TT (Toro-Titarev: exact
+ * leading Riemann problem, derivative Riemann problems, Cauchy-Kovalevskaya)
+ * or OR_SOLVER_DET (space-time Galerkin predictor per cell, Riemann problems
+ * of the evolved edge values at the time integration points). */
+int or_run_solver(int system, double lambda, double gamma, int M, int recon, int solver, double cfl,
+                  int n_domains, const int *n_cells, const double *x_left, const double *x_right,
+                  const int *bc, double newton_rtol, int newton_max_iter, int guess_kind, int dt_hold,
+                  double *avg, double *iface, double *t, int *nstep, double *dt_prev, int *status,
+                  int n_steps, double t_end, long long *stats, const double *dt_fixed, int n_threads);
 
 #ifdef __cplusplus
 }

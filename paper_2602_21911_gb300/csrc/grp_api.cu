@@ -33,6 +33,7 @@ struct grp_ctx {
   double* flux = nullptr;
   double* pold = nullptr;        // pressure of the current averages (S_max pass)
   DomStep* ds = nullptr;         // per-domain time step of the current step
+  double* det_ed = nullptr;      // DET: evolved edge values of every cell
   unsigned char *low = nullptr, *troubled = nullptr;
   double *t = nullptr, *dt_prev = nullptr;
   int *nstep = nullptr, *status = nullptr;
@@ -113,7 +114,7 @@ void free_all(grp_ctx* c)
   c->ev_free.clear();
   c->ev_pending.clear();
   void* ptrs[] = {c->cell_off, c->if_off, c->cell_dom, c->if_dom, c->dx, c->bc, c->avg[0], c->avg[1],
-                  c->ifc[0], c->ifc[1], c->flux, c->pold, c->ds, c->low, c->troubled, c->t, c->dt_prev, c->nstep,
+                  c->ifc[0], c->ifc[1], c->flux, c->pold, c->ds, c->det_ed, c->low, c->troubled, c->t, c->dt_prev, c->nstep,
                   c->status, c->smax_bits, c->bad, c->inad, c->fail, c->any_bad, c->tlist0, c->tlist1,
                   c->ilist, c->lcount, c->stats,
                   c->scratch_norm, c->mlp, c->mlp_norm, c->grp};
@@ -213,6 +214,7 @@ cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s)
 // the launch form grp_step takes: FLAT, FUSED or SPLIT
 int launch_form(const grp_ctx* c)
 {
+  if (c->p.solver == GRP_SOLVER_DET) return GRP_LAUNCH_FLAT;     // DET has the flat form only
   if (c->mode != GRP_LAUNCH_AUTO) return c->mode;
   // auto: whole domains per block pay off when the batch has many short domains
   return c->D >= 1024 && c->max_cells <= 4096 ? GRP_LAUNCH_SPLIT : GRP_LAUNCH_FLAT;
@@ -322,8 +324,13 @@ int enqueue_step(grp_ctx* c, double t_end)
     }
     CK(record(c, e0));
   }
-  CK(launch_flux(a, s));
-  c->launches++;
+  if (c->p.solver == GRP_SOLVER_DET) {
+    CK(launch_det_step(a, c->det_ed, s));            // predictor, then the interface Riemann problems
+    c->launches += 2;
+  } else {
+    CK(launch_flux(a, s));
+    c->launches++;
+  }
   if (c->timing) {
     CK(record(c, e1));
     c->ev_pending.push_back(e0);
@@ -400,6 +407,7 @@ int grp_create(grp_ctx** out, const grp_problem* p)
   if (p->guess < GRP_GUESS_PVRS || p->guess > GRP_GUESS_MLP) return GRP_E_INVALID_ARG;
   if (p->dt_hold < 1) return GRP_E_INVALID_ARG;
   if (p->recon != GRP_RECON_GRPREC && p->recon != GRP_RECON_GRPRECNL) return GRP_E_INVALID_ARG;
+  if (p->solver != GRP_SOLVER_TT && p->solver != GRP_SOLVER_DET) return GRP_E_INVALID_ARG;
   grp_ctx* c = new grp_ctx();
   c->p = *p;
   c->p.n_cells = nullptr; c->p.x_left = nullptr; c->p.x_right = nullptr; c->p.bc = nullptr;
@@ -444,6 +452,10 @@ int grp_create(grp_ctx** out, const grp_problem* p)
   AL(status, D) AL(smax_bits, D) AL(bad, (MAX_REPAIR + 1) * D) AL(inad, D) AL(fail, D)
   AL(any_bad, MAX_REPAIR + 1) AL(stats, (long long)NSTATS * D) AL(scratch_norm, 3 * D)
   AL(tlist0, c->ncell) AL(tlist1, c->ncell) AL(ilist, c->nif) AL(lcount, 2 * (MAX_REPAIR + 1))
+  if (p->solver == GRP_SOLVER_DET) {
+    AL(det_ed, (long long)det_doubles_per_cell(p->M, C) * c->ncell)
+    if (det_prepare(p->device) != 0) { free_all(c); delete c; return cuda_fail(cudaErrorUnknown, "DET tables"); }
+  }
 #undef AL
   struct Cp { void* dst; const void* src; size_t n; } cps[] = {
       {c->cell_off, c->h_cell_off.data(), sizeof(long long) * (D + 1)},

@@ -37,5 +37,11 @@ cudaError_t launch_batch_euler_m2(const BatchLaunch& L, cudaStream_t s);
 cudaError_t launch_batch_euler_m3(const BatchLaunch& L, cudaStream_t s);
 cudaError_t launch_batch_euler_m4(const BatchLaunch& L, cudaStream_t s);
 cudaError_t launch_post_adv(const BatchLaunch& L, cudaStream_t s);
+
+// DET solver (grp_det.cu): constant tables of the device (once), the size of
+// the edge-value scratch, and the two launches of a step's GRP phase
+int det_prepare(int device);
+size_t det_doubles_per_cell(int M, int C);
+cudaError_t launch_det_step(const StepArgs& a, double* ed, cudaStream_t s);
 cudaError_t launch_post_euler(const BatchLaunch& L, cudaStream_t s);
 }  // namespace grp

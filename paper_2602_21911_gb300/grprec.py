@@ -31,7 +31,7 @@ class grp_problem(ctypes.Structure):
                 ("x_right", ctypes.POINTER(ctypes.c_double)), ("bc", ctypes.POINTER(ctypes.c_int)),
                 ("newton_rtol", ctypes.c_double), ("newton_max_iter", ctypes.c_int),
                 ("guess", ctypes.c_int), ("dt_hold", ctypes.c_int), ("device", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("recon", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("recon", ctypes.c_int), ("solver", ctypes.c_int)]
 
 
 class GrpError(RuntimeError):
@@ -99,6 +99,7 @@ def grp_probe_fp64_peak(device=0):
 
 GRP_NOALLOC_MAX_CELLS = 65536
 GRP_RECON_GRPREC, GRP_RECON_GRPRECNL = 0, 1
+GRP_SOLVER_TT, GRP_SOLVER_DET = 0, 1
 GRP_MLP_NPARAM = 4673
 
 
@@ -218,6 +219,7 @@ class Solver:
         p.device = int(device)
         p.stream = stream
         p.recon = int(prob.get("recon", GRP_RECON_GRPREC))
+        p.solver = int(prob.get("solver", GRP_SOLVER_TT))
         self.prob = prob
         self.C = 3 if p.system == GRP_EULER_IDEAL else 1
         self.D = p.n_domains
