@@ -221,8 +221,8 @@ def other_workloads(local, stream):
     headline): the smooth Euler density wave at N = 8192 for M = 1..4 (plain
     single-domain path; launch-latency bound at this size), its L1 density
     error at t = 1 for M = 2, the shock tube at 2^22 cells (M = 2), the batch
-    and the shock tube with the GRPrecNL reconstruction, and the advection sine
-    at N = 100 (M = 2) to t = 1."""
+    and the shock tube with the GRPrecNL reconstruction and with the DET
+    solver, and the advection sine at N = 100 (M = 2) to t = 1."""
     import torch
     from paper_2602_21911_gb300 import grprec, inputs as I
     out = {}
@@ -278,6 +278,20 @@ def other_workloads(local, stream):
     s.set_initial(avg, lm, lp)
     ms = timed(s, 32)
     out["sod_N4194304_M2_grprecnl"] = {"cell_updates_per_s": (1 << 22) / (ms * 1e-3), "ms_per_step": ms}
+    s.close()
+    # DET solver (the paper's GRP solver): the batch and the shock tube
+    prob, avg, lm, lp = I.batched(65536, seed=2602, M=2)
+    s = grprec.Solver(dict(prob, solver=grprec.GRP_SOLVER_DET), device=local, stream=stream.cuda_stream)
+    s.set_initial(avg, lm, lp)
+    ms = timed(s, 32)
+    out["batched_det_M2"] = {"cell_updates_per_s": cells / (ms * 1e-3), "ms_per_step": ms,
+                             "launch": "flat", "window": "steps 9..40"}
+    s.close()
+    prob, avg, lm, lp = I.sod(1 << 22, M=2)
+    s = grprec.Solver(dict(prob, solver=grprec.GRP_SOLVER_DET), device=local, stream=stream.cuda_stream)
+    s.set_initial(avg, lm, lp)
+    ms = timed(s, 32)
+    out["sod_N4194304_M2_det"] = {"cell_updates_per_s": (1 << 22) / (ms * 1e-3), "ms_per_step": ms}
     s.close()
     prob, avg, lm, lp = I.advection_sine(100, M=2)
     s = grprec.Solver(prob, device=local, stream=stream.cuda_stream)
