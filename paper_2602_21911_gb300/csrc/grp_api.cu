@@ -514,6 +514,11 @@ int grp_set_initial(grp_ctx* c, const double* averages, const double* lim_minus,
   CK(cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * NSTATS * D, s));
   CK(cudaMemsetAsync(c->low, 0, c->nif, s));
   CK(cudaMemsetAsync(c->troubled, 0, c->ncell, s));
+  // per-domain repair and failure words: the flat form clears them every
+  // step, the block-local forms at the start of their first step
+  CK(cudaMemsetAsync(c->bad, 0, sizeof(int) * (MAX_REPAIR + 1) * D, s));
+  CK(cudaMemsetAsync(c->inad, 0, sizeof(int) * D, s));
+  CK(cudaMemsetAsync(c->fail, 0, sizeof(int) * D, s));
   c->initialized = true;
   c->smax_ready = false;
   return GRP_OK;

@@ -131,10 +131,18 @@ __device__ __forceinline__ bool domain_dt(const StepArgs& a, int d, double& dt, 
   return r.active != 0;
 }
 
+// Per-domain words of the step: repair flags and failure code cleared (every
+// system; the S_max pass clears them too for the Euler equations), then the
+// time step.
 static __global__ void k_dt(StepArgs a)
 {
   const int d = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d < a.n_domains) compute_domain_step(a, d);
+  if (d < a.n_domains) {
+    for (int p = 0; p <= MAX_REPAIR; ++p) a.bad[p * a.n_domains + d] = 0;
+    a.inad[d] = 0;
+    a.fail[d] = 0;
+    compute_domain_step(a, d);
+  }
 }
 
 // Neighbour cells of cell i (domain-local) under the domain's boundary rule:
