@@ -260,3 +260,17 @@ def test_autotuner_picks_a_candidate_and_leaves_results_unchanged():
     L = s.get_launch()
     assert (L["form"], L["threads"], L["cells_per_block"], L["steps_per_launch"]) == best
     check_parity(prob, avg, lm, lp, 20, DISC_TOL, solver=s)
+
+
+def test_no_state_is_read_before_written_on_reused_memory():
+    """Device memory handed back to the driver full of non-zero bytes, then a
+    new context: results must not depend on what the memory held."""
+    torch = pytest.importorskip("torch")
+    junk = torch.full((1 << 28,), -1, dtype=torch.int32, device="cuda")     # 1 GiB of 0xFF bytes
+    del junk
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    for prob, avg, lm, lp, tol in ((*I.advection_sine(100, M=2), SMOOTH_TOL),
+                                   (*I.euler_wave(64, 2), SMOOTH_TOL),
+                                   (*I.sod(100, M=2), DISC_TOL)):
+        check_parity(prob, avg, lm, lp, 40, tol)
