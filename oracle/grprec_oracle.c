@@ -25,6 +25,9 @@ typedef double real;
 #ifndef OR_PHASE
 #define OR_PHASE(k)           /* op counting: 0 CFL, 1 reconstruction + GRP, 2 update + repair */
 #endif
+#ifndef OR_LEADING_RP
+#define OR_LEADING_RP(L, R, k) /* op counting: brackets the leading Riemann problem (k = 0 before, 1 after) */
+#endif
 
 #define MAXM 4
 #define MAXC 3
@@ -705,7 +708,9 @@ static int grp_interface(int system, real lambda, real gamma, int M, real dt,
     }
   } else {
     real Q0[3];
+    OR_LEADING_RP(trL, trR, 0);
     int st = riemann_state(gamma, trL, trR, guess_kind, 0, rtol, max_iter, 0, Q0, iters);
+    OR_LEADING_RP(trL, trR, 1);
     if (st != OR_OK) return st;
     for (int c = 0; c < 3; ++c) q[SIDX(0, 0)][c] = Q0[c];
     for (int k = 1; k <= M; ++k) {
@@ -1140,7 +1145,7 @@ static int step_domain(const params *P, int N, int bc, real dx, real dt, real *a
      * state keeps its cell average, unevolved (READING, counted with the
      * reconstruction fallbacks) */
     const int n = M + 1;
-    real (*ed)[2][DET_N + 1][MAXC] = malloc(sizeof(*ed) * N);
+    real (*ed)[2][DET_N + 1][MAXC] = (real (*)[2][DET_N + 1][MAXC])malloc(sizeof(*ed) * N);
     real nu = dt / dx;
     for (int i = 0; i < N; ++i) {
       if (det_predict(P->system, P->lambda, P->gamma, M, nu, coef + i * C * (MAXM + 1), ed[i]) != 0) {

@@ -16,7 +16,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "opcount.cpp")
 LIB = os.path.join(HERE, "libopcount.so")
 KINDS = ("add", "mul", "div", "sqrt", "pow")
-PHASES = ("cfl", "flux", "update")
+PHASES = ("cfl", "flux", "update", "rs_equal")
+# Algorithmic flops of resolving one leading Riemann problem as equal data
+# (the test of the traces: 3 differences, 2 sums, 5 products; admissibility:
+# 3 products; the primitive state of the common trace: 1 division, 5 more)
+EQUAL_DATA_FLOPS = 19
 
 
 def build(force=False):
@@ -32,7 +36,8 @@ def build(force=False):
 
 def count(prob, avg, iface, n_steps):
     """Counts (dict) of one single-threaded run of n_steps from (avg, iface),
-    and the number of cell-updates performed."""
+    the number of cell-updates performed and the number of leading Riemann
+    problems with equal data (their operations are in counts["rs_equal"])."""
     import oracle as O
     L = ctypes.CDLL(build())
     L.or_opcount.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
@@ -54,12 +59,12 @@ def count(prob, avg, iface, n_steps):
                   S.dt_prev.ctypes.data_as(D), S.status.ctypes.data_as(I), n_steps, float("inf"),
                   S.stats.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), None, 1)
     assert rc == 0
-    out = (ctypes.c_longlong * 15)()
+    out = (ctypes.c_longlong * 21)()
     L.or_opcount(out)
     counts = {ph: dict(zip(KINDS, [int(v) for v in out[5 * i:5 * i + 5]]))
               for i, ph in enumerate(PHASES)}
     updates = int((S.stats[:, 0] * n).sum())
-    return counts, updates
+    return counts, updates, int(out[20])
 
 
 if __name__ == "__main__":
@@ -68,7 +73,10 @@ if __name__ == "__main__":
     import oracle as O
     from paper_2602_21911_gb300 import inputs as I
     for name, maker, steps in (
+            ("batched M=1 (every 128th domain)", lambda: I.batched(domains=np.arange(0, 65536, 128), M=1), 50),
             ("batched M=2 (every 128th domain)", lambda: I.batched(domains=np.arange(0, 65536, 128)), 50),
+            ("batched M=3 (every 128th domain)", lambda: I.batched(domains=np.arange(0, 65536, 128), M=3), 50),
+            ("batched M=4 (every 128th domain)", lambda: I.batched(domains=np.arange(0, 65536, 128), M=4), 50),
             ("euler wave N=256 M=1", lambda: I.euler_wave(256, 1), 100),
             ("euler wave N=256 M=2", lambda: I.euler_wave(256, 2), 100),
             ("euler wave N=256 M=3", lambda: I.euler_wave(256, 3), 100),
@@ -77,8 +85,12 @@ if __name__ == "__main__":
             ("advection N=256 M=2", lambda: I.advection_sine(256, 2), 100)):
         prob, avg, lm, lp = maker()
         st, g = O.init_iface(prob["system"], 1.0, 1.4, lm, lp)
-        c, u = count(prob, avg, g, steps)
+        c, u, neq = count(prob, avg, g, steps)
         per = {ph: sum(c[ph].values()) / u for ph in PHASES}
-        print("%-36s flops/cell-update: total %7.1f  cfl %5.1f  flux %7.1f  update %6.1f   flux: %s" % (
-            name, sum(per.values()), per["cfl"], per["flux"], per["update"],
-            ", ".join("%s %.1f" % (k, c["flux"][k] / u) for k in KINDS)))
+        # the flux phase as the product path computes it: equal-data leading
+        # Riemann problems resolved by the test instead of Newton
+        flux_eq = per["flux"] + neq / u * EQUAL_DATA_FLOPS
+        print("%-36s flops/cell-update: total %7.1f  cfl %5.1f  flux %7.1f (equal data resolved: %7.1f, "
+              "%.3f per cell-update)  update %6.1f" % (
+                  name, sum(per.values()), per["cfl"], per["flux"] + per["rs_equal"], flux_eq,
+                  neq / u, per["update"]))

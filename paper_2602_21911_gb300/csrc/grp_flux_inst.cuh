@@ -9,7 +9,7 @@
 #define GRP_DEFINE_EULER_LAUNCHERS(MM, NLV, SUFFIX)                                                          \
   cudaError_t launch_flux_euler_##SUFFIX(const StepArgs& a, cudaStream_t s)                                  \
   {                                                                                                          \
-    const unsigned g = (unsigned)((a.nif + 127) / 128);                                                      \
+    const unsigned g = (unsigned)((flux_threads(a.nif) + 127) / 128);                                         \
     if (a.ph.gamma == 1.4) k_flux<SYS_EULER, MM, true, NLV><<<g, 128, 0, s>>>(a);                            \
     else k_flux<SYS_EULER, MM, false, NLV><<<g, 128, 0, s>>>(a);                                             \
     return cudaGetLastError();                                                                               \
@@ -28,7 +28,7 @@
 #define GRP_DEFINE_ADV_LAUNCHERS(NLV, SUFFIX)                                                                \
   cudaError_t launch_flux_adv##SUFFIX(const StepArgs& a, cudaStream_t s)                                     \
   {                                                                                                          \
-    const unsigned g = (unsigned)((a.nif + 127) / 128);                                                      \
+    const unsigned g = (unsigned)((flux_threads(a.nif) + 127) / 128);                                         \
     switch (a.M) {                                                                                           \
       case 1: k_flux<SYS_ADV, 1, false, NLV><<<g, 128, 0, s>>>(a); break;                                    \
       case 2: k_flux<SYS_ADV, 2, false, NLV><<<g, 128, 0, s>>>(a); break;                                    \
