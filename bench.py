@@ -166,7 +166,7 @@ def train_guess(args, device):
     runs = [(*I.batched(args.domains, seed=2603, M=args.M), 500), (*I.sod(4096, M=args.M), 400)]
     rec = learned.harvest(runs, capacity=2_000_000, log2_stride=0, device=device)
     w, box, info = learned.fit_from_records(rec)
-    return w, box, {"records": int(rec.shape[0]), "val_rms": info["val_rms"],
+    return w, box, {"records": int(rec.shape[0]), "trained_on": info["n_train"], "val_rms": info["val_rms"],
                     "target_std": float(rec[:, 6].std().item()), "seconds": time.perf_counter() - t0,
                     "harvest": "batched seed 2603 x 500 steps + Sod 4096 x 400 steps"}
 

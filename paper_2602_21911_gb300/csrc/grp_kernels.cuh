@@ -169,10 +169,14 @@ __device__ __forceinline__ void smax_cell(const StepArgs& a, long long gi, bool 
     d = a.cell_dom[gi];
     const double g = a.ph.gamma;
     const double r = a.avg[gi], m = a.avg[a.ncell + gi], E = a.avg[2 * a.ncell + gi];
-    const double u = __ddiv_rn(m, r);
-    const double p = __dmul_rn(g - 1.0, __dadd_rn(E, -__dmul_rn(__dmul_rn(0.5, m), u)));
+    // |u| + c with one refined reciprocal and one reciprocal square root (an
+    // ulp or two from the correctly rounded divisions and root)
+    const double ir = rcp64(r);
+    const double u = m * ir;
+    const double p = (g - 1.0) * (E - 0.5 * m * u);
     a.pold[gi] = p;                                // for the discrete maximum principle of the update
-    double sp = __dadd_rn(fabs(u), __dsqrt_rn(__ddiv_rn(__dmul_rn(g, p), r)));
+    const double c2 = g * p * ir;
+    double sp = fabs(u) + (c2 > 0.0 ? c2 * rsqrt(c2) : 0.0);
     if (!(sp >= 0.0)) sp = 0.0;
     bits = (unsigned long long)__double_as_longlong(sp);
   }
@@ -288,6 +292,9 @@ __device__ __forceinline__ void cell_coeffs(const StepArgs& a, long long c0, lon
 }
 
 // First-order Godunov flux and state at interface j from cell averages.
+// The repair rounds start Newton from PVRS: the network's evaluation is a
+// chain of thousands of dependent FP32 operations, longer than the Newton
+// iterations it saves, and the repair kernels are bound by that latency.
 template <bool G75>
 static __device__ int first_order(const StepArgs& a, long long c0, int N, int bc, int j, double F[3], double Q0[3], int& iters)
 {
@@ -335,6 +342,24 @@ __device__ __forceinline__ void ghost_edge(const StepArgs& a, long long c0, int 
   }
 }
 
+// Harvest of a solve the network served (strong data with a shock): keep one
+// in 2^k, by a hash of (interface, step).
+__device__ __forceinline__ void harvest_record(const StepArgs& a, long long gj, int d, const RSInfo& info, int iters)
+{
+  unsigned h = (unsigned)gj * 2654435761u ^ ((unsigned)a.nstep[d] * 2246822519u);
+  h ^= h >> 15; h *= 2654435761u; h ^= h >> 13;
+  if ((h & ((1u << a.harvest_log2_stride) - 1u)) == 0u) {
+    const unsigned long long k = atomicAdd(a.harvest_count, 1ull);
+    if ((long long)k < a.harvest_cap) {
+      float* r = a.harvest + 8 * k;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) r[i] = info.x[i];
+      r[6] = (float)(log(info.ps / info.base) / (MLP_T_SCALE * info.s3));
+      r[7] = (float)iters;
+    }
+  }
+}
+
 // The GRP at interface gj of an active domain d from the Taylor coefficients
 // of the two one-sided reconstructions (tL: left cell at its right edge, tR:
 // right cell at its left edge): flux, new interface datum, statistics.
@@ -357,21 +382,7 @@ __device__ __forceinline__ void grp_at(const StepArgs& a, long long gj, int d, l
     st[3] = trunc ? 1u : 0u;
     st[6] = info.guess == 1 ? 1u : 0u;
     st[7] = info.guess == 2 ? 1u : 0u;
-    if (a.harvest && info.has_x && rs_st == ST_OK) {
-      // keep one non-trivial interface in 2^k, by a hash of (interface, step)
-      unsigned h = (unsigned)gj * 2654435761u ^ ((unsigned)a.nstep[d] * 2246822519u);
-      h ^= h >> 15; h *= 2654435761u; h ^= h >> 13;
-      if ((h & ((1u << a.harvest_log2_stride) - 1u)) == 0u) {
-        const unsigned long long k = atomicAdd(a.harvest_count, 1ull);
-        if ((long long)k < a.harvest_cap) {
-          float* r = a.harvest + 8 * k;
-#pragma unroll
-          for (int i = 0; i < 6; ++i) r[i] = info.x[i];
-          r[6] = (float)(log(info.ps / info.base) / (MLP_T_SCALE * info.s3));
-          r[7] = (float)iters;
-        }
-      }
-    }
+    if (a.harvest && info.has_x && rs_st == ST_OK) harvest_record(a, gj, d, info, iters);
     if (rs_st != ST_OK) {
       // no solution of the traces' Riemann problem: first-order flux here
       int it2 = 0;
@@ -577,20 +588,26 @@ __device__ __forceinline__ int update_one(const StepArgs& a, long long gi, int d
     int im, ip;
     nbr(i, N, a.bc[d], im, ip);
     const int nb[3] = {im, i, ip};
-    double lo0 = 0.0, hi0 = 0.0, lo1 = 0.0, hi1 = 0.0;
+    // old density and pressure (the pressure as reduced with S_max) of cells
+    // i-1, i, i+1.  Both are positive (the old averages are admissible), and
+    // positive doubles order as their bit patterns do, so the bounds come from
+    // integer min / max (exactly fmin / fmax, off the FP64 pipe), and
+    // max(|lo|, |hi|) is hi.
+    long long lo0, hi0, lo1, hi1;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      // old density and pressure (the pressure as reduced with S_max)
       const long long q = c0 + nb[k];
-      const double r = a.avg[q], pr = a.pold[q];
-      lo0 = k == 0 ? r : fmin(lo0, r); hi0 = k == 0 ? r : fmax(hi0, r);
-      lo1 = k == 0 ? pr : fmin(lo1, pr); hi1 = k == 0 ? pr : fmax(hi1, pr);
+      const long long r = __double_as_longlong(a.avg[q]), pr = __double_as_longlong(a.pold[q]);
+      lo0 = k == 0 ? r : min(lo0, r); hi0 = k == 0 ? r : max(hi0, r);
+      lo1 = k == 0 ? pr : min(lo1, pr); hi1 = k == 0 ? pr : max(hi1, pr);
     }
+    const double rlo = __longlong_as_double(lo0), rhi = __longlong_as_double(hi0);
+    const double plo = __longlong_as_double(lo1), phi = __longlong_as_double(hi1);
     // the candidate pressure p = (g-1)(E - m^2/(2 rho)) against its bounds,
     // multiplied through by rho > 0 (admissible): no division
     const double rp = (g - 1.0) * (Q[2] * Q[0] - 0.5 * Q[1] * Q[1]);
-    const double d0 = DMP_REL * fmax(fabs(lo0), fabs(hi0)), d1 = DMP_REL * fmax(fabs(lo1), fabs(hi1));
-    ok = Q[0] >= lo0 - d0 && Q[0] <= hi0 + d0 && rp >= (lo1 - d1) * Q[0] && rp <= (hi1 + d1) * Q[0];
+    const double d0 = DMP_REL * rhi, d1 = DMP_REL * phi;
+    ok = Q[0] >= rlo - d0 && Q[0] <= rhi + d0 && rp >= (plo - d1) * Q[0] && rp <= (phi + d1) * Q[0];
   }
   const unsigned char flag = adm ? (ok ? 0 : 1) : 2;
   const unsigned char before = pass < 0 ? 0 : a.troubled[gi];

@@ -70,8 +70,10 @@ def input_box(x, margin=0.05):
     return torch.cat([lo - pad, hi + pad]).contiguous()
 
 
-def train(x, t, epochs=800, batch=1024, lr=3e-3, lr_end=1e-5, seed=0, weights=None, verbose=False):
-    """Mini-batch Adam, learning rate decayed geometrically from lr to lr_end.
+def train(x, t, epochs=800, batch=1024, lr=3e-3, lr_end=1e-5, seed=0, weights=None, verbose=False,
+          max_steps=50_000):
+    """Mini-batch Adam, learning rate decayed geometrically from lr to lr_end,
+    at most max_steps optimizer steps (fewer epochs on large sets).
     x: float32 device [n, 6]; t: float32 device [n].  Returns (weights, losses
     per epoch)."""
     import torch
@@ -85,6 +87,7 @@ def train(x, t, epochs=800, batch=1024, lr=3e-3, lr_end=1e-5, seed=0, weights=No
     work = torch.empty(grprec.mlp_work_floats(batch), dtype=torch.float32, device=dev)
     gen = torch.Generator(device=dev).manual_seed(seed)
     nb = max(1, n // batch)
+    epochs = max(1, min(epochs, -(-max_steps // nb)))
     decay = (lr_end / lr) ** (1.0 / max(1, epochs * nb - 1))
     step, rate, hist = 0, lr, []
     for ep in range(epochs):
@@ -129,13 +132,14 @@ def states_from_features(x, gamma=1.4):
     return cons(rl, ul, pl), cons(rr, ur, pr)
 
 
-def fit_from_records(records, val_fraction=0.1, seed=0, **kw):
-    """Split harvested records, train, and report the validation RMS error of
-    the target v and the input box."""
+def fit_from_records(records, val_fraction=0.1, seed=0, max_records=120_000, **kw):
+    """Split harvested records (a random subset of at most max_records),
+    train, and report the validation RMS error of the target v and the input
+    box."""
     import torch
-    n = records.shape[0]
     gen = torch.Generator(device=records.device).manual_seed(seed + 1)
-    perm = torch.randperm(n, generator=gen, device=records.device)
+    perm = torch.randperm(int(records.shape[0]), generator=gen, device=records.device)[:max_records]
+    n = int(perm.shape[0])
     nv = max(1, int(n * val_fraction))
     val, tr = records[perm[:nv]], records[perm[nv:]]
     x, t = tr[:, :6].contiguous(), tr[:, 6].contiguous()
