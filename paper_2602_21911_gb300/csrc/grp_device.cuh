@@ -740,20 +740,43 @@ GRP_HD __forceinline__ void char_back(const Eig& e, const double w[3], double D[
   D[2] = (e.H - e.u * e.c) * w[0] + 0.5 * e.u * e.u * w[1] + (e.H + e.u * e.c) * w[2];
 }
 
-// With theta_j = 0 (lam_j > 0), 1 (lam_j < 0), 1/2 (tie) the upwind value
-// sum_j (l_j.(DL - theta_j (DL - DR))) r_j is DL - sum_j theta_j (l_j.J) r_j,
-// J = DL - DR: one projection (of the jump) instead of one per side.
-GRP_HD __forceinline__ void deriv_rp(const Eig& e, const double DL[3], const double DR[3], double D[3])
+// All M derivative Riemann problems of one interface at once:
+// D_k = DL_k - sum_j theta_j (l_j . J_k) r_j with J_k = DL_k - DR_k.  theta_j
+// depends on the field only, so a field that takes right data (theta_j != 0)
+// is applied to every order k in one branch; in smooth subsonic flow that is
+// one field of the three.  t[c][k]: Taylor coefficients of the traces;
+// D[k][c] for k = 1..M.
+template <int M>
+GRP_HD __forceinline__ void deriv_rps(const Eig& e, const double tL[][M + 1], const double tR[][M + 1],
+                                      double D[M + 1][3])
 {
-  const double J[3] = {DL[0] - DR[0], DL[1] - DR[1], DL[2] - DR[2]};
-  double w[3], C[3];
-  char_proj(e, J, w);
+  double J[M + 1][3];
 #pragma unroll
-  for (int j = 0; j < 3; ++j) w[j] = e.lam[j] > e.tie ? 0.0 : (e.lam[j] < -e.tie ? w[j] : 0.5 * w[j]);
-  char_back(e, w, C);
-  D[0] = DL[0] - C[0];
-  D[1] = DL[1] - C[1];
-  D[2] = DL[2] - C[2];
+  for (int k = 1; k <= M; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      J[k][c] = tL[c][k] - tR[c][k];
+      D[k][c] = tL[c][k];
+    }
+  const double uc = e.u * e.ic, bu = e.b1 * e.u, uc2 = e.u * e.c;
+  // rows of R^{-1} (left eigenvectors) and the right eigenvectors (1, r1, r2)
+  const double Lr[3][3] = {{0.5 * (e.b2 + uc), -0.5 * (bu + e.ic), 0.5 * e.b1},
+                           {1.0 - e.b2, bu, -e.b1},
+                           {0.5 * (e.b2 - uc), -0.5 * (bu - e.ic), 0.5 * e.b1}};
+  const double Rr[3][2] = {{e.u - e.c, e.H - uc2}, {e.u, 0.5 * e.u * e.u}, {e.u + e.c, e.H + uc2}};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const double th = e.lam[j] > e.tie ? 0.0 : (e.lam[j] < -e.tie ? 1.0 : 0.5);
+    if (th != 0.0) {
+#pragma unroll
+      for (int k = 1; k <= M; ++k) {
+        const double w = th * (Lr[j][0] * J[k][0] + Lr[j][1] * J[k][1] + Lr[j][2] * J[k][2]);
+        D[k][0] -= w;
+        D[k][1] -= w * Rr[j][0];
+        D[k][2] -= w * Rr[j][1];
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -924,20 +947,20 @@ GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[
   rho[0] = Q0[0]; m[0] = Q0[1]; E[0] = Q0[2];
   {
     const Eig e = make_eig(ph, Q0, W0, ir0);
+    double D[M + 1][3];
+    deriv_rps<M>(e, tL, tR, D);
 #pragma unroll
     for (int k = 1; k <= M; ++k) {
-      const double DL[3] = {tL[0][k], tL[1][k], tL[2][k]}, DR[3] = {tR[0][k], tR[1][k], tR[2][k]};
-      double D[3];
-      deriv_rp(e, DL, DR, D);
-      rho[T::idx(k, 0)] = D[0]; m[T::idx(k, 0)] = D[1]; E[T::idx(k, 0)] = D[2];
+      rho[T::idx(k, 0)] = D[k][0]; m[T::idx(k, 0)] = D[k][1]; E[T::idx(k, 0)] = D[k][2];
     }
   }
   double s[3][M + 1];
   ck_euler<M>(g, rho, m, E, s);
-  // states at the Gauss nodes and at tau = dt; one reciprocal per state
-  // serves both the admissibility test and the flux
+  // states at the Gauss nodes and at tau = dt; at a node one reciprocal
+  // serves both the admissibility test and the flux, at dt (no flux) the
+  // test is division-free
   constexpr int G = Gauss<M>::G;
-  double Qg[G + 1][3], ug[G + 1], pg[G + 1];
+  double Qg[G + 1][3], ug[G], pg[G];
   bool ok = true;
 #pragma unroll
   for (int al = 0; al <= G; ++al) {
@@ -949,16 +972,20 @@ GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[
       for (int k = M - 1; k >= 0; --k) v = v * Tn + s[c][k];
       Qg[al][c] = v;
     }
-    ug[al] = Qg[al][1] * rcp64(Qg[al][0]);        // a non-positive density fails the test below
-    pg[al] = (g - 1.0) * (Qg[al][2] - 0.5 * Qg[al][1] * ug[al]);
-    ok = ok && Qg[al][0] > 0.0 && pg[al] > 0.0;
+    if (al < G) {
+      ug[al] = Qg[al][1] * rcp64(Qg[al][0]);        // a non-positive density fails the test below
+      pg[al] = (g - 1.0) * (Qg[al][2] - 0.5 * Qg[al][1] * ug[al]);
+      ok = ok && Qg[al][0] > 0.0 && pg[al] > 0.0;
+    } else {
+      ok = ok && admissible(g, Qg[al][0], Qg[al][1], Qg[al][2]);
+    }
   }
   if (!ok) {
     truncated = true;
 #pragma unroll
     for (int al = 0; al <= G; ++al) {
       Qg[al][0] = Q0[0]; Qg[al][1] = Q0[1]; Qg[al][2] = Q0[2];
-      ug[al] = W0.u; pg[al] = W0.p;
+      if (al < G) { ug[al] = W0.u; pg[al] = W0.p; }
     }
   }
   F[0] = F[1] = F[2] = 0.0;
