@@ -374,8 +374,24 @@ GRP_HD __forceinline__ double pvrs(const Side& L, const Side& R)
   return fmax(ppv, 1e-14 * fmax(L.p, R.p));
 }
 
+// Two-shock estimate of the star pressure from the pressure p0 (the PVRS
+// estimate): the shock branches linearised at p0.
+GRP_HD __forceinline__ double tsrs(const Side& L, const Side& R, double p0)
+{
+  const double gL = L.sA * rsqrt(p0 + L.B), gR = R.sA * rsqrt(p0 + R.B);
+  return (gL * L.p + gR * R.p - (R.u - L.u)) * rcp64(gL + gR);
+}
+
+// Internal start for the repair (first-order) Riemann problems of cell
+// averages, whose data are strong: the textbook adaptive choice of PVRS when
+// the pressures are close and its estimate lies between them, the
+// two-rarefaction estimate when it falls below both, the two-shock estimate
+// otherwise.
+constexpr int GUESS_ADAPTIVE = 3;
+
 // Returns ST_OK / ST_NO_CONV / ST_VACUUM.  p0 > 0 is used as the start when
-// given (learned guess), otherwise PVRS or TRRS per ph.guess.
+// given (learned guess), otherwise PVRS, TRRS or the adaptive choice per
+// ph.guess.
 template <bool G75>
 static GRP_HD int star_pressure(const Phys& ph, const Side& L, const Side& R, double p0, double& ps, double& us,
                                 int& iters)
@@ -389,6 +405,11 @@ static GRP_HD int star_pressure(const Phys& ph, const Side& L, const Side& R, do
     p = p0;
   } else if (ph.guess == 1) {
     p = trrs<G75>(ph, L, R);
+  } else if (ph.guess == GUESS_ADAPTIVE) {
+    const double ppv = pvrs(L, R), pmin = fmin(L.p, R.p), pmax = fmax(L.p, R.p);
+    if (pmax < 2.0 * pmin && ppv >= pmin && ppv <= pmax) p = ppv;
+    else if (ppv < pmin) p = trrs<G75>(ph, L, R);
+    else p = tsrs(L, R, ppv);
   } else {
     p = pvrs(L, R);
   }

@@ -292,9 +292,11 @@ __device__ __forceinline__ void cell_coeffs(const StepArgs& a, long long c0, lon
 }
 
 // First-order Godunov flux and state at interface j from cell averages.
-// The repair rounds start Newton from PVRS: the network's evaluation is a
-// chain of thousands of dependent FP32 operations, longer than the Newton
-// iterations it saves, and the repair kernels are bound by that latency.
+// Newton starts from the adaptive classical estimate (these data are strong;
+// p* does not depend on the start).  The learned guess is not used here: the
+// network's evaluation is a chain of thousands of dependent FP32 operations,
+// longer than the Newton iterations it saves, and the repair kernels are
+// bound by that latency.
 template <bool G75>
 static __device__ int first_order(const StepArgs& a, long long c0, int N, int bc, int j, double F[3], double Q0[3], int& iters)
 {
@@ -305,7 +307,9 @@ static __device__ int first_order(const StepArgs& a, long long c0, int N, int bc
 #pragma unroll
   for (int c = 0; c < 3; ++c) { QL[c] = a.avg[c * a.ncell + c0 + cl]; QR[c] = a.avg[c * a.ncell + c0 + cr]; }
   Prim W;
-  const int st = riemann_state<G75>(a.ph, QL, QR, true, Q0, W, iters);
+  Phys ph = a.ph;
+  ph.guess = GUESS_ADAPTIVE;
+  const int st = riemann_state<G75>(ph, QL, QR, true, Q0, W, iters);
   if (st != ST_OK && st != ST_VACUUM) return st;
   if (Q0[0] > 0.0) euler_flux(a.ph.gamma, Q0[0], Q0[1], Q0[2], F);
   else F[0] = F[1] = F[2] = 0.0;
@@ -449,12 +453,16 @@ __device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d,
 __host__ __device__ constexpr long long flux_threads(long long nif) { return (nif + 30) / 31 * 32; }
 
 // Every thread of the grid reaches the shuffles and the statistics (no early
-// return), so the warp-synchronous operations see a full warp.  At least 3
-// blocks of 128 per SM: that lets the compiler keep about 130-140 registers
-// per thread, which measured 11 % faster on the batched workload than the
-// ~108 it picks for 128-thread blocks without the bound.
+// return), so the warp-synchronous operations see a full warp.  At least
+// GRP_FLUX_MIN_BLOCKS (default 3) blocks of 128 per SM: that lets the compiler
+// keep about 130-140 registers per thread, which measured 11 % faster on the
+// batched workload than the ~108 it picks for 128-thread blocks without the
+// bound.
+#ifndef GRP_FLUX_MIN_BLOCKS
+#define GRP_FLUX_MIN_BLOCKS 3
+#endif
 template <int SYS, int M, bool G75, bool NL>
-__global__ void __launch_bounds__(128, 3) k_flux(StepArgs a)
+__global__ void __launch_bounds__(128, GRP_FLUX_MIN_BLOCKS) k_flux(StepArgs a)
 {
   constexpr int C = SYS == SYS_EULER ? 3 : 1;
   const int lane = lane_id();
@@ -685,11 +693,16 @@ __global__ void __launch_bounds__(LIST_THREADS) k_repair_list(StepArgs a, int pa
   __shared__ int qn;
   const int n = a.lcount[pass];
   const int* L = a.tlist[pass & 1];
-  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {   // uniform per block
+  // the list spread evenly over the whole grid: a short list gives every
+  // block a few cells, so each thread solves at most one Riemann problem per
+  // pass (the solves are long dependent chains; parallel ones hide latency)
+  const int per = (n + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int chunk = per < (int)blockDim.x ? per : (int)blockDim.x;
+  for (int base = blockIdx.x * chunk; base < n; base += gridDim.x * chunk) {   // uniform per block
     if (threadIdx.x == 0) qn = 0;
     __syncthreads();
     const int k = base + threadIdx.x;
-    if (k < n) {
+    if ((int)threadIdx.x < chunk && k < n) {
       const long long gi = L[k];
       const int d = a.cell_dom[gi];
       const long long c0 = a.cell_off[d], i0 = a.if_off[d];
