@@ -95,6 +95,34 @@ __device__ __forceinline__ void warp_stat_max(unsigned long long* stats, int d, 
   if (d >= 0 && lane_id() == __ffs(grp) - 1 && s) atomicMax(stats + (long long)d * NSTATS + which, (unsigned long long)s);
 }
 
+// The eight per-interface counters of the flux kernels, aggregated per warp
+// and domain with one match and four reductions: the Newton sum and maximum,
+// and two words packing the small counters (RS calls 0..2 in 7 bits; the 0/1
+// flags in 6 bits each: at most 64 and 32 per warp).  st: newton sum, newton
+// max, RS calls, truncated, first order, recon fallback, learned guess used,
+// learned guess rejected.
+__device__ __forceinline__ void warp_flux_stats(unsigned long long* stats, int d, const unsigned st[8], bool guess)
+{
+  const unsigned grp = __match_any_sync(0xffffffffu, d);
+  const unsigned nsum = __reduce_add_sync(grp, st[0]);
+  const unsigned nmax = __reduce_max_sync(grp, st[1]);
+  const unsigned wa = __reduce_add_sync(grp, st[2] | (st[3] << 7) | (st[4] << 14) | (st[5] << 21));
+  const unsigned wb = guess ? __reduce_add_sync(grp, st[6] | (st[7] << 6)) : 0u;
+  if (d >= 0 && lane_id() == __ffs(grp) - 1) {
+    unsigned long long* S = stats + (long long)d * NSTATS;
+    if (nsum) atomicAdd(S + S_NEWTON_SUM, (unsigned long long)nsum);
+    if (nmax) atomicMax(S + S_NEWTON_MAX, (unsigned long long)nmax);
+    const unsigned rs = wa & 127u, tr = (wa >> 7) & 127u, lo = (wa >> 14) & 127u, fb = (wa >> 21) & 127u;
+    if (rs) atomicAdd(S + S_RS_CALLS, (unsigned long long)rs);
+    if (tr) atomicAdd(S + S_FLUX_FB, (unsigned long long)tr);
+    if (lo) atomicAdd(S + S_LOW, (unsigned long long)lo);
+    if (fb) atomicAdd(S + S_RECON_FB, (unsigned long long)fb);
+    const unsigned gu = wb & 63u, gr = (wb >> 6) & 63u;
+    if (gu) atomicAdd(S + S_GUESS_USED, (unsigned long long)gu);
+    if (gr) atomicAdd(S + S_GUESS_REJ, (unsigned long long)gr);
+  }
+}
+
 // Time-step rule (Section 4.1): dt = C dx / S_max, recomputed every dt_hold
 // steps, the last step clipped to t_end.  false: the domain does not move.
 // Time step of domain d from its words (S_max complete): one division.
@@ -537,16 +565,7 @@ __global__ void __launch_bounds__(128, GRP_FLUX_MIN_BLOCKS) k_flux(StepArgs a)
   }
   __syncwarp();
   if (SYS == SYS_EULER) {
-    warp_stat_add(a.stats, d, S_NEWTON_SUM, st[0]);
-    warp_stat_max(a.stats, d, S_NEWTON_MAX, st[1]);
-    warp_stat_add(a.stats, d, S_RS_CALLS, st[2]);
-    warp_stat_add(a.stats, d, S_FLUX_FB, st[3]);
-    warp_stat_add(a.stats, d, S_LOW, st[4]);
-    warp_stat_add(a.stats, d, S_RECON_FB, st[5]);
-    if (a.ph.guess == 2) {
-      warp_stat_add(a.stats, d, S_GUESS_USED, st[6]);
-      warp_stat_add(a.stats, d, S_GUESS_REJ, st[7]);
-    }
+    warp_flux_stats(a.stats, d, st, a.ph.guess == 2);
   }
 }
 
@@ -851,16 +870,7 @@ __global__ void __launch_bounds__(256, 2) k_batch(StepArgs a, const int* __restr
       }
       __syncwarp();
       if (SYS == SYS_EULER) {
-        warp_stat_add(w.stats, d, S_NEWTON_SUM, st[0]);
-        warp_stat_max(w.stats, d, S_NEWTON_MAX, st[1]);
-        warp_stat_add(w.stats, d, S_RS_CALLS, st[2]);
-        warp_stat_add(w.stats, d, S_FLUX_FB, st[3]);
-        warp_stat_add(w.stats, d, S_LOW, st[4]);
-        warp_stat_add(w.stats, d, S_RECON_FB, st[5]);
-        if (w.ph.guess == 2) {
-          warp_stat_add(w.stats, d, S_GUESS_USED, st[6]);
-          warp_stat_add(w.stats, d, S_GUESS_REJ, st[7]);
-        }
+        warp_flux_stats(w.stats, d, st, w.ph.guess == 2);
       }
     }
     __syncthreads();
