@@ -813,19 +813,25 @@ struct Tri {
 };
 
 // In: q0[c][idx(a,0)] filled for a = 0..M (others ignored).  Out: s[c][b] = q[0][b].
+// irho, u0, p0: 1/rho, velocity and pressure of the leading state (known to
+// the caller), the series' constant terms.
 template <int M>
 GRP_HD __forceinline__ void ck_euler(double g, double rho[Tri<M>::N], double m[Tri<M>::N],
-                                         double E[Tri<M>::N], double s[3][M + 1])
+                                         double E[Tri<M>::N], double s[3][M + 1], double irho, double u0, double p0)
 {
   using T = Tri<M>;
   double u[T::N], mu[T::N], Ep[T::N], F1[T::N], F2[T::N];
-  const double irho = rcp64(rho[0]);
   const double gm1 = g - 1.0;
 #pragma unroll
   for (int b = 0; b < M; ++b) {
 #pragma unroll
     for (int a = 0; a + b <= M; ++a) {
       const int k = T::idx(a, b);
+      if (k == 0) {
+        u[0] = u0;
+        Ep[0] = E[0] + p0;
+        continue;
+      }
       double acc = m[k];
 #pragma unroll
       for (int i = 0; i <= a; ++i)
@@ -895,6 +901,14 @@ constexpr double EQ_TOL = 3.552713678800501e-15;   // 2^-48
 
 GRP_HD __forceinline__ bool equal_data(const double QL[3], const double QR[3])
 {
+#ifdef __CUDA_ARCH__
+  // identical bits first (integer compares; the interpolating degrees give
+  // exactly this at every interface whose cells kept their polynomials)
+  if (__double_as_longlong(QL[0]) == __double_as_longlong(QR[0]) &&
+      __double_as_longlong(QL[1]) == __double_as_longlong(QR[1]) &&
+      __double_as_longlong(QL[2]) == __double_as_longlong(QR[2]))
+    return true;
+#endif
   const double sr = QL[0] + QR[0], sE = QL[2] + QR[2], dm = QR[1] - QL[1];
   return fabs(QR[0] - QL[0]) <= EQ_TOL * sr && fabs(QR[2] - QL[2]) <= EQ_TOL * sE &&
          dm * dm <= (EQ_TOL * EQ_TOL) * (sr * sE);
@@ -949,8 +963,9 @@ GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[
   Prim W0;
   double ir0;
   truncated = false;
-  if (equal_data(QL, QR) && admissible(g, QL[0], QL[1], QL[2])) {
-    // equal data: the exact solution is the constant state, no Newton
+  if (equal_data(QL, QR)) {
+    // equal data: the exact solution is the constant state, no Newton (the
+    // traces are admissible: an inadmissible one sends its cell to degree 0)
     Q0[0] = QL[0]; Q0[1] = QL[1]; Q0[2] = QL[2];
     ir0 = rcp64(Q0[0]);
     W0.r = Q0[0];
@@ -976,7 +991,7 @@ GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[
     }
   }
   double s[3][M + 1];
-  ck_euler<M>(g, rho, m, E, s);
+  ck_euler<M>(g, rho, m, E, s, ir0, W0.u, W0.p);
   // states at the Gauss nodes and at tau = dt; at a node one reciprocal
   // serves both the admissibility test and the flux, at dt (no flux) the
   // test is division-free

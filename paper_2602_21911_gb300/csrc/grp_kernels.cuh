@@ -353,6 +353,42 @@ __device__ __forceinline__ void cell_edges(const StepArgs& a, long long c0, long
 {
   constexpr int C = SYS == SYS_EULER ? 3 : 1;
   double b[3][5];
+  if (!NL && (M == 2 || M == 4)) {
+    // Degrees 2 and 4 interpolate the cell's interface data (Section 3.1):
+    // the polynomial's values at the edges are g_{i-1/2} and g_{i+1/2}
+    // themselves, so they are taken as loaded and only the derivative
+    // coefficients are evaluated.  The degree-0 fallback tests those values.
+    int im, ip;
+    nbr(cell, N, bc, im, ip);
+    const int jl = cell, jr = (bc == 0) ? (cell == N - 1 ? 0 : cell + 1) : cell + 1;
+    double gl[3], gr[3], q0[3];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const double* A = a.avg + c * a.ncell + c0;
+      const double* G = a.ifc + c * a.nif + i0;
+      const double qm = (M >= 3) ? A[im] : 0.0, qp = (M >= 3) ? A[ip] : 0.0;
+      q0[c] = A[cell];
+      gl[c] = G[jl];
+      gr[c] = G[jr];
+      grprec_coeffs<M>(qm, q0[c], qp, gl[c], gr[c], b[c]);
+    }
+    fb = SYS == SYS_EULER && (!admissible(a.ph.gamma, gl[0], gl[1], gl[2]) ||
+                              !admissible(a.ph.gamma, gr[0], gr[1], gr[2]));
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      double tm[M + 1], tp[M + 1];
+      edge_taylor<M>(b[c], -1.0, tm);
+      edge_taylor<M>(b[c], 1.0, tp);
+      em[c][0] = fb ? q0[c] : gl[c];
+      ep[c][0] = fb ? q0[c] : gr[c];
+#pragma unroll
+      for (int k = 1; k <= M; ++k) {
+        em[c][k] = fb ? 0.0 : tm[k];
+        ep[c][k] = fb ? 0.0 : tp[k];
+      }
+    }
+    return;
+  }
   cell_coeffs<SYS, M, NL>(a, c0, i0, N, bc, cell, b, fb);
 #pragma unroll
   for (int c = 0; c < C; ++c) {
