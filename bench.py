@@ -130,21 +130,24 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(cells, kname):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, scaled from its workload to this one by cell count; None when the
-    kernel source has changed since the capture or the summary is of another
-    kernel."""
+def profiled(cells, kname):
+    """From the committed ncu summary of the dominant kernel: DRAM bytes per
+    launch, scaled from its workload to this one by cell count, and the
+    executed FP64 flops (dadd + dmul + 2 dfma) as a fraction of the peak's.
+    (None, None) when the kernel source has changed since the capture or the
+    summary is of another kernel."""
     if not os.path.exists(PROFILE):
-        return None
+        return None, None
     kv = {}
     for line in open(PROFILE):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
     if kv.get("source_digest") != source_digest() or kv.get("bench_kernel") != kname:
-        return None
-    return float(kv["dram_bytes_per_launch"]) * cells / float(kv["cells_per_launch"])
+        return None, None
+    traffic = float(kv["dram_bytes_per_launch"]) * cells / float(kv["cells_per_launch"])
+    executed = float(kv["executed_fp64_frac_of_peak"]) if "executed_fp64_frac_of_peak" in kv else None
+    return traffic, executed
 
 
 def workload(args, rank, world):
@@ -498,12 +501,17 @@ def main():
         per_launch_updates = (upd / world) / args.steps
     if flops and flux_n:
         ach = flops * per_launch_updates / (flux_ms / flux_n * 1e-3)
+        traffic, executed = profiled(int(prob["n_cells"].sum()), kname)
         line["roofline"] = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                             "frac": ach / peak,
-                            "traffic": profiled_traffic(int(prob["n_cells"].sum()), kname),
+                            "traffic": traffic,
                             "kernel": kname,
                             "peak_source": "measured FP64 FMA-chain probe (grp_probe_fp64_peak), this GPU",
-                            "flops_per_cell_update": flops}
+                            "flops_per_cell_update": flops,
+                            "flops_note": "algorithmic = the CPU oracle's operation count (an upper bound on the "
+                                          "kernel's own arithmetic); executed_frac_ncu = the kernel's executed "
+                                          "FP64 flops over the peak's, from the committed ncu summary",
+                            "executed_frac_ncu": executed}
     if not args.no_other:
         line["workloads"] = other_workloads(local, stream)
     if not args.no_cpu_baseline:
