@@ -274,3 +274,18 @@ def test_no_state_is_read_before_written_on_reused_memory():
                                    (*I.euler_wave(64, 2), SMOOTH_TOL),
                                    (*I.sod(100, M=2), DISC_TOL)):
         check_parity(prob, avg, lm, lp, 40, tol)
+
+
+def test_interpolating_degrees_resolve_smooth_riemann_data_without_newton():
+    """Degrees 2 and 4 interpolate the interface data, so on smooth periodic
+    flow both traces at every interface are the interface datum itself: every
+    leading Riemann problem has equal data and takes no Newton iteration.  The
+    least-squares degrees 1 and 3 give two different traces and iterate.  The
+    oracle runs Newton everywhere; the results agree either way."""
+    from paper_2602_21911_gb300 import grprec
+    for M, no_newton in ((1, False), (2, True), (3, False), (4, True)):
+        prob, avg, lm, lp = I.euler_wave(100, M)
+        S, (a, g, t, stats, status), rd = check_parity(prob, avg, lm, lp, 60, SMOOTH_TOL)
+        assert S.stats[:, O.ST_NEWTON_SUM].sum() > 0
+        n = int(stats[:, grprec.STAT_NEWTON_SUM].sum())
+        assert (n == 0) == no_newton, (M, n)

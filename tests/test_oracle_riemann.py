@@ -281,3 +281,23 @@ def test_derivative_rp_tie_averages_and_is_continuous_there():
     # away from the tie the contact component is upwinded
     up = O.deriv_rp(G, cons((1.0, 1e-3, 1.0)), DL, DR)
     assert not np.allclose(up, base, rtol=1e-6)
+
+
+def test_nearly_equal_data_give_the_left_state_to_the_jump():
+    """Riemann data whose conserved states agree to a relative 2^-49 (each
+    component on its own scale, the momentum on sqrt(rho E)): the exact
+    solution at x/t = 0 lies within the jump of either state.  This is what
+    lets the flux kernel resolve such data as the constant state without a
+    Newton solve; here the oracle's full Newton solver is the judge."""
+    rng = np.random.default_rng(11)
+    eps = 2.0 ** -49
+    worst = 0.0
+    for _ in range(400):
+        W = np.array([rng.uniform(0.05, 5.0), rng.uniform(-2.0, 2.0), rng.uniform(0.05, 5.0)])
+        QL = cons(W)
+        scale = np.array([QL[0], math.sqrt(QL[0] * QL[2]), QL[2]])
+        QR = QL + eps * scale * rng.uniform(-1.0, 1.0, 3)
+        st, Q, it = O.riemann_state(G, QL, QR)
+        assert st == 0 and it >= 1            # the oracle iterates
+        worst = max(worst, float(np.max(np.abs(Q - QL) / scale)))
+    assert worst <= 4.0 * eps, worst
