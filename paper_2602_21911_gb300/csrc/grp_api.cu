@@ -325,8 +325,8 @@ int enqueue_step(grp_ctx* c, double t_end)
     CK(record(c, e0));
   }
   if (c->p.solver == GRP_SOLVER_DET) {
-    CK(launch_det_step(a, c->det_ed, s));            // predictor, then the interface Riemann problems
-    c->launches += 2;
+    CK(launch_det_step(a, c->det_ed, s));            // predictor (two phases), then the interface Riemann problems
+    c->launches += 3;
   } else {
     CK(launch_flux(a, s));
     c->launches++;
@@ -453,7 +453,7 @@ int grp_create(grp_ctx** out, const grp_problem* p)
   AL(any_bad, MAX_REPAIR + 1) AL(stats, (long long)NSTATS * D) AL(scratch_norm, 3 * D)
   AL(tlist0, c->ncell) AL(tlist1, c->ncell) AL(ilist, c->nif) AL(lcount, 2 * (MAX_REPAIR + 1))
   if (p->solver == GRP_SOLVER_DET) {
-    AL(det_ed, (long long)det_doubles_per_cell(p->M, C) * c->ncell)
+    AL(det_ed, (long long)det_doubles(p->M, C, c->ncell))
     if (det_prepare(p->device) != 0) { free_all(c); delete c; return cuda_fail(cudaErrorUnknown, "DET tables"); }
   }
 #undef AL

@@ -91,6 +91,13 @@ int det_tables(int dev)
       }
     }
     for (int l = 0; l < n; ++l) for (int b = 0; b < n; ++b) T.Ti[l][b] = A[l][n + b];
+    for (int l = 0; l < n; ++l) {
+      T.Te[l] = 0.0;
+      for (int b = 0; b < n; ++b) {
+        T.Te[l] += T.Ti[l][b] * T.e0[b];
+        T.Tw[l][b] = T.Ti[l][b] * T.w[b];
+      }
+    }
   }
   if (cudaMemcpyToSymbol(c_det, t, sizeof(t)) != cudaSuccess) return -1;
   g_det_ready[dev] = true;
@@ -108,41 +115,33 @@ __device__ __forceinline__ void phys_flux(const Phys& ph, const double* Q, doubl
   F[2] = u * (Q[2] + p);
 }
 
-// predictor of cell gi: reconstruction (GRPrec or GRPrecNL), Picard
-// iteration, edge values.  One thread per cell.
-template <int SYS, int M, bool NL>
-__global__ void __launch_bounds__(128) k_det_predict(StepArgs a, double* __restrict__ ed)
+// The predictor's Picard iteration runs in two phases.  Most cells converge
+// in a few iterations (constant states in one, smooth flow in three), a few
+// near strong waves take tens; one thread per cell would hold every warp with
+// such a cell for all of them.  Phase 1 runs at most DET_PHASE1 iterations in
+// every cell; a cell still iterating saves its nodal values and joins a list
+// that phase 2 resumes on a fixed grid, with the same iteration and the same
+// limit, so the results are those of one uninterrupted iteration.
+constexpr int DET_PHASE1 = 4, DET_MAXIT = 64;
+
+// resume area after the edge values: slot s holds w[n][C] then q[n][n][C]
+struct DetResume {
+  double* state;       // [cap][(n + n n) C]
+  int* list;           // [cap] cells
+  int* count;          // cells offered to phase 2 (may exceed cap)
+  int cap;
+};
+
+// Picard iterations it0 <= it < it1 of one cell.  Returns 1 when converged,
+// -1 on an inadmissible nodal state, 0 when it1 was reached first.
+template <int SYS, int M>
+__device__ __forceinline__ int det_picard(const StepArgs& a, const DetTab& T, double nu, const double w[][SYS == SYS_EULER ? 3 : 1],
+                                          double q[][M + 1][SYS == SYS_EULER ? 3 : 1], int it0, int it1)
 {
   constexpr int n = M + 1, C = SYS == SYS_EULER ? 3 : 1;
-  const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gi >= a.ncell) return;
-  const int d = a.cell_dom[gi];
-  const DomStep& ds = a.ds[d];
-  if (!ds.active) return;
-  const long long c0 = a.cell_off[d], i0 = a.if_off[d];
-  const int N = (int)(a.cell_off[d + 1] - c0);
-  const int i = (int)(gi - c0);
-  const DetTab& T = c_det[M - 1];
-  double b[3][5];
-  bool fb = false;
-  cell_coeffs<SYS, M, NL>(a, c0, i0, N, a.bc[d], i, b, fb);
-  double w[n][C], q[n][n][C];
-#pragma unroll
-  for (int k = 0; k < n; ++k) {
-    const double xi = T.x[k] - 0.5, x2 = xi * xi;
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      const double v = b[c][0] + b[c][1] * xi + b[c][2] * (x2 - 1.0 / 12.0) + b[c][3] * x2 * xi +
-                       b[c][4] * (x2 * x2 - 1.0 / 80.0);
-      w[k][c] = v;
-#pragma unroll
-      for (int l = 0; l < n; ++l) q[k][l][c] = v;
-    }
-  }
-  const double nu = ds.nu;
-  bool ok = true;
-  for (int it = 0; it < 64 && ok; ++it) {
+  for (int it = it0; it < it1; ++it) {
     double f[n][n][C];
+    bool ok = true;
 #pragma unroll
     for (int k = 0; k < n; ++k)
 #pragma unroll
@@ -150,32 +149,45 @@ __global__ void __launch_bounds__(128) k_det_predict(StepArgs a, double* __restr
         if (SYS == SYS_EULER && !admissible(a.ph.gamma, q[k][l][0], q[k][l][1], q[k][l][2])) ok = false;
         phys_flux<SYS>(a.ph, q[k][l], f[k][l]);
       }
-    if (!ok) break;
-    double diff = 0.0, scale = 0.0;
+    if (!ok) return -1;
+    // q_kl = T^{-1} (phi(0) w_k - nu diag(w) df_k) = Te w_k - nu Tw df_k.  The
+    // largest update and value are maxima of non-negative doubles, taken on
+    // their bit patterns (integer max, the same order) off the FP64 pipe.
+    long long diff = 0, scale = 0;
 #pragma unroll
     for (int k = 0; k < n; ++k)
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        double rhs[n];
+        double df[n];
 #pragma unroll
         for (int l = 0; l < n; ++l) {
-          double df = 0.0;
+          double acc = 0.0;
 #pragma unroll
-          for (int aa = 0; aa < n; ++aa) df += T.D[k][aa] * f[aa][l][c];
-          rhs[l] = T.e0[l] * w[k][c] - nu * T.w[l] * df;
+          for (int aa = 0; aa < n; ++aa) acc += T.D[k][aa] * f[aa][l][c];
+          df[l] = nu * acc;
         }
 #pragma unroll
         for (int l = 0; l < n; ++l) {
-          double v = 0.0;
+          double v = T.Te[l] * w[k][c];
 #pragma unroll
-          for (int bb = 0; bb < n; ++bb) v += T.Ti[l][bb] * rhs[bb];
-          diff = fmax(diff, fabs(v - q[k][l][c]));
-          scale = fmax(scale, fabs(v));
+          for (int bb = 0; bb < n; ++bb) v -= T.Tw[l][bb] * df[bb];
+          diff = max(diff, __double_as_longlong(v - q[k][l][c]) & 0x7fffffffffffffffll);
+          scale = max(scale, __double_as_longlong(v) & 0x7fffffffffffffffll);
           q[k][l][c] = v;
         }
       }
-    if (diff <= 1e-13 * scale) break;
+    if (__longlong_as_double(diff) <= 1e-13 * __longlong_as_double(scale)) return 1;
   }
+  return 0;
+}
+
+// Edge values of cell gi from its converged nodal values (or, after an
+// inadmissible nodal state, its cell average, unevolved).
+template <int SYS, int M>
+__device__ __forceinline__ void det_finish(const StepArgs& a, const DetTab& T, long long gi, int d, bool ok,
+                                           const double q[][M + 1][SYS == SYS_EULER ? 3 : 1], double* ed)
+{
+  constexpr int n = M + 1, C = SYS == SYS_EULER ? 3 : 1;
   if (SYS == SYS_EULER && ok) {
 #pragma unroll
     for (int k = 0; k < n; ++k)
@@ -183,11 +195,9 @@ __global__ void __launch_bounds__(128) k_det_predict(StepArgs a, double* __restr
       for (int l = 0; l < n; ++l)
         if (!admissible(a.ph.gamma, q[k][l][0], q[k][l][1], q[k][l][2])) ok = false;
   }
-  unsigned long long* S = a.stats + (long long)d * NSTATS;
-  if (fb) atomicAdd(S + S_RECON_FB, 1ull);
   if (!ok) {
     // an inadmissible predictor state: the cell keeps its average, unevolved
-    atomicAdd(S + S_RECON_FB, 1ull);
+    atomicAdd(a.stats + (long long)d * NSTATS + S_RECON_FB, 1ull);
 #pragma unroll
     for (int side = 0; side < 2; ++side)
 #pragma unroll
@@ -214,6 +224,92 @@ __global__ void __launch_bounds__(128) k_det_predict(StepArgs a, double* __restr
         for (int bb = 0; bb < n; ++bb) v += (side ? T.e1[aa] : T.e0[aa]) * T.e1[bb] * q[aa][bb][c];
       ed[det_idx(M, C, a.ncell, side, n, c, gi)] = v;
     }
+  }
+}
+
+// Phase 1, one thread per cell: reconstruction (GRPrec or GRPrecNL), the
+// first DET_PHASE1 Picard iterations, edge values or a place on the list.
+template <int SYS, int M, bool NL>
+__global__ void __launch_bounds__(128) k_det_predict(StepArgs a, double* __restrict__ ed, DetResume r)
+{
+  constexpr int n = M + 1, C = SYS == SYS_EULER ? 3 : 1;
+  const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= a.ncell) return;
+  const int d = a.cell_dom[gi];
+  const DomStep& ds = a.ds[d];
+  if (!ds.active) return;
+  const long long c0 = a.cell_off[d], i0 = a.if_off[d];
+  const int N = (int)(a.cell_off[d + 1] - c0);
+  const int i = (int)(gi - c0);
+  const DetTab& T = c_det[M - 1];
+  double b[3][5];
+  bool fb = false;
+  cell_coeffs<SYS, M, NL>(a, c0, i0, N, a.bc[d], i, b, fb);
+  if (fb) atomicAdd(a.stats + (long long)d * NSTATS + S_RECON_FB, 1ull);
+  double w[n][C], q[n][n][C];
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    const double xi = T.x[k] - 0.5, x2 = xi * xi;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const double v = b[c][0] + b[c][1] * xi + b[c][2] * (x2 - 1.0 / 12.0) + b[c][3] * x2 * xi +
+                       b[c][4] * (x2 * x2 - 1.0 / 80.0);
+      w[k][c] = v;
+#pragma unroll
+      for (int l = 0; l < n; ++l) q[k][l][c] = v;
+    }
+  }
+  const double nu = ds.nu;
+  int st, it0 = 0, it1 = DET_PHASE1;
+  while (true) {                     // one Picard call site (twice at most: the list may be full)
+    st = det_picard<SYS, M>(a, T, nu, w, q, it0, it1);
+    if (st != 0 || it1 == DET_MAXIT) break;
+    const int slot = atomicAdd(r.count, 1);
+    if (slot < r.cap) {
+      double* z = r.state + (long long)slot * ((n + n * n) * C);
+#pragma unroll
+      for (int k = 0; k < n; ++k)
+#pragma unroll
+        for (int c = 0; c < C; ++c) z[k * C + c] = w[k][c];
+#pragma unroll
+      for (int k = 0; k < n; ++k)
+#pragma unroll
+        for (int l = 0; l < n; ++l)
+#pragma unroll
+          for (int c = 0; c < C; ++c) z[n * C + (k * n + l) * C + c] = q[k][l][c];
+      r.list[slot] = (int)gi;
+      return;
+    }
+    it0 = DET_PHASE1;                // the list is full: go on here
+    it1 = DET_MAXIT;
+  }
+  det_finish<SYS, M>(a, T, gi, d, st >= 0, q, ed);
+}
+
+// Phase 2: the listed cells resume their iteration, one thread per slot.
+template <int SYS, int M>
+__global__ void __launch_bounds__(128) k_det_resume(StepArgs a, double* __restrict__ ed, DetResume r)
+{
+  constexpr int n = M + 1, C = SYS == SYS_EULER ? 3 : 1;
+  const int cnt = *r.count < r.cap ? *r.count : r.cap;
+  const DetTab& T = c_det[M - 1];
+  for (int k0 = blockIdx.x * blockDim.x + threadIdx.x; k0 < cnt; k0 += gridDim.x * blockDim.x) {
+    const long long gi = r.list[k0];
+    const int d = a.cell_dom[gi];
+    const double* z = r.state + (long long)k0 * ((n + n * n) * C);
+    double w[n][C], q[n][n][C];
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int c = 0; c < C; ++c) w[k][c] = z[k * C + c];
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int l = 0; l < n; ++l)
+#pragma unroll
+        for (int c = 0; c < C; ++c) q[k][l][c] = z[n * C + (k * n + l) * C + c];
+    const int st = det_picard<SYS, M>(a, T, a.ds[d].nu, w, q, DET_PHASE1, DET_MAXIT);
+    det_finish<SYS, M>(a, T, gi, d, st >= 0, q, ed);
   }
 }
 
@@ -301,10 +397,32 @@ __global__ void __launch_bounds__(128) k_det_flux(StepArgs a, const double* __re
   }
 }
 
+// The resume area follows the edge values in the same buffer (det_doubles).
+long long det_cap(long long ncell) { return ncell / 4 + 1024; }
+
+DetResume det_resume(int M, int C, long long ncell, double* ed)
+{
+  const long long n = M + 1;
+  DetResume r;
+  r.cap = (int)det_cap(ncell);
+  r.state = ed + (long long)det_doubles_per_cell(M, C) * ncell;
+  r.list = reinterpret_cast<int*>(r.state + (long long)r.cap * (n + n * n) * C);
+  r.count = r.list + r.cap;
+  return r;
+}
+
 template <int SYS, int M, bool NL>
 cudaError_t predict_launch(const StepArgs& a, double* ed, cudaStream_t s)
 {
-  k_det_predict<SYS, M, NL><<<(unsigned)((a.ncell + 127) / 128), 128, 0, s>>>(a, ed);
+  constexpr int C = SYS == SYS_EULER ? 3 : 1;
+  const DetResume r = det_resume(M, C, a.ncell, ed);
+  cudaError_t e = cudaMemsetAsync(r.count, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  k_det_predict<SYS, M, NL><<<(unsigned)((a.ncell + 127) / 128), 128, 0, s>>>(a, ed, r);
+  // one thread per slot of the list (its capacity fixes the grid, so a
+  // captured graph serves every step; blocks past the count exit at once):
+  // the listed cells iterate side by side, not one after another
+  k_det_resume<SYS, M><<<(unsigned)((r.cap + 127) / 128), 128, 0, s>>>(a, ed, r);
   return cudaGetLastError();
 }
 
@@ -322,6 +440,13 @@ cudaError_t flux_launch(const StepArgs& a, const double* ed, cudaStream_t s)
 int det_prepare(int device) { return det_tables(device); }
 
 size_t det_doubles_per_cell(int M, int C) { return (size_t)2 * (M + 2) * C; }
+
+size_t det_doubles(int M, int C, long long ncell)
+{
+  const long long n = M + 1, cap = det_cap(ncell);
+  // edge values, resume states, then the list and its counter as ints
+  return (size_t)(det_doubles_per_cell(M, C) * ncell + cap * (n + n * n) * C + (cap + 2) / 2 + 1);
+}
 
 cudaError_t launch_det_step(const StepArgs& a, double* ed, cudaStream_t s)
 {

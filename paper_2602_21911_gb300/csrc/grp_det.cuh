@@ -24,6 +24,8 @@ struct DetTab {
   double D[DET_MAXN][DET_MAXN];        // D[k][a] = phi_a'(x_k)
   double e0[DET_MAXN], e1[DET_MAXN];   // phi_a(0), phi_a(1)
   double Ti[DET_MAXN][DET_MAXN];       // T^{-1}
+  double Te[DET_MAXN];                 // T^{-1} phi(0): sum_b Ti[l][b] e0[b]
+  double Tw[DET_MAXN][DET_MAXN];       // T^{-1} diag(w): Ti[l][b] w[b]
 };
 
 // ed layout: ed[((side * (M + 2) + g) * C + c) * ncell + cell], side 0 the

@@ -42,6 +42,7 @@ cudaError_t launch_post_adv(const BatchLaunch& L, cudaStream_t s);
 // the edge-value scratch, and the two launches of a step's GRP phase
 int det_prepare(int device);
 size_t det_doubles_per_cell(int M, int C);
+size_t det_doubles(int M, int C, long long ncell);   // the whole DET buffer: edge values and the resume area
 cudaError_t launch_det_step(const StepArgs& a, double* ed, cudaStream_t s);
 cudaError_t launch_post_euler(const BatchLaunch& L, cudaStream_t s);
 }  // namespace grp
