@@ -59,6 +59,77 @@ inline Phys make_phys(double lambda, double gamma, double rtol, int max_iter, in
 }
 
 // ---------------------------------------------------------------------------
+// Arithmetic helpers.  FP64 is the scarce pipe on this GPU; seeds come from
+// the FP32 special-function unit and are refined by FP64 Newton steps.
+// ---------------------------------------------------------------------------
+GRP_HD __forceinline__ float f32_log2(float x)
+{
+#ifdef __CUDA_ARCH__
+  return __log2f(x);
+#else
+  return log2f(x);
+#endif
+}
+
+GRP_HD __forceinline__ float f32_exp2(float x)
+{
+#ifdef __CUDA_ARCH__
+  return exp2f(x);
+#else
+  return exp2f(x);
+#endif
+}
+
+// 1/y to ~1e-14 relative: FP32 reciprocal seed, one FP64 Newton step.  Used
+// only for the Newton update of the star pressure, whose next iterate corrects
+// any residual of the step.
+GRP_HD __forceinline__ double rcp_newton_step(double y)
+{
+  const float yf = (float)y;
+  const float af = fabsf(yf);
+  if (!(af > 1e-30f && af < 1e30f)) return 1.0 / y;
+  double r = (double)(1.0f / yf);
+  const double e = fma(-y, r, 1.0);
+  return fma(r, e, r);
+}
+
+// 1/y for a positive normal y, correct to about an ulp: the hardware
+// reciprocal approximation (rcp.approx.ftz.f64, about 2^-22 relative) and two
+// Newton steps r <- r + r (1 - y r), each squaring the relative error.  Half
+// the FP64 instructions of a correctly rounded division; used where the result
+// feeds further arithmetic, not a comparison with the oracle's rounding.
+GRP_HD __forceinline__ double rcp64(double y)
+{
+#ifdef __CUDA_ARCH__
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(y));
+  double e = fma(-y, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-y, r, 1.0);
+  return fma(r, e, r);
+#else
+  return 1.0 / y;
+#endif
+}
+
+// x^(-1/7) for x > 0: FP32 seed 2^(-log2(x)/7), then two FP64 Newton steps on
+// w^-7 = x, w <- w (8 - x w^7)/7, each squaring the relative error
+// (2^-21 -> 2^-40 -> rounding).  Outside the FP32 normal range: pow.
+GRP_HD __forceinline__ double inv_root7(double x)
+{
+  const float xf = (float)x;
+  if (!(xf > 1e-36f && xf < 1e36f)) return pow(x, -1.0 / 7.0);
+  double w = (double)f32_exp2(-f32_log2(xf) * (1.0f / 7.0f));
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const double w2 = w * w, w4 = w2 * w2;
+    const double w7 = w4 * w2 * w;
+    w = w * fma(-x, w7, 8.0) * (1.0 / 7.0);
+  }
+  return w;
+}
+
+// ---------------------------------------------------------------------------
 // Section 3.1, GRPrec: closed forms of the four constrained fits in the
 // zero-mean basis phi_1 = xi, phi_2 = xi^2 - 1/12, phi_3 = xi^3,
 // phi_4 = xi^4 - 1/80 (each has zero cell average, so conservation in cell i
@@ -158,16 +229,19 @@ GRP_HD __forceinline__ void grprec_nl_coeffs(const double d[7], double dx, doubl
   double p[3][5];
   nl_sides<M>(d, p[0], p[2]);
   grprec_coeffs<M>(d[0], d[1], d[2], d[4], d[5], p[1]);
-  const double lam[3] = {1.0, NL_LAMBDA_C, 1.0};
-  double om[3], sum = 0.0;
+  // beta_k = (lambda_k / s_k) / sum_j (lambda_j / s_j), s_k = (eps + OI_k)^4,
+  // with numerator and denominator multiplied by s_L s_C s_R: products and
+  // one reciprocal instead of four divisions (s_k >= eps^4 = 1e-56, so the
+  // products of two stay far inside the double range)
+  double sk[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const double o = NL_EPS + dx * nl_indicator<M>(p[k]);
     const double o2 = o * o;
-    om[k] = lam[k] / (o2 * o2);
-    sum += om[k];
+    sk[k] = o2 * o2;
   }
-  const double is = 1.0 / sum;
+  const double om[3] = {sk[1] * sk[2], NL_LAMBDA_C * (sk[0] * sk[2]), sk[0] * sk[1]};
+  const double is = rcp64(om[0] + om[1] + om[2]);
   b[0] = d[1];
 #pragma unroll
   for (int q = 1; q <= 4; ++q) b[q] = q <= M ? (om[0] * p[0][q] + om[1] * p[1][q] + om[2] * p[2][q]) * is : 0.0;
@@ -220,77 +294,6 @@ GRP_HD __forceinline__ void euler_flux(double g, double r, double m, double E, d
   F[0] = m;
   F[1] = m * u + p;
   F[2] = u * (E + p);
-}
-
-// ---------------------------------------------------------------------------
-// Arithmetic helpers.  FP64 is the scarce pipe on this GPU; seeds come from
-// the FP32 special-function unit and are refined by FP64 Newton steps.
-// ---------------------------------------------------------------------------
-GRP_HD __forceinline__ float f32_log2(float x)
-{
-#ifdef __CUDA_ARCH__
-  return __log2f(x);
-#else
-  return log2f(x);
-#endif
-}
-
-GRP_HD __forceinline__ float f32_exp2(float x)
-{
-#ifdef __CUDA_ARCH__
-  return exp2f(x);
-#else
-  return exp2f(x);
-#endif
-}
-
-// 1/y to ~1e-14 relative: FP32 reciprocal seed, one FP64 Newton step.  Used
-// only for the Newton update of the star pressure, whose next iterate corrects
-// any residual of the step.
-GRP_HD __forceinline__ double rcp_newton_step(double y)
-{
-  const float yf = (float)y;
-  const float af = fabsf(yf);
-  if (!(af > 1e-30f && af < 1e30f)) return 1.0 / y;
-  double r = (double)(1.0f / yf);
-  const double e = fma(-y, r, 1.0);
-  return fma(r, e, r);
-}
-
-// 1/y for a positive normal y, correct to about an ulp: the hardware
-// reciprocal approximation (rcp.approx.ftz.f64, about 2^-22 relative) and two
-// Newton steps r <- r + r (1 - y r), each squaring the relative error.  Half
-// the FP64 instructions of a correctly rounded division; used where the result
-// feeds further arithmetic, not a comparison with the oracle's rounding.
-GRP_HD __forceinline__ double rcp64(double y)
-{
-#ifdef __CUDA_ARCH__
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(y));
-  double e = fma(-y, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-y, r, 1.0);
-  return fma(r, e, r);
-#else
-  return 1.0 / y;
-#endif
-}
-
-// x^(-1/7) for x > 0: FP32 seed 2^(-log2(x)/7), then two FP64 Newton steps on
-// w^-7 = x, w <- w (8 - x w^7)/7, each squaring the relative error
-// (2^-21 -> 2^-40 -> rounding).  Outside the FP32 normal range: pow.
-GRP_HD __forceinline__ double inv_root7(double x)
-{
-  const float xf = (float)x;
-  if (!(xf > 1e-36f && xf < 1e36f)) return pow(x, -1.0 / 7.0);
-  double w = (double)f32_exp2(-f32_log2(xf) * (1.0f / 7.0f));
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const double w2 = w * w, w4 = w2 * w2;
-    const double w7 = w4 * w2 * w;
-    w = w * fma(-x, w7, 8.0) * (1.0 / 7.0);
-  }
-  return w;
 }
 
 // ---------------------------------------------------------------------------

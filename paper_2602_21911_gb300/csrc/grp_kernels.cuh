@@ -276,7 +276,12 @@ __device__ __forceinline__ void cell_coeffs(const StepArgs& a, long long c0, lon
     const double dx = a.dx[(int)a.cell_dom[c0 + i]];
     if (SYS == SYS_EULER) {
       const double Qi[3] = {d[0][1], d[1][1], d[2][1]};
-      const Eig e = make_eig(a.ph, Qi, to_prim(a.ph.gamma, Qi[0], Qi[1], Qi[2]));
+      const double iri = rcp64(Qi[0]);
+      Prim wi;
+      wi.r = Qi[0];
+      wi.u = Qi[1] * iri;
+      wi.p = a.ph.gm1 * (Qi[2] - 0.5 * Qi[1] * wi.u);
+      const Eig e = make_eig(a.ph, Qi, wi, iri);
       double w[3][7];
 #pragma unroll
       for (int j = 0; j < 7; ++j) {
