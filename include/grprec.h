@@ -72,11 +72,13 @@ enum {
 /* per-domain counters (grp_get_stats), each an unsigned 64-bit integer */
 enum {
   GRP_STAT_STEPS = 0,          /* steps taken */
-  GRP_STAT_NEWTON_SUM = 1,     /* star-pressure Newton iterations, summed */
+  GRP_STAT_NEWTON_SUM = 1,     /* star-pressure Newton iterations, summed (a leading Riemann problem
+                                  whose two states agree to 2^-48 has equal data: its exact solution
+                                  is that state, and it counts no iteration) */
   GRP_STAT_NEWTON_MAX = 2,     /* max iterations at one interface */
   GRP_STAT_RECON_FB = 3,       /* cells reconstructed at degree 0 (inadmissible trace) */
   GRP_STAT_FLUX_FB = 4,        /* interfaces whose time series was cut to its leading term */
-  GRP_STAT_RS_CALLS = 5,       /* exact Riemann solves */
+  GRP_STAT_RS_CALLS = 5,       /* exact Riemann solves, equal data included */
   GRP_STAT_LOW_ORDER = 6,      /* interfaces recomputed with the first-order Godunov flux */
   GRP_STAT_GUESS_USED = 7,     /* Newton solves started from the network's prediction */
   GRP_STAT_GUESS_REJECTED = 8, /* learned guesses rejected (range / non-finite / stall) */
