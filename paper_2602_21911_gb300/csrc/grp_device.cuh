@@ -280,11 +280,17 @@ GRP_HD __forceinline__ void to_cons(const Phys& ph, Prim w, double Q[3])
   Q[2] = w.p * ph.i_gm1 + 0.5 * w.r * w.u * w.u;
 }
 
-// rho > 0 and p = (g-1)(E - m^2/(2 rho)) > 0, written without a division
+// rho > 0 and p = (g-1)(E - m^2/(2 rho)) > 0, written without a division.
+// On the GPU rho > 0 is a signed-integer test of the bits (off the FP64 pipe:
+// true for positive values; a NaN rho passes it but fails the second test).
 GRP_HD __forceinline__ bool admissible(double g, double r, double m, double E)
 {
   (void)g;
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(r) > 0ll && 2.0 * E * r > m * m;
+#else
   return r > 0.0 && 2.0 * E * r > m * m;
+#endif
 }
 
 GRP_HD __forceinline__ void euler_flux(double g, double r, double m, double E, double F[3])

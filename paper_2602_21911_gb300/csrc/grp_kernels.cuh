@@ -675,7 +675,11 @@ __device__ __forceinline__ int update_one(const StepArgs& a, long long gi, int d
     // multiplied through by rho > 0 (admissible): no division
     const double rp = (g - 1.0) * (Q[2] * Q[0] - 0.5 * Q[1] * Q[1]);
     const double d0 = DMP_REL * rhi, d1 = DMP_REL * phi;
-    ok = Q[0] >= rlo - d0 && Q[0] <= rhi + d0 && rp >= (plo - d1) * Q[0] && rp <= (phi + d1) * Q[0];
+    // Q[0] and rp are positive here, so each bound test is a signed-integer
+    // compare of the bits (exact: a negative bound has a negative pattern)
+    const long long q0 = __double_as_longlong(Q[0]), rq = __double_as_longlong(rp);
+    ok = q0 >= __double_as_longlong(rlo - d0) && q0 <= __double_as_longlong(rhi + d0) &&
+         rq >= __double_as_longlong((plo - d1) * Q[0]) && rq <= __double_as_longlong((phi + d1) * Q[0]);
   }
   const unsigned char flag = adm ? (ok ? 0 : 1) : 2;
   const unsigned char before = pass < 0 ? 0 : a.troubled[gi];
