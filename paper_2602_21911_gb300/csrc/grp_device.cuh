@@ -904,8 +904,8 @@ struct Gauss {
 // 2^-48 of the sum of its two values; the momentum on the scale
 // sqrt(rho E)) are equal data: the exact solution is the constant state and
 // no wave forms.  The interpolating reconstructions (degrees 2 and 4) put the
-// interface datum itself on both sides of every interface of smooth flow, so
-// there both traces differ by a few ulps only.
+// interface datum itself on both sides of every interface whose two cells
+// kept their polynomials, so there the traces are bitwise equal.
 constexpr double EQ_TOL = 3.552713678800501e-15;   // 2^-48
 
 GRP_HD __forceinline__ bool equal_data(const double QL[3], const double QR[3])
