@@ -319,7 +319,7 @@ int grp_probe_fp64_peak(int device, double *flops_per_s);
  * buffers the caller owns, and keeps its scratch (interface fluxes, repair
  * flags, per-domain words, index tables) in a file-scope __device__ array of
  * the library sized for GRP_NOALLOC_MAX_CELLS cells; every GPU that loads the
- * library holds that array (about 2.3 MB) until the process exits.
+ * library holds that array (about 3.5 MB) until the process exits.
  *   avg_in, iface_in:   device, C planes of n_cells / n_ifaces doubles (read)
  *   avg_out, iface_out: device, same sizes (written); must not alias the inputs
  *   t, t_end:           time of the input state, end time (INFINITY: none)
@@ -328,7 +328,11 @@ int grp_probe_fp64_peak(int device, double *flops_per_s);
  * n_ifaces = n_cells + (bc == GRP_BC_TRANSMISSIVE).  Allocates nothing: no
  * cudaMalloc, no cudaFree, no allocating library routine.  The first call on a
  * device (with that device current) looks up the device address of the scratch
- * array; make that first call before any stream capture.  Every call shares the
+ * array and keeps it for that device; make that first call before any stream
+ * capture.  A reset of the device's primary context (cudaDeviceReset)
+ * invalidates the kept address: do not call this entry point on a device after
+ * resetting it in the same process.  A launch error pending from earlier,
+ * unrelated work on the calling thread is cleared on entry, not reported.  Every call shares the
  * scratch and it keeps the last call's contents; the call clears what must
  * start at zero.  Calls that overlap on the GPU (other streams, other host
  * threads) race on the scratch: serialise them.  Synchronises `stream` before

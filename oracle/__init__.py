@@ -63,6 +63,8 @@ def lib():
                                     _D, _I, ctypes.c_int, ctypes.c_double, _L, _D, ctypes.c_int]
         L.or_recon_nl.argtypes = [ctypes.c_int, _D, ctypes.c_double, _D, _D]
         L.or_char_basis.argtypes = [ctypes.c_double, _D, _D, _D]
+        L.or_update_repair.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, _D, _D, _D, ctypes.c_char_p, _D, _L]
         _lib = L
     return _lib
 
@@ -96,6 +98,25 @@ def char_basis(gamma, Q):
     R, L = np.zeros(9), np.zeros(9)
     lib().or_char_basis(float(gamma), _dp(Q), _dp(R), _dp(L))
     return R.reshape(3, 3), L.reshape(3, 3)
+
+
+def update_repair(gamma, avg, flux, gnew, bc, dx, dt, low=None):
+    """The update and a-posteriori repair of one Euler step on given fluxes
+    (Section 2, eq. eq_finite_volume; the repair is a reading, not in the
+    paper).  avg [3, N]; flux, gnew [nif, 3] high-order fluxes and interface
+    data; low [nif] (1 = already first order).  Returns (status, cand [3, N],
+    flux, gnew, low, stats) after the repair."""
+    avg = _f64(avg)
+    N = avg.shape[1]
+    nif = N if bc == PERIODIC else N + 1
+    f = _f64(flux).reshape(nif, 3).copy()
+    g = _f64(gnew).reshape(nif, 3).copy()
+    lo = np.zeros(nif, dtype=np.int8) if low is None else np.ascontiguousarray(low, dtype=np.int8).copy()
+    cand = np.zeros((3, N))
+    stats = np.zeros(NSTATS, dtype=np.int64)
+    st = lib().or_update_repair(float(gamma), N, int(bc), float(dx), float(dt), _dp(avg), _dp(f), _dp(g),
+                                lo.ctypes.data_as(ctypes.c_char_p), _dp(cand), stats.ctypes.data_as(_L))
+    return st, cand, f, g, lo, stats
 
 
 def recon(M, qbar, g):

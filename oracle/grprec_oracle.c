@@ -1064,6 +1064,55 @@ static int first_order_interface(const params *P, int N, int bc, int j, const re
 }
 
 /*
+ * Conservative update, eq. eq_finite_volume with S = 0 (Section 2), from the
+ * fluxes flux[j * C + c] of the nif interfaces, into cand[c * N + i], with
+ * the a-posteriori repair (READING, MOOD-like; not in the paper): a candidate
+ * average that is inadmissible, or whose density or pressure leaves the range
+ * of the old averages of cells i-1, i, i+1 by more than OR_DMP_REL of the
+ * range's magnitude (dmp_ok), marks its cell troubled; both of its interfaces
+ * not yet recomputed (low[j] == 0) take the first-order Godunov flux of the
+ * cell averages and its state as interface datum (gnew), and low[j] is set.
+ * The candidates are then formed again from the current fluxes.  Passes
+ * 0 .. OR_MAX_REPAIR - 1 repair; pass OR_MAX_REPAIR only checks.  A cell
+ * still inadmissible when no further interface can change gives
+ * OR_NONPHYSICAL (the candidates are kept: the domain freezes on them).
+ */
+static int update_repair(const params *P, int N, int bc, real dx, real dt, const real *avg, long cstride,
+                         real *flux, real *gnew, char *low, real *cand, long long *st)
+{
+  const int C = P->system == OR_EULER ? 3 : 1;
+  int status = OR_OK;
+  for (int pass = 0; ; ++pass) {
+    int bad = 0, changed = 0;
+    for (int i = 0; i < N; ++i) {
+      int jl = i, jr = (bc == OR_BC_PERIODIC) ? (i + 1) % N : i + 1;
+      for (int c = 0; c < C; ++c)
+        cand[c * N + i] = avg[c * cstride + i] - dt / dx * (flux[jr * C + c] - flux[jl * C + c]);
+    }
+    if (P->system != OR_EULER) break;
+    for (int i = 0; i < N && status == OR_OK; ++i) {
+      real Q[3] = { cand[i], cand[N + i], cand[2 * N + i] };
+      int adm = euler_admissible(P->gamma, Q);
+      if (adm && dmp_ok(P->gamma, N, bc, i, avg, cstride, Q)) continue;
+      if (!adm) bad = 1;
+      if (pass >= OR_MAX_REPAIR) continue;
+      int js[2] = { i, (bc == OR_BC_PERIODIC) ? (i + 1) % N : i + 1 };
+      for (int e = 0; e < 2; ++e) {
+        int j = js[e];
+        if (low[j]) continue;
+        int s = first_order_interface(P, N, bc, j, avg, cstride, flux + j * C, gnew + j * C, st);
+        if (s != OR_OK) { status = s; break; }
+        low[j] = 1;
+        changed = 1;
+      }
+    }
+    if (status != OR_OK) break;
+    if (!changed) { if (bad) status = OR_NONPHYSICAL; break; }
+  }
+  return status;
+}
+
+/*
  * avg, iface point at this domain's first cell / interface; strides are the
  * plane lengths.  Returns a status; on success the domain holds step n+1.
  */
@@ -1236,43 +1285,7 @@ static int step_domain(const params *P, int N, int bc, real dx, real dt, real *a
 
   OR_PHASE(2);
   real *cand = (real *)malloc(sizeof(real) * N * C);
-  if (status == OR_OK) {
-    /* conservative update, eq. eq_finite_volume with S = 0 */
-    for (int pass = 0; ; ++pass) {
-      int bad = 0, changed = 0;
-      for (int i = 0; i < N; ++i) {
-        int jl = i, jr = (bc == OR_BC_PERIODIC) ? (i + 1) % N : i + 1;
-        for (int c = 0; c < C; ++c)
-          cand[c * N + i] = avg[c * cstride + i] - dt / dx * (flux[jr * C + c] - flux[jl * C + c]);
-      }
-      if (P->system != OR_EULER) break;
-      /* READING (a posteriori, MOOD-like): a candidate average that is
-       * inadmissible, or whose density or pressure leaves the range of the
-       * old averages of cells i-1, i, i+1 by more than OR_DMP_REL of the
-       * range's magnitude, marks its cell troubled; both of its interfaces
-       * are recomputed with the first-order Godunov flux of the cell
-       * averages, in at most OR_MAX_REPAIR rounds.  A cell still
-       * inadmissible at the end freezes the domain. */
-      for (int i = 0; i < N && status == OR_OK; ++i) {
-        real Q[3] = { cand[i], cand[N + i], cand[2 * N + i] };
-        int adm = euler_admissible(P->gamma, Q);
-        if (adm && dmp_ok(P->gamma, N, bc, i, avg, cstride, Q)) continue;
-        if (!adm) bad = 1;
-        if (pass >= OR_MAX_REPAIR) continue;
-        int js[2] = { i, (bc == OR_BC_PERIODIC) ? (i + 1) % N : i + 1 };
-        for (int e = 0; e < 2; ++e) {
-          int j = js[e];
-          if (low[j]) continue;
-          int s = first_order_interface(P, N, bc, j, avg, cstride, flux + j * C, gnew + j * C, st);
-          if (s != OR_OK) { status = s; break; }
-          low[j] = 1;
-          changed = 1;
-        }
-      }
-      if (status != OR_OK) break;
-      if (!changed) { if (bad) status = OR_NONPHYSICAL; break; }
-    }
-  }
+  if (status == OR_OK) status = update_repair(P, N, bc, dx, dt, avg, cstride, flux, gnew, low, cand, st);
   if (status == OR_OK || status == OR_NONPHYSICAL) {
     for (int i = 0; i < N; ++i)
       for (int c = 0; c < C; ++c) avg[c * cstride + i] = cand[c * N + i];
@@ -1375,4 +1388,28 @@ int or_run_solver(int system, double lambda, double gamma, int M, int recon, int
   }
   free(coff); free(ioff);
   return 0;
+}
+
+/* The update and repair phase of one Euler step on given fluxes (see
+ * update_repair): avg [3][N] old averages, flux and gnew [nif][3] the
+ * high-order fluxes and interface data (in: as the GRP produced them; out:
+ * after the repair), low [nif] (in/out; 1 = already first order), cand [3][N]
+ * the new averages, stats [OR_NSTATS] counters (added to).  Returns the status. */
+int or_update_repair(double gamma, int N, int bc, double dx, double dt, const double *avg, double *flux,
+                     double *gnew, char *low, double *cand, long long *stats)
+{
+  params P;
+  memset(&P, 0, sizeof(P));
+  P.system = OR_EULER; P.gamma = gamma; P.M = 1; P.cfl = 1;
+  P.rtol = 1e-12; P.max_iter = 50; P.guess_kind = OR_GUESS_PVRS; P.dt_hold = 1;
+  const int nif = bc == OR_BC_PERIODIC ? N : N + 1;
+  real *a = (real *)malloc(sizeof(real) * 3 * N), *f = (real *)malloc(sizeof(real) * 3 * nif);
+  real *g = (real *)malloc(sizeof(real) * 3 * nif), *cd = (real *)malloc(sizeof(real) * 3 * N);
+  for (int k = 0; k < 3 * N; ++k) a[k] = avg[k];
+  for (int k = 0; k < 3 * nif; ++k) { f[k] = flux[k]; g[k] = gnew[k]; }
+  int st = update_repair(&P, N, bc, dx, dt, a, N, f, g, low, cd, stats);
+  for (int k = 0; k < 3 * N; ++k) cand[k] = (double)cd[k];
+  for (int k = 0; k < 3 * nif; ++k) { flux[k] = (double)f[k]; gnew[k] = (double)g[k]; }
+  free(a); free(f); free(g); free(cd);
+  return st;
 }

@@ -82,6 +82,14 @@ int or_init_iface(int system, double lambda, double gamma, int n_ifaces,
                   const double *lim_minus, const double *lim_plus, double *iface);
 
 /* Advance every domain n_steps steps or to t_end, whichever comes first. */
+/* The update and repair phase of one Euler step (eq. eq_finite_volume with the
+ * a-posteriori first-order repair, a reading: not in the paper) on given
+ * high-order fluxes: avg [3][N]; flux, gnew [nif][3] in/out; low [nif] in/out;
+ * cand [3][N] out; stats [OR_NSTATS] added to.  Returns OR_OK, OR_NONPHYSICAL
+ * or the status of a failed first-order Riemann problem. */
+int or_update_repair(double gamma, int N, int bc, double dx, double dt, const double *avg, double *flux,
+                     double *gnew, char *low, double *cand, long long *stats);
+
 int or_run(int system, double lambda, double gamma, int M, double cfl,
            int n_domains, const int *n_cells, const double *x_left, const double *x_right,
            const int *bc, double newton_rtol, int newton_max_iter, int guess_kind, int dt_hold,

@@ -11,6 +11,8 @@
 // GPU loading the library holds until the process exits.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "grp_kernels.cuh"
 #include "grp_launch.h"
 #include "grprec.h"
@@ -49,12 +51,19 @@ struct Words {
   unsigned char bc;
 };
 constexpr size_t SCRATCH_BYTES = align256(OFF_WORDS + sizeof(Words));
+// the public header states the size as about 3.5 MB
+static_assert(SCRATCH_BYTES > 3400000 && SCRATCH_BYTES < 3600000, "update the scratch size in grprec.h");
 
 // The scratch.  Every call shares it and it keeps the last call's contents.
 static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
 
 constexpr int MAX_DEVICES = 64;
-unsigned char* g_scratch_addr[MAX_DEVICES];   // device address of g_scratch, per device
+// Device address of g_scratch per device, looked up once per device with that
+// device current.  The lock makes concurrent first calls from several host
+// threads safe.  A reset of a device's primary context (cudaDeviceReset)
+// invalidates the address kept for it (the header says so).
+std::mutex g_scratch_lock;
+unsigned char* g_scratch_addr[MAX_DEVICES];
 
 // Zeroes what must start at zero and writes the index tables and words.
 __global__ void k_noalloc_setup(unsigned char* base, int N, int nif, double dx, int bc, double t)
@@ -110,14 +119,20 @@ extern "C" int grp_step_noalloc(int system, double lambda, double gamma, int M, 
   if ((const double*)avg_out == avg_in || (const double*)iface_out == iface_in) return GRP_E_INVALID_ARG;
   if (isnan(t) || isnan(t_end)) return GRP_E_INVALID_ARG;
 
+  // a pending launch error of earlier, unrelated work on this thread is
+  // cleared here so that it is not reported as this call's failure
+  (void)cudaGetLastError();
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return GRP_E_CUDA;
-  if (!g_scratch_addr[dev]) {
-    // once per device, with that device current: the device address of the
-    // scratch (in host code the symbol itself is only a host-side stand-in)
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return GRP_E_CUDA;
-    g_scratch_addr[dev] = (unsigned char*)p;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_lock);
+    if (!g_scratch_addr[dev]) {
+      // once per device, with that device current: the device address of the
+      // scratch (in host code the symbol itself is only a host-side stand-in)
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return GRP_E_CUDA;
+      g_scratch_addr[dev] = (unsigned char*)p;
+    }
   }
   unsigned char* base = g_scratch_addr[dev];
   cudaStream_t s = (cudaStream_t)stream;

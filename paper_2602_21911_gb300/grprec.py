@@ -148,24 +148,56 @@ def grp_riemann_batch(QL, QR, ps, iters, status, used=None, gamma=1.4, guess=0, 
                                     stream), "grp_riemann_batch")
 
 
-def grp_step_noalloc(prob, avg_in, iface_in, avg_out, iface_out, t, t_end=float("inf"), stream=None):
-    """One step of a single-domain problem through the allocation-free entry
-    point; the four buffers are device tensors the caller owns.  Returns
-    (t_new, status)."""
-    n = np.asarray(prob["n_cells"])
+def noalloc_check_buffers(prob, avg_in, iface_in, avg_out, iface_out, current_device=None):
+    """Reject, before any call into the library, buffers the allocation-free
+    step cannot take: each must be a contiguous float64 CUDA tensor on the
+    current device (the library resolves its scratch on the current device),
+    holding C planes of n_cells (averages) or n_ifaces (interface data)
+    doubles, and the outputs must not overlap the inputs.  Returns the four
+    device addresses."""
+    n = np.asarray(prob["n_cells"]).reshape(-1)
     if n.size != 1:
         raise GrpError("grp_step_noalloc advances one domain")
-    ptrs = []
-    for x in (avg_in, iface_in, avg_out, iface_out):
-        p, dev = _ptr(x)
-        if not dev:
-            raise GrpError("grp_step_noalloc takes device buffers")
-        ptrs.append(p)
+    C = 3 if int(prob["system"]) == GRP_EULER_IDEAL else 1
+    N = int(n[0])
+    nif = N + (1 if int(np.asarray(prob["bc"]).reshape(-1)[0]) == GRP_BC_TRANSMISSIVE else 0)
+    spans = []
+    for name, x, size in (("avg_in", avg_in, C * N), ("iface_in", iface_in, C * nif),
+                          ("avg_out", avg_out, C * N), ("iface_out", iface_out, C * nif)):
+        if not hasattr(x, "data_ptr") or not getattr(x, "is_cuda", False):
+            raise GrpError("grp_step_noalloc: %s must be a CUDA tensor" % name)
+        if str(x.dtype) != "torch.float64":
+            raise GrpError("grp_step_noalloc: %s must be float64" % name)
+        if not x.is_contiguous():
+            raise GrpError("grp_step_noalloc: %s must be contiguous" % name)
+        if x.numel() != size:
+            raise GrpError("grp_step_noalloc: %s holds %d doubles, %d expected" % (name, x.numel(), size))
+        if current_device is None:
+            import torch
+            current_device = torch.cuda.current_device()
+        if x.device.index != current_device:
+            raise GrpError("grp_step_noalloc: %s is on cuda:%s, the current device is cuda:%d"
+                           % (name, x.device.index, current_device))
+        spans.append((x.data_ptr(), x.data_ptr() + 8 * size))
+    for o in (2, 3):
+        for i in (0, 1):
+            if spans[o][0] < spans[i][1] and spans[i][0] < spans[o][1]:
+                raise GrpError("grp_step_noalloc: outputs must not overlap the inputs")
+    return [sp[0] for sp in spans]
+
+
+def grp_step_noalloc(prob, avg_in, iface_in, avg_out, iface_out, t, t_end=float("inf"), stream=None):
+    """One step of a single-domain problem through the allocation-free entry
+    point; the four buffers are device tensors the caller owns (checked by
+    noalloc_check_buffers).  Returns (t_new, status)."""
+    ptrs = noalloc_check_buffers(prob, avg_in, iface_in, avg_out, iface_out)
+    n = np.asarray(prob["n_cells"]).reshape(-1)
     t_out, st = ctypes.c_double(0.0), ctypes.c_int(0)
     _check(load().grp_step_noalloc(int(prob["system"]), float(prob.get("lam", 1.0)),
                                    float(prob.get("gamma", 1.4)), int(prob["M"]), float(prob["cfl"]),
-                                   int(n[0]), float(np.asarray(prob["x_left"])[0]),
-                                   float(np.asarray(prob["x_right"])[0]), int(np.asarray(prob["bc"])[0]),
+                                   int(n[0]), float(np.asarray(prob["x_left"]).reshape(-1)[0]),
+                                   float(np.asarray(prob["x_right"]).reshape(-1)[0]),
+                                   int(np.asarray(prob["bc"]).reshape(-1)[0]),
                                    *ptrs, float(t), float(t_end), ctypes.byref(t_out), ctypes.byref(st),
                                    stream), "grp_step_noalloc")
     return t_out.value, st.value

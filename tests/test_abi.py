@@ -38,3 +38,53 @@ def test_invalid_problem_is_rejected_on_the_host():
             grprec.Solver(dict(prob, **bad))
     with pytest.raises(grprec.GrpError, match="invalid"):
         grprec.Solver(dict(prob, n_cells=[0]))
+
+
+class _FakeCuda:
+    """Stands in for a torch CUDA tensor: only the attributes the buffer
+    checks of the allocation-free step read (no GPU, no library call)."""
+
+    def __init__(self, n, dtype="torch.float64", contiguous=True, device=0, addr=1 << 20, cuda=True):
+        self.n, self.dtype, self.contiguous, self.addr, self.is_cuda = n, dtype, contiguous, addr, cuda
+        self.device = type("Dev", (), {"index": device})()
+
+    def data_ptr(self):
+        return self.addr
+
+    def is_contiguous(self):
+        return self.contiguous
+
+    def numel(self):
+        return self.n
+
+
+def test_noalloc_buffers_are_checked_before_any_launch():
+    from paper_2602_21911_gb300 import grprec, inputs
+    prob, *_ = inputs.sod(100, M=2)                      # transmissive: 101 interfaces
+    N, nif = 100, 101
+
+    def bufs(**over):
+        b = dict(avg_in=_FakeCuda(3 * N, addr=1 << 20), iface_in=_FakeCuda(3 * nif, addr=2 << 20),
+                 avg_out=_FakeCuda(3 * N, addr=3 << 20), iface_out=_FakeCuda(3 * nif, addr=4 << 20))
+        b.update(over)
+        return [b[k] for k in ("avg_in", "iface_in", "avg_out", "iface_out")]
+
+    assert grprec.noalloc_check_buffers(prob, *bufs(), current_device=0) == [1 << 20, 2 << 20, 3 << 20, 4 << 20]
+    bad = {
+        "CUDA tensor": dict(avg_in=_FakeCuda(3 * N, cuda=False)),
+        "float64": dict(iface_in=_FakeCuda(3 * nif, dtype="torch.float32", addr=2 << 20)),
+        "contiguous": dict(avg_out=_FakeCuda(3 * N, contiguous=False, addr=3 << 20)),
+        "expected": dict(iface_out=_FakeCuda(3 * N, addr=4 << 20)),          # 3 N instead of 3 (N + 1)
+        "current device": dict(avg_out=_FakeCuda(3 * N, device=1, addr=3 << 20)),
+        "overlap": dict(avg_out=_FakeCuda(3 * N, addr=(1 << 20) + 8)),
+    }
+    for what, over in bad.items():
+        with pytest.raises(grprec.GrpError, match=what):
+            grprec.noalloc_check_buffers(prob, *bufs(**over), current_device=0)
+    with pytest.raises(grprec.GrpError, match="one domain"):
+        two = dict(prob, n_cells=[50, 50])
+        grprec.noalloc_check_buffers(two, *bufs(), current_device=0)
+    # a numpy array is host memory: rejected
+    import numpy as np
+    with pytest.raises(grprec.GrpError, match="CUDA tensor"):
+        grprec.noalloc_check_buffers(prob, np.zeros(3 * N), *bufs()[1:], current_device=0)

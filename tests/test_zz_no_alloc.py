@@ -34,14 +34,30 @@ def _context_two_steps(prob, avg, lm, lp):
     return g0, out
 
 
-@pytest.mark.parametrize("case,tol", [("wave", SMOOTH_TOL), ("sod", DISC_TOL)])
-def test_noalloc_matches_the_allocating_entry_point_on_two_calls(case, tol):
+CASES = {
+    # periodic smooth runs (smooth tolerance)
+    "advection_sine_M2": (lambda: I.advection_sine(300, M=2), SMOOTH_TOL),
+    "advection_sine_M3": (lambda: I.advection_sine(257, M=3), SMOOTH_TOL),
+    "euler_wave_M1": (lambda: I.euler_wave(500, 1), SMOOTH_TOL),
+    "euler_wave_M2": (lambda: I.euler_wave(500, 2), SMOOTH_TOL),
+    "euler_wave_M3": (lambda: I.euler_wave(333, 3), SMOOTH_TOL),
+    "euler_wave_M4": (lambda: I.euler_wave(400, 4), SMOOTH_TOL),
+    # gamma other than 7/5 takes the generic-gamma kernels
+    "euler_wave_gamma53_M2": (lambda: I.euler_wave(256, 2, gamma=5.0 / 3.0), SMOOTH_TOL),
+    # transmissive shock tubes (discontinuous tolerance; repair rounds run)
+    "sod_M1": (lambda: I.sod(513, M=1), DISC_TOL),
+    "sod_M2": (lambda: I.sod(777, M=2), DISC_TOL),
+    "sod_M4": (lambda: I.sod(640, M=4), DISC_TOL),
+    "sod_gamma53_M3": (lambda: I.sod(300, M=3, gamma=5.0 / 3.0), DISC_TOL),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_noalloc_matches_the_allocating_entry_point_on_two_calls(case):
     torch = pytest.importorskip("torch")
     from paper_2602_21911_gb300 import grprec
-    if case == "wave":
-        prob, avg, lm, lp = I.euler_wave(500, 2)
-    else:
-        prob, avg, lm, lp = I.sod(777, M=2)
+    make, tol = CASES[case]
+    prob, avg, lm, lp = make()
     g0, ref = _context_two_steps(prob, avg, lm, lp)
     dev = torch.device("cuda", 0)
     a_in = torch.tensor(avg, device=dev)
