@@ -55,8 +55,7 @@ def rel_diff_iface(a, b, prob):
 
 def oracle_ulp_sensitivity(prob, avg, lm, lp, n_steps, t_end=np.inf, seed=0):
     """How far the oracle's own result moves when every input average moves
-    by one ulp (seeded signs): the conditioning of the run.  A GPU result
-    within a modest multiple of it is as close as the arithmetic allows."""
+    by one ulp (seeded signs): the conditioning of the run."""
     rng = np.random.default_rng(seed)
     a0 = oracle_run(prob, avg, lm, lp, n_steps, t_end)
     pert = np.where(rng.random(avg.shape) < 0.5, np.nextafter(avg, -np.inf), np.nextafter(avg, np.inf))
@@ -64,12 +63,25 @@ def oracle_ulp_sensitivity(prob, avg, lm, lp, n_steps, t_end=np.inf, seed=0):
     return float(rel_diff(a1.avg, a0.avg, prob).max())
 
 
-def check_parity(prob, avg, lm, lp, n_steps, tol, t_end=np.inf, conditioned=False, **kw):
-    """GPU vs oracle after n_steps (or at t_end).  conditioned: the tolerance
-    becomes max(tol, 100 x the oracle's one-ulp sensitivity of this run), for
-    runs whose conditioning the method itself makes worse than tol."""
-    if conditioned:
-        tol = max(tol, 100.0 * oracle_ulp_sensitivity(prob, avg, lm, lp, n_steps, t_end))
+def oracle_one_value_sensitivity(prob, avg, lm, lp, n_steps, t_end=np.inf):
+    """The oracle's response to a one-ulp increase of one input value (the
+    density of the middle cell of the first domain)."""
+    a0 = oracle_run(prob, avg, lm, lp, n_steps, t_end)
+    ap = avg.copy()
+    k = I.cell_offsets(prob)[1] // 2
+    ap[0, k] = np.nextafter(ap[0, k], np.inf)
+    a1 = oracle_run(prob, ap, lm, lp, n_steps, t_end)
+    return float(rel_diff(a1.avg, a0.avg, prob).max())
+
+
+def check_parity(prob, avg, lm, lp, n_steps, tol, t_end=np.inf, exempt=None, **kw):
+    """GPU vs oracle after n_steps (or at t_end): statuses and step counts
+    exactly, times, averages and interface data within tol per domain and
+    component.  exempt: {domain position: label} of domains listed as out of
+    tolerance (tests/out_of_tolerance.py); each such domain is checked for
+    ill-conditioning instead of the bound.  Returns (oracle state, GPU
+    results, largest difference over the domains held to the bound)."""
+    from out_of_tolerance import check_exempt
     S = oracle_run(prob, avg, lm, lp, n_steps, t_end)
     s, a, g, t, stats, status = gpu_run(prob, avg, lm, lp, n_steps, t_end, **kw)
     assert np.array_equal(status, S.status), (status, S.status)
@@ -77,9 +89,15 @@ def check_parity(prob, avg, lm, lp, n_steps, tol, t_end=np.inf, conditioned=Fals
     ok = (S.status == O.OK) | (S.status == O.NONPHYSICAL)
     assert ok.any()
     assert np.array_equal(stats[ok, 0].astype(np.int64), S.stats[ok, 0]), "step counts differ"
-    assert np.allclose(t[ok], S.t[ok], rtol=tol, atol=0)   # dt follows S_max of the state
-    rd = rel_diff(a, S.avg, prob)[ok]
-    ri = rel_diff_iface(g, S.iface, prob)[ok]
+    held = ok.copy()
+    for d, label in (exempt or {}).items():
+        held[d] = False
+        if ok[d]:
+            one = I.split_domains(prob, avg, lm, lp, which=[d])[0]
+            check_exempt(oracle_one_value_sensitivity(*one, n_steps, t_end), tol, label)
+    assert np.allclose(t[held], S.t[held], rtol=tol, atol=0)   # dt follows S_max of the state
+    rd = rel_diff(a, S.avg, prob)[held]
+    ri = rel_diff_iface(g, S.iface, prob)[held]
     assert rd.max() <= tol, ("averages", rd.max())
     assert ri.max() <= tol, ("interface data", ri.max())
     return S, (a, g, t, stats, status), rd.max()

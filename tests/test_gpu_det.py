@@ -42,17 +42,17 @@ def test_euler_wave_transmissive():
 @pytest.mark.parametrize("M", [1, 2, 3])
 def test_sod(M):
     prob, avg, lm, lp = I.sod(200, M=M)
-    check_parity(_det(prob), avg, lm, lp, 10 ** 6, DISC_TOL, t_end=0.2, conditioned=True)
+    check_parity(_det(prob), avg, lm, lp, 10 ** 6, DISC_TOL, t_end=0.2)
 
 
 def test_sod_grprecnl():
     prob, avg, lm, lp = I.sod(150, M=2, xc=0.3)
-    check_parity(_det(prob, recon=1), avg, lm, lp, 10 ** 6, DISC_TOL, t_end=0.2, conditioned=True)
+    check_parity(_det(prob, recon=1), avg, lm, lp, 10 ** 6, DISC_TOL, t_end=0.2)
 
 
 def test_batched_subset():
     prob, avg, lm, lp = I.batched(domains=np.arange(0, 65536, 401)[:120])
-    check_parity(_det(prob), avg, lm, lp, 25, DISC_TOL, conditioned=True)
+    check_parity(_det(prob), avg, lm, lp, 25, DISC_TOL)
 
 
 def test_det_runs_flat_and_graphs_replay_bitwise():

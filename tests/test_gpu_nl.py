@@ -3,18 +3,19 @@ discontinuous advection, the Euler density wave, the shock tube, the 123
 problem, transmissive ghost handling at degree 4, and every launch form on a
 batch of domains.
 
-The nonlinear weights (r = 4, eps = 1e-14) switch steeply where an
-indicator of a nearly constant characteristic field crosses eps; a run that
-passes such a point answers a one-ulp change of its input with up to ~1e-9
-(the Euler density wave at degree 1: 2.6e-9 in the oracle itself).  The
-Euler tests therefore take the tolerance max(base, 100 x the oracle's own
-one-ulp sensitivity of the same run)."""
+Every case holds the stated tolerance except the degree-1 Euler density wave
+run to t = 1, which is listed as out of tolerance (tests/out_of_tolerance.py):
+there the oracle itself answers a one-ulp input change with ~1e-9, so its
+first 100 steps are held to 1e-11 and the full run is checked for that
+ill-conditioning instead."""
 import numpy as np
 import pytest
 
 from paper_2602_21911_gb300 import inputs as I
 
-from parity import DISC_TOL, SMOOTH_TOL, check_parity
+from out_of_tolerance import NL_EULER_WAVE_M1_T1, check_exempt
+from parity import (DISC_TOL, SMOOTH_TOL, check_parity, gpu_run, oracle_run, oracle_ulp_sensitivity, rel_diff,
+                    rel_diff_iface)
 
 pytestmark = pytest.mark.gpu
 
@@ -42,26 +43,47 @@ def test_multiwave_many_periods():
     check_parity(_nl(prob), avg, lm, lp, 10 ** 6, DISC_TOL, t_end=20.0)
 
 
-@pytest.mark.parametrize("M", [1, 2, 3, 4])
+@pytest.mark.parametrize("M", [2, 3, 4])
 def test_euler_wave(M):
     prob, avg, lm, lp = I.euler_wave(64, M)
-    check_parity(_nl(prob), avg, lm, lp, 10 ** 6, SMOOTH_TOL, t_end=1.0, conditioned=True)
+    check_parity(_nl(prob), avg, lm, lp, 10 ** 6, SMOOTH_TOL, t_end=1.0)
+
+
+def test_euler_wave_degree1_first_100_steps():
+    prob, avg, lm, lp = I.euler_wave(64, 1)
+    check_parity(_nl(prob), avg, lm, lp, 100, SMOOTH_TOL)
+
+
+def test_euler_wave_degree1_to_t1_is_listed_out_of_tolerance():
+    """Not held to 1e-11: the oracle's own one-ulp response is ~1e-9 (the
+    listed entry); the test asserts that ill-conditioning and reports the
+    GPU difference."""
+    prob, avg, lm, lp = I.euler_wave(64, 1)
+    prob = _nl(prob)
+    sens = oracle_ulp_sensitivity(prob, avg, lm, lp, 10 ** 6, 1.0)
+    check_exempt(sens, SMOOTH_TOL, "GRPrecNL degree-1 Euler wave to t = 1")
+    S = oracle_run(prob, avg, lm, lp, 10 ** 6, 1.0)
+    s, a, g, t, stats, status = gpu_run(prob, avg, lm, lp, 10 ** 6, 1.0)
+    assert np.array_equal(status, S.status) and t[0] == S.t[0] == 1.0
+    d = max(rel_diff(a, S.avg, prob).max(), rel_diff_iface(g, S.iface, prob).max())
+    print("GRPrecNL degree-1 Euler wave to t = 1: GPU - oracle %.2e, oracle one-ulp response %.2e "
+          "(listed: %s)" % (d, sens, NL_EULER_WAVE_M1_T1))
 
 
 def test_euler_wave_transmissive_degree4_ghosts():
     prob, avg, lm, lp = I.euler_wave(77, 4, bc=I.TRANSMISSIVE)
-    check_parity(_nl(prob), avg, lm, lp, 60, SMOOTH_TOL, conditioned=True)
+    check_parity(_nl(prob), avg, lm, lp, 60, SMOOTH_TOL)
 
 
 @pytest.mark.parametrize("M", [1, 2, 3, 4])
 def test_sod(M):
     prob, avg, lm, lp = I.sod(200, M=M, xc=0.3)
-    check_parity(_nl(prob), avg, lm, lp, 10 ** 6, DISC_TOL, t_end=0.2, conditioned=True)
+    check_parity(_nl(prob), avg, lm, lp, 10 ** 6, DISC_TOL, t_end=0.2)
 
 
 def test_123_problem():
     prob, avg, lm, lp = I.euler_123(200, M=2)
-    check_parity(_nl(prob), avg, lm, lp, 10 ** 6, DISC_TOL, t_end=0.15, conditioned=True)
+    check_parity(_nl(prob), avg, lm, lp, 10 ** 6, DISC_TOL, t_end=0.15)
 
 
 @pytest.mark.parametrize("form", [1, 2, 3])
@@ -70,4 +92,4 @@ def test_batched_forms(form):
     prob, avg, lm, lp = I.batched(domains=np.arange(0, 65536, 331)[:150])
     s = grprec.Solver(_nl(prob))
     s.set_launch(form, 256, 2048, 4)
-    check_parity(_nl(prob), avg, lm, lp, 30, DISC_TOL, solver=s, conditioned=True)
+    check_parity(_nl(prob), avg, lm, lp, 30, DISC_TOL, solver=s)

@@ -62,6 +62,17 @@ def test_batched_subset_100_steps():
     S, G, rd = check_parity(prob, avg, lm, lp, 100, DISC_TOL)
 
 
+@pytest.mark.parametrize("M", [1, 3, 4])
+def test_batched_subset_other_degrees(M):
+    """The batch at the degrees bench.py also reports (150 domains, 100 steps);
+    at degree 4 two domains of this subset are listed as out of tolerance."""
+    from out_of_tolerance import BATCH_SUBSET_M4
+    ids = np.arange(0, 65536, 331)[:150]
+    prob, avg, lm, lp = I.batched(M=M, domains=ids)
+    pos = {int(np.flatnonzero(ids == d)[0]): "batch subset domain %d at degree 4" % d for d in BATCH_SUBSET_M4}
+    check_parity(prob, avg, lm, lp, 100, DISC_TOL, exempt=pos if M == 4 else None)
+
+
 def test_batched_stats_agree():
     ids = np.arange(0, 65536, 997)[:60]
     prob, avg, lm, lp = I.batched(domains=ids)
