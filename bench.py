@@ -72,6 +72,7 @@ def parse():
                     help="N > 1: a batch per rank (weak) or one batch split across the ranks (strong)")
     ap.add_argument("--plain-domains", type=int, default=128, help="sample size of the plain form (0: skip)")
     ap.add_argument("--plain-steps", type=int, default=60)
+    ap.add_argument("--no-l1", action="store_true", help="skip the L1 errors against exact solutions")
     return ap.parse_args()
 
 
@@ -313,6 +314,152 @@ def other_workloads(local, stream):
     return out
 
 
+# ---------------------------------------------------------------------------
+# Exact solutions for the L1 errors of the measurement (host, numpy): the
+# textbook ideal-gas Riemann solution (pressure function, Newton on the star
+# pressure, self-similar sampling), vectorised over problems and points.  A
+# reference for error norms, not the scheme: nothing here feeds the kernels.
+# ---------------------------------------------------------------------------
+def _pressure_fn(p, rho, pk, c, g):
+    A, B = 2.0 / ((g + 1.0) * rho), (g - 1.0) / (g + 1.0) * pk
+    shock = p > pk
+    sq = np.sqrt(A / (p + B))
+    f = np.where(shock, (p - pk) * sq, 2.0 * c / (g - 1.0) * ((p / pk) ** ((g - 1.0) / (2.0 * g)) - 1.0))
+    df = np.where(shock, sq * (1.0 - 0.5 * (p - pk) / (p + B)), (p / pk) ** (-(g + 1.0) / (2.0 * g)) / (rho * c))
+    return f, df
+
+
+def exact_riemann_density(WL, WR, xi, g=1.4):
+    """Density of the exact Riemann solution of primitive states WL | WR (each
+    a tuple of arrays of shape (n,)) at the rays xi (shape (n, k)); also
+    returns the largest wave speed of each problem.  No vacuum data."""
+    rl, ul, pl = [np.asarray(v, dtype=np.float64)[:, None] for v in WL]
+    rr, ur, pr = [np.asarray(v, dtype=np.float64)[:, None] for v in WR]
+    cl, cr = np.sqrt(g * pl / rl), np.sqrt(g * pr / rr)
+    z = (g - 1.0) / (2.0 * g)
+    p = ((cl + cr - 0.5 * (g - 1.0) * (ur - ul)) / (cl / pl ** z + cr / pr ** z)) ** (1.0 / z)
+    p = np.maximum(p, 1e-12 * np.maximum(pl, pr))
+    for _ in range(80):
+        fl, dfl = _pressure_fn(p, rl, pl, cl, g)
+        fr, dfr = _pressure_fn(p, rr, pr, cr, g)
+        p = np.maximum(p - (fl + fr + ur - ul) / (dfl + dfr), 1e-3 * p)
+    fl, _ = _pressure_fn(p, rl, pl, cl, g)
+    fr, _ = _pressure_fn(p, rr, pr, cr, g)
+    us = 0.5 * (ul + ur) + 0.5 * (fr - fl)
+    gm = (g - 1.0) / (g + 1.0)
+    # left wave
+    sl_shock = ul - cl * np.sqrt((g + 1.0) / (2.0 * g) * p / pl + z)
+    rl_star = np.where(p > pl, rl * (p / pl + gm) / (gm * p / pl + 1.0), rl * (p / pl) ** (1.0 / g))
+    cl_star = cl * (p / pl) ** z
+    # right wave
+    sr_shock = ur + cr * np.sqrt((g + 1.0) / (2.0 * g) * p / pr + z)
+    rr_star = np.where(p > pr, rr * (p / pr + gm) / (gm * p / pr + 1.0), rr * (p / pr) ** (1.0 / g))
+    cr_star = cr * (p / pr) ** z
+    x = np.asarray(xi, dtype=np.float64)
+    with np.errstate(invalid="ignore"):            # the fan formulas outside their fans are not selected
+        left_fan = rl * (2.0 / (g + 1.0) + gm / cl * (ul - x)) ** (2.0 / (g - 1.0))
+        right_fan = rr * (2.0 / (g + 1.0) - gm / cr * (ur - x)) ** (2.0 / (g - 1.0))
+    rho_left = np.where(p > pl, np.where(x < sl_shock, rl, rl_star),
+                        np.where(x < ul - cl, rl, np.where(x < us - cl_star, left_fan, rl_star)))
+    rho_right = np.where(p > pr, np.where(x > sr_shock, rr, rr_star),
+                         np.where(x > ur + cr, rr, np.where(x > us + cr_star, right_fan, rr_star)))
+    rho = np.where(x < us, rho_left, rho_right)
+    smax = np.maximum(np.abs(np.where(p > pl, sl_shock, ul - cl)), np.abs(np.where(p > pr, sr_shock, ur + cr)))
+    return rho, smax[:, 0]
+
+
+def exact_riemann_averages(WL, WR, xc, t, edges, g=1.4, n_gauss=16):
+    """Cell averages of the exact density at time t, 16-point Gauss per cell;
+    edges (n, N + 1) per problem."""
+    s, w = np.polynomial.legendre.leggauss(n_gauss)
+    e = np.asarray(edges, dtype=np.float64)
+    dx = e[:, 1:] - e[:, :-1]
+    x = 0.5 * (e[:, :-1] + e[:, 1:])[:, :, None] + 0.5 * dx[:, :, None] * s[None, None, :]
+    n, N = dx.shape
+    rho, _ = exact_riemann_density(WL, WR, ((x - xc) / t).reshape(n, -1), g)
+    return (rho.reshape(n, N, n_gauss) * (0.5 * w)).sum(axis=2)
+
+
+def l1_measurements(args, device, stream, w, box):
+    """L1 density errors against exact solutions, the 'fixed L1 error' of the
+    metric: (a) the batch's Riemann-problem domains of the plain sample at a
+    common time before their waves reach the ends, advanced by the plain form
+    (one solver per domain), the batched form and the batched form with the
+    learned guess: the three L1 errors agree; (b) Sod's shock tube
+    (x_c = 0.5) at t = 0.2 on 2^16, 2^17 and 2^18 cells, with the observed
+    order."""
+    import torch
+    from paper_2602_21911_gb300 import grprec, inputs as I
+    out = {}
+    t_l1 = 0.01
+    ids = np.unique(np.linspace(0, args.domains - 1, args.plain_domains).astype(np.int64))
+    par = I.batched_params(args.domains, 2602)
+    rp = [int(d) for d in ids if not par["smooth"][d]]
+    WL = (np.ones(len(rp)), par["uL"][rp], np.ones(len(rp)))
+    WR = (par["r_rho"][rp], par["uR"][rp], par["r_p"][rp])
+    _, smax = exact_riemann_density(WL, WR, np.zeros((len(rp), 1)))
+    keep = [d for d, sm in zip(rp, smax) if 0.45 / sm >= t_l1]
+    prob, avg, lm, lp = I.batched(args.domains, seed=2602, M=args.M, domains=keep)
+    co = I.cell_offsets(prob)
+    exact = np.zeros(int(prob["n_cells"].sum()))
+    for k, d in enumerate(keep):
+        N = int(prob["n_cells"][k])
+        e = np.linspace(0.0, 1.0, N + 1)[None, :]
+        exact[co[k]:co[k + 1]] = exact_riemann_averages((np.ones(1), par["uL"][[d]], np.ones(1)),
+                                                        (par["r_rho"][[d]], par["uR"][[d]], par["r_p"][[d]]),
+                                                        0.5, t_l1, e)[0]
+    res = {}
+    for name, guess in (("batched_pvrs", grprec.GRP_GUESS_PVRS), ("batched_learned", grprec.GRP_GUESS_MLP)):
+        if guess == grprec.GRP_GUESS_MLP and w is None:
+            continue
+        sb = grprec.Solver(prob, device=device, stream=stream.cuda_stream, guess=guess)
+        if guess == grprec.GRP_GUESS_MLP:
+            sb.set_guess_model(w, box)
+        sb.set_initial(avg, lm, lp)
+        sb.advance_to(t_l1)
+        l1, _, _ = sb.error_norms(exact)
+        res[name] = l1
+        sb.close()
+    l1p = np.zeros(len(keep))
+    for k, (pj, aj, mj, qj) in enumerate(I.split_domains(prob, avg, lm, lp)):
+        sj = grprec.Solver(pj, device=device, stream=stream.cuda_stream)
+        sj.set_launch(grprec.GRP_LAUNCH_FLAT)
+        sj.set_graph(0)
+        sj.set_initial(aj, mj, qj)
+        sj.advance_to(t_l1)
+        l1p[k] = sj.error_norms(np.ascontiguousarray(exact[co[k]:co[k + 1]]))[0][0]
+        sj.close()
+    res["plain"] = l1p
+    out["batch_riemann_domains"] = {
+        "t": t_l1, "domains": len(keep), "of_riemann_domains_in_sample": len(rp),
+        "selection": "Riemann-problem domains of the plain sample whose fastest wave stays 0.05 from the ends",
+        "mean_l1_rho": {k: float(v.mean()) for k, v in res.items()},
+        "max_rel_diff_of_l1_vs_plain": {k: float(np.max(np.abs(v - l1p) / l1p)) for k, v in res.items()
+                                        if k != "plain"}}
+    sod = []
+    for N in (1 << 16, 1 << 17, 1 << 18):
+        prob, avg, lm, lp = I.sod(N, M=args.M)
+        s = grprec.Solver(prob, device=device, stream=stream.cuda_stream)
+        s.set_initial(avg, lm, lp)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.advance_to(0.2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        stats, status = s.get_stats()
+        ex = exact_riemann_averages((np.ones(1), np.zeros(1), np.ones(1)), (np.full(1, 0.125), np.zeros(1),
+                                    np.full(1, 0.1)), 0.5, 0.2, np.linspace(0.0, 1.0, N + 1)[None, :])[0]
+        l1, _, _ = s.error_norms(ex)
+        sec = e0.elapsed_time(e1) * 1e-3
+        sod.append({"N": N, "steps": int(stats[0, 0]), "l1_rho": float(l1[0]), "seconds": sec,
+                    "cell_updates_per_s": N * int(stats[0, 0]) / sec})
+        s.close()
+    for a, b in zip(sod[:-1], sod[1:]):
+        b["order"] = float(np.log2(a["l1_rho"] / b["l1_rho"]))
+    out["sod_t0.2"] = sod
+    return out
+
+
 def cpu_baseline(args, steps=100, stride=4):
     """The oracle as it stands, OpenMP over domains, on a bounded sample."""
     import oracle as O
@@ -517,6 +664,8 @@ def main():
                                           "kernel's own arithmetic); executed_frac_ncu = the kernel's executed "
                                           "FP64 flops over the peak's, from the committed ncu summary",
                             "executed_frac_ncu": executed}
+    if not args.no_l1 and args.plain_domains > 0:
+        line["l1"] = l1_measurements(args, local, stream, w, box)
     if not args.no_other:
         line["workloads"] = other_workloads(local, stream)
     if not args.no_cpu_baseline:

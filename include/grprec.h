@@ -6,7 +6,7 @@
  * finite volume schemes" (arXiv 2602.21911), for 1D linear advection and the
  * ideal-gas Euler equations, over many independent 1D domains at once:
  *
- *   Q_i^{n+1} = Q_i^n - dt/dx (F_{i+1/2} - F_{i-1/2})         (Section 2, eq. eq_finite_volume, S = 0)
+ *   Q_i^{n+1} = Q_i^n - dt/dx (F_{i+1/2} - F_{i-1/2}) + dt S_i   (Section 2, eq. eq_finite_volume)
  *
  *   - GRPrec reconstruction of degree M = 1..4 from the cell averages and the
  *     interface data kept from the previous step                (Section 3.1)
@@ -50,6 +50,7 @@ enum { GRP_GUESS_PVRS = 0, GRP_GUESS_TRRS = 1, GRP_GUESS_MLP = 2 };/* Newton ini
 enum { GRP_LAUNCH_AUTO = 0, GRP_LAUNCH_FLAT = 1, GRP_LAUNCH_FUSED = 2, GRP_LAUNCH_SPLIT = 3 }; /* grp_set_launch */
 enum { GRP_RECON_GRPREC = 0, GRP_RECON_GRPRECNL = 1 };            /* reconstruction (Sections 3.1, 3.3-3.4) */
 enum { GRP_SOLVER_TT = 0, GRP_SOLVER_DET = 1 };                   /* GRP solver (Section 2, Section 4.1) */
+enum { GRP_SOURCE_NONE = 0, GRP_SOURCE_LINEAR = 1, GRP_SOURCE_GRAVITY = 2 };  /* source term S(Q) (Section 2) */
 
 /* return codes */
 enum {
@@ -115,6 +116,16 @@ typedef struct {
                             problems of the evolved edge values at the M+1 time nodes (flux) and at
                             the end of the step (interface datum).  DET runs the FLAT launch form
                             whatever grp_set_launch asks; grp_step_noalloc always uses TT. */
+  int source;            /* source term S(Q) of the balance law d_t Q + d_x F(Q) = S(Q) (Section 2):
+                            GRP_SOURCE_NONE; GRP_SOURCE_LINEAR, advection only, S(q) = source_coef q;
+                            GRP_SOURCE_GRAVITY, Euler only, S = (0, -g rho, -g m) with
+                            g = source_coef (a constant acceleration -g along x).  The source enters
+                            the GRP's Cauchy-Kovalevskaya series, and the update adds dt S_i, S_i the
+                            space-time average of S over the cell's own evolution (eq. eq:source).
+                            Needs GRP_SOLVER_TT and GRP_RECON_GRPREC; runs the FLAT launch form;
+                            grp_step_noalloc has no source.  Reconstructions of degree <= 2 keep a
+                            steady state that is a polynomial of degree <= 2 (Section 3.5). */
+  double source_coef;    /* k or g above (finite) */
 } grp_problem;
 
 /*

@@ -19,6 +19,7 @@ from . import build as _build
 ADVECTION, EULER = 0, 1
 RECON_GRPREC, RECON_GRPRECNL = 0, 1
 SOLVER_TT, SOLVER_DET = 0, 1
+SOURCE_NONE, SOURCE_LINEAR, SOURCE_GRAVITY = 0, 1, 2
 PERIODIC, TRANSMISSIVE = 0, 1
 GUESS_PVRS, GUESS_TRRS, GUESS_GIVEN = 0, 1, 2
 OK, NEWTON_NO_CONV, VACUUM, NONPHYSICAL = 0, 1, 2, 3
@@ -62,6 +63,13 @@ def lib():
                                     ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _I,
                                     _D, _I, ctypes.c_int, ctypes.c_double, _L, _D, ctypes.c_int]
         L.or_recon_nl.argtypes = [ctypes.c_int, _D, ctypes.c_double, _D, _D]
+        L.or_run_full.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                  _I, _D, _D, _I, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  _D, _D, _D, _I, _D, _I, ctypes.c_int, ctypes.c_double, _L, _D, ctypes.c_int]
+        L.or_ck_series_src.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_double, _D, _D]
+        L.or_ck_series_src.restype = None
         L.or_char_basis.argtypes = [ctypes.c_double, _D, _D, _D]
         L.or_update_repair.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, _D, _D, _D, ctypes.c_char_p, _D, _L]
@@ -160,6 +168,16 @@ def ck_series(system, lam, gamma, M, qa0):
     return out
 
 
+def ck_series_src(system, lam, gamma, M, source, coef, qa0):
+    """ck_series with a source term S(Q) (SOURCE_LINEAR: S = coef q for
+    advection; SOURCE_GRAVITY: S = (0, -coef rho, -coef m) for Euler)."""
+    C = 3 if system == EULER else 1
+    qa0 = _f64(np.reshape(qa0, (M + 1, C)))
+    out = np.zeros((M + 1, M + 1, C))
+    lib().or_ck_series_src(system, lam, gamma, M, source, float(coef), _dp(qa0), _dp(out))
+    return out
+
+
 def grp_interface(system, lam, gamma, M, dt, trL, trR, rtol=1e-12, max_iter=50,
                   guess_kind=GUESS_PVRS):
     """(status, flux[C], g_new[C], iterations, truncated) for traces tr[k, c]."""
@@ -200,7 +218,8 @@ def run(prob, state, n_steps, t_end=np.inf, dt_fixed=None, n_threads=1):
     """Advance ``state`` in place by n_steps or to t_end (Section 2 update).
 
     ``prob`` keys: system, lam, gamma, M, cfl, n_cells, x_left, x_right, bc,
-    newton_rtol, newton_max_iter, guess, dt_hold, recon and solver (optional).
+    newton_rtol, newton_max_iter, guess, dt_hold, recon, solver, source and
+    source_coef (the last four optional).
     """
     n_cells = np.ascontiguousarray(prob["n_cells"], dtype=np.int32)
     xl = _f64(prob["x_left"])
@@ -210,8 +229,10 @@ def run(prob, state, n_steps, t_end=np.inf, dt_fixed=None, n_threads=1):
     if dt_fixed is not None:
         dtf = _f64(dt_fixed)
         assert len(dtf) >= n_steps
-    rc = lib().or_run_solver(prob["system"], prob.get("lam", 1.0), prob.get("gamma", 1.4), prob["M"],
-                      prob.get("recon", RECON_GRPREC), prob.get("solver", SOLVER_TT), prob["cfl"], len(n_cells), _ip(n_cells), _dp(xl), _dp(xr), _ip(bc),
+    rc = lib().or_run_full(prob["system"], prob.get("lam", 1.0), prob.get("gamma", 1.4), prob["M"],
+                      prob.get("recon", RECON_GRPREC), prob.get("solver", SOLVER_TT),
+                      prob.get("source", SOURCE_NONE), float(prob.get("source_coef", 0.0)),
+                      prob["cfl"], len(n_cells), _ip(n_cells), _dp(xl), _dp(xr), _ip(bc),
                       prob.get("newton_rtol", 1e-12), prob.get("newton_max_iter", 50),
                       prob.get("guess", GUESS_PVRS), prob.get("dt_hold", 1),
                       _dp(state.avg), _dp(state.iface), _dp(state.t), _ip(state.nstep),

@@ -612,6 +612,24 @@ static void deriv_rp(real gamma, const real *Q0, const real *DL, const real *DR,
 /* ------------------------------------------------------------------------- */
 #define SIDX(a, b) ((a) * (MAXM + 1) + (b))
 
+/* Source term S(Q) of eq. eq_hyperbolic_system (Section 2).  Both sources
+ * built here are linear in Q, so the series of S(Q(x, tau)) is S applied to
+ * each coefficient:
+ *   OR_SOURCE_LINEAR (advection):  S(q) = k q
+ *   OR_SOURCE_GRAVITY (Euler):     S(rho, m, E) = (0, -g rho, -g m), a constant
+ *                                  acceleration -g along x
+ * A NULL descriptor or OR_SOURCE_NONE is S = 0. */
+typedef struct { int kind; real coef; } srcspec;
+
+static void source_apply(const srcspec *S, const real *Q, real *out)
+{
+  out[0] = out[1] = out[2] = 0;
+  if (!S || S->kind == OR_SOURCE_NONE) return;
+  if (S->kind == OR_SOURCE_LINEAR) { out[0] = S->coef * Q[0]; return; }
+  out[1] = -S->coef * Q[0];
+  out[2] = -S->coef * Q[1];
+}
+
 static real series_product(const real *x, const real *y, int a, int b)
 {
   real s = 0;
@@ -620,12 +638,18 @@ static real series_product(const real *x, const real *y, int a, int b)
   return s;
 }
 
-static void ck_series(int system, real lambda, real gamma, int M, real q[][MAXC])
+/* With a source, d_tau Q = -d_x F(Q) + S(Q) (the PDE of the GRP, eq. eq:GRP):
+ * q[a][b+1] = (-(a+1) f[a+1][b] + s[a][b]) / (b+1), s the series of S(Q). */
+static void ck_series(int system, real lambda, real gamma, int M, real q[][MAXC], const srcspec *S)
 {
   if (system == OR_ADVECTION) {
     for (int b = 0; b < M; ++b)
-      for (int a = 0; a + b + 1 <= M; ++a)
+      for (int a = 0; a + b + 1 <= M; ++a) {
+        real sq[3];
+        source_apply(S, q[SIDX(a, b)], sq);
         q[SIDX(a, b + 1)][0] = -(real)(a + 1) / (b + 1) * lambda * q[SIDX(a + 1, b)][0];
+        if (S && S->kind != OR_SOURCE_NONE) q[SIDX(a, b + 1)][0] = q[SIDX(a, b + 1)][0] + sq[0] / (b + 1);
+      }
     return;
   }
   real rho[(MAXM + 1) * (MAXM + 1)], m[(MAXM + 1) * (MAXM + 1)], E[(MAXM + 1) * (MAXM + 1)];
@@ -655,9 +679,14 @@ static void ck_series(int system, real lambda, real gamma, int M, real q[][MAXC]
       F[1][SIDX(a, b)] = mu[SIDX(a, b)] + p[SIDX(a, b)];
       F[2][SIDX(a, b)] = series_product(u, Ep, a, b);
     }
-    for (int a = 0; a + b + 1 <= M; ++a)
-      for (int c = 0; c < 3; ++c)
+    for (int a = 0; a + b + 1 <= M; ++a) {
+      real sq[3];
+      source_apply(S, q[SIDX(a, b)], sq);
+      for (int c = 0; c < 3; ++c) {
         q[SIDX(a, b + 1)][c] = -(real)(a + 1) / (b + 1) * F[c][SIDX(a + 1, b)];
+        if (S && S->kind != OR_SOURCE_NONE) q[SIDX(a, b + 1)][c] = q[SIDX(a, b + 1)][c] + sq[c] / (b + 1);
+      }
+    }
   }
 }
 
@@ -668,7 +697,22 @@ void or_ck_series(int system, double lambda, double gamma, int M, const double *
   for (int i = 0; i < (MAXM + 1) * (MAXM + 1); ++i) q[i][0] = q[i][1] = q[i][2] = 0;
   for (int a = 0; a <= M; ++a)
     for (int c = 0; c < C; ++c) q[SIDX(a, 0)][c] = qa0[a * C + c];
-  ck_series(system, lambda, gamma, M, q);
+  ck_series(system, lambda, gamma, M, q, 0);
+  for (int a = 0; a <= M; ++a)
+    for (int b = 0; b <= M; ++b)
+      for (int c = 0; c < C; ++c) qout[(a * (M + 1) + b) * C + c] = q[SIDX(a, b)][c];
+}
+
+void or_ck_series_src(int system, double lambda, double gamma, int M, int source, double coef,
+                      const double *qa0, double *qout)
+{
+  int C = system == OR_EULER ? 3 : 1;
+  srcspec S = { source, coef };
+  real q[(MAXM + 1) * (MAXM + 1)][MAXC];
+  for (int i = 0; i < (MAXM + 1) * (MAXM + 1); ++i) q[i][0] = q[i][1] = q[i][2] = 0;
+  for (int a = 0; a <= M; ++a)
+    for (int c = 0; c < C; ++c) q[SIDX(a, 0)][c] = qa0[a * C + c];
+  ck_series(system, lambda, gamma, M, q, &S);
   for (int a = 0; a <= M; ++a)
     for (int b = 0; b <= M; ++b)
       for (int c = 0; c < C; ++c) qout[(a * (M + 1) + b) * C + c] = q[SIDX(a, b)][c];
@@ -691,7 +735,7 @@ static int gauss_rule(int M, real *s, real *w)
 
 static int grp_interface(int system, real lambda, real gamma, int M, real dt,
                          const real *trL, const real *trR, real rtol, int max_iter, int guess_kind,
-                         real *flux, real *gnew, int *iters, int *truncated)
+                         real *flux, real *gnew, int *iters, int *truncated, const srcspec *S)
 {
   int C = system == OR_EULER ? 3 : 1;
   real q[(MAXM + 1) * (MAXM + 1)][MAXC];
@@ -721,7 +765,7 @@ static int grp_interface(int system, real lambda, real gamma, int M, real dt,
       for (int c = 0; c < 3; ++c) q[SIDX(k, 0)][c] = D[c] / fact;
     }
   }
-  ck_series(system, lambda, gamma, M, q);
+  ck_series(system, lambda, gamma, M, q, S);
 
   real s[3], w[3], Qt[MAXC][4];
   int G = gauss_rule(M, s, w);
@@ -797,7 +841,7 @@ int or_grp_interface(int system, double lambda, double gamma, int M, double dt,
   real tl[(MAXM + 1) * MAXC], tr[(MAXM + 1) * MAXC], f[MAXC], g[MAXC];
   for (int i = 0; i < (M + 1) * C; ++i) { tl[i] = trL[i]; tr[i] = trR[i]; }
   int st = grp_interface(system, lambda, gamma, M, dt, tl, tr, rtol, max_iter, guess_kind, f, g,
-                         iters, truncated);
+                         iters, truncated, 0);
   for (int c = 0; c < C; ++c) { flux[c] = f[c]; gnew[c] = g[c]; }
   return st;
 }
@@ -997,6 +1041,7 @@ typedef struct {
   real rtol; int max_iter; int guess_kind; int dt_hold;
   int recon;                  /* OR_RECON_GRPREC or OR_RECON_GRPRECNL */
   int solver;                 /* OR_SOLVER_TT or OR_SOLVER_DET */
+  srcspec src;                /* source term S(Q) (Section 2), kind OR_SOURCE_* */
 } params;
 
 /* Time-step rule (Section 4.1): dt = C dx / S_max, S_max over the cell averages.
@@ -1064,8 +1109,54 @@ static int first_order_interface(const params *P, int N, int bc, int j, const re
 }
 
 /*
- * Conservative update, eq. eq_finite_volume with S = 0 (Section 2), from the
- * fluxes flux[j * C + c] of the nif interfaces, into cand[c * N + i], with
+ * Numerical source of cell i, eq. eq:source: the space-time average of S(Q)
+ * over the cell and [t^n, t^n + dt] (Section 2: "a similar but simpler
+ * approach" than the flux).  READING: Q(x, tau) is the cell's own evolution,
+ * the Cauchy-Kovalevskaya series (with the source) at the cell centre from
+ * the Taylor coefficients of its reconstruction polynomial (no Riemann
+ * problem inside a cell), integrated by the G-point Gauss-Legendre rule in
+ * space and in time (exact: the series has total degree M and S is linear).
+ * A centre state that is not admissible (Euler) is replaced by the cell
+ * average, held constant before the evolution.  coef: monomial coefficients in
+ * xi = (x - x_i)/dx; avg: the cell average.  out[C].
+ */
+static void cell_source(const params *P, real dx, real dt, const real *coef, const real *avg, real *out)
+{
+  const int M = P->M, C = P->system == OR_EULER ? 3 : 1;
+  real q[(MAXM + 1) * (MAXM + 1)][MAXC];
+  for (int i = 0; i < (MAXM + 1) * (MAXM + 1); ++i) q[i][0] = q[i][1] = q[i][2] = 0;
+  real scale = 1;
+  for (int a = 0; a <= M; ++a) {
+    for (int c = 0; c < C; ++c) q[SIDX(a, 0)][c] = coef[c * (MAXM + 1) + a] / scale;
+    scale = scale * dx;
+  }
+  if (P->system == OR_EULER && !euler_admissible(P->gamma, q[SIDX(0, 0)])) {
+    for (int a = 0; a <= M; ++a)
+      for (int c = 0; c < 3; ++c) q[SIDX(a, 0)][c] = a == 0 ? avg[c] : (real)0;
+  }
+  ck_series(P->system, P->lambda, P->gamma, M, q, &P->src);
+  real s[3], w[3];
+  const int G = gauss_rule(M, s, w);
+  for (int c = 0; c < 3; ++c) out[c] = 0;
+  for (int al = 0; al < G; ++al)
+    for (int be = 0; be < G; ++be) {
+      const real x = 0.5 * dx * s[al], tau = 0.5 * dt * (1 + s[be]);
+      real Q[3] = { 0, 0, 0 }, S[3];
+      for (int c = 0; c < C; ++c)
+        for (int a = M; a >= 0; --a) {          /* Horner in x over the tau-polynomials of each power */
+          real v = 0;
+          for (int b = M - a; b >= 0; --b) v = v * tau + q[SIDX(a, b)][c];
+          Q[c] = Q[c] * x + v;
+        }
+      source_apply(&P->src, Q, S);
+      for (int c = 0; c < C; ++c) out[c] = out[c] + w[al] * w[be] * S[c];
+    }
+}
+
+/*
+ * Conservative update, eq. eq_finite_volume (Section 2), from the fluxes
+ * flux[j * C + c] of the nif interfaces and the numerical sources
+ * src[i * C + c] of the cells (NULL: S = 0), into cand[c * N + i], with
  * the a-posteriori repair (READING, MOOD-like; not in the paper): a candidate
  * average that is inadmissible, or whose density or pressure leaves the range
  * of the old averages of cells i-1, i, i+1 by more than OR_DMP_REL of the
@@ -1078,7 +1169,7 @@ static int first_order_interface(const params *P, int N, int bc, int j, const re
  * OR_NONPHYSICAL (the candidates are kept: the domain freezes on them).
  */
 static int update_repair(const params *P, int N, int bc, real dx, real dt, const real *avg, long cstride,
-                         real *flux, real *gnew, char *low, real *cand, long long *st)
+                         real *flux, real *gnew, char *low, real *cand, const real *src, long long *st)
 {
   const int C = P->system == OR_EULER ? 3 : 1;
   int status = OR_OK;
@@ -1087,7 +1178,9 @@ static int update_repair(const params *P, int N, int bc, real dx, real dt, const
     for (int i = 0; i < N; ++i) {
       int jl = i, jr = (bc == OR_BC_PERIODIC) ? (i + 1) % N : i + 1;
       for (int c = 0; c < C; ++c)
-        cand[c * N + i] = avg[c * cstride + i] - dt / dx * (flux[jr * C + c] - flux[jl * C + c]);
+        cand[c * N + i] = src ? avg[c * cstride + i] - dt / dx * (flux[jr * C + c] - flux[jl * C + c])
+                                    + dt * src[i * C + c]
+                              : avg[c * cstride + i] - dt / dx * (flux[jr * C + c] - flux[jl * C + c]);
     }
     if (P->system != OR_EULER) break;
     for (int i = 0; i < N && status == OR_OK; ++i) {
@@ -1267,7 +1360,7 @@ static int step_domain(const params *P, int N, int bc, real dx, real dt, real *a
     }
     int it = 0, tr = 0;
     int s = grp_interface(P->system, P->lambda, P->gamma, M, dt, trL, trR, P->rtol, P->max_iter,
-                          P->guess_kind, flux + j * C, gnew + j * C, &it, &tr);
+                          P->guess_kind, flux + j * C, gnew + j * C, &it, &tr, &P->src);
     if (P->system == OR_EULER) {
       st[OR_ST_RS_CALLS] += 1;
       st[OR_ST_NEWTON_SUM] += it;
@@ -1283,9 +1376,26 @@ static int step_domain(const params *P, int N, int bc, real dx, real dt, real *a
     if (s != OR_OK) status = s;
   }
 
+  /* numerical sources of the cells (eq. eq:source), from the reconstructions
+   * as used for the traces (degree-0 fallback included) */
+  real *src = 0;
+  if (status == OR_OK && P->src.kind != OR_SOURCE_NONE) {
+    src = (real *)malloc(sizeof(real) * N * C);
+    for (int i = 0; i < N; ++i) {
+      real cf[MAXC * (MAXM + 1)], av[MAXC], out[3];
+      for (int c = 0; c < C; ++c) {
+        for (int k = 0; k <= MAXM; ++k) cf[c * (MAXM + 1) + k] = coef[(i * C + c) * (MAXM + 1) + k];
+        av[c] = avg[c * cstride + i];
+      }
+      cell_source(P, dx, dt, cf, av, out);
+      for (int c = 0; c < C; ++c) src[i * C + c] = out[c];
+    }
+  }
+
   OR_PHASE(2);
   real *cand = (real *)malloc(sizeof(real) * N * C);
-  if (status == OR_OK) status = update_repair(P, N, bc, dx, dt, avg, cstride, flux, gnew, low, cand, st);
+  if (status == OR_OK) status = update_repair(P, N, bc, dx, dt, avg, cstride, flux, gnew, low, cand, src, st);
+  free(src);
   if (status == OR_OK || status == OR_NONPHYSICAL) {
     for (int i = 0; i < N; ++i)
       for (int c = 0; c < C; ++c) avg[c * cstride + i] = cand[c * N + i];
@@ -1325,8 +1435,25 @@ int or_run_solver(int system, double lambda, double gamma, int M, int recon, int
                   double *avg, double *iface, double *t, int *nstep, double *dt_prev, int *status,
                   int n_steps, double t_end, long long *stats, const double *dt_fixed, int n_threads)
 {
+  return or_run_full(system, lambda, gamma, M, recon, solver, OR_SOURCE_NONE, 0.0, cfl, n_domains, n_cells,
+                     x_left, x_right, bc, newton_rtol, newton_max_iter, guess_kind, dt_hold, avg, iface, t,
+                     nstep, dt_prev, status, n_steps, t_end, stats, dt_fixed, n_threads);
+}
+
+int or_run_full(int system, double lambda, double gamma, int M, int recon, int solver, int source,
+                double source_coef, double cfl, int n_domains, const int *n_cells, const double *x_left,
+                const double *x_right, const int *bc, double newton_rtol, int newton_max_iter, int guess_kind,
+                int dt_hold, double *avg, double *iface, double *t, int *nstep, double *dt_prev, int *status,
+                int n_steps, double t_end, long long *stats, const double *dt_fixed, int n_threads)
+{
   params P;
   P.solver = solver;
+  P.src.kind = source;
+  P.src.coef = source_coef;
+  if (source != OR_SOURCE_NONE && source != OR_SOURCE_LINEAR && source != OR_SOURCE_GRAVITY) return -1;
+  if (source == OR_SOURCE_LINEAR && system != OR_ADVECTION) return -1;
+  if (source == OR_SOURCE_GRAVITY && system != OR_EULER) return -1;
+  if (source != OR_SOURCE_NONE && solver != OR_SOLVER_TT) return -1;   /* the source enters the TT series */
   P.system = system; P.lambda = lambda; P.gamma = gamma; P.M = M; P.cfl = cfl;
   P.rtol = newton_rtol; P.max_iter = newton_max_iter; P.guess_kind = guess_kind;
   P.dt_hold = dt_hold < 1 ? 1 : dt_hold;
@@ -1407,7 +1534,7 @@ int or_update_repair(double gamma, int N, int bc, double dx, double dt, const do
   real *g = (real *)malloc(sizeof(real) * 3 * nif), *cd = (real *)malloc(sizeof(real) * 3 * N);
   for (int k = 0; k < 3 * N; ++k) a[k] = avg[k];
   for (int k = 0; k < 3 * nif; ++k) { f[k] = flux[k]; g[k] = gnew[k]; }
-  int st = update_repair(&P, N, bc, dx, dt, a, N, f, g, low, cd, stats);
+  int st = update_repair(&P, N, bc, dx, dt, a, N, f, g, low, cd, 0, stats);
   for (int k = 0; k < 3 * N; ++k) cand[k] = (double)cd[k];
   for (int k = 0; k < 3 * nif; ++k) { flux[k] = (double)f[k]; gnew[k] = (double)g[k]; }
   free(a); free(f); free(g); free(cd);

@@ -27,6 +27,8 @@ enum { OR_BC_PERIODIC = 0, OR_BC_TRANSMISSIVE = 1 };
 enum { OR_GUESS_PVRS = 0, OR_GUESS_TRRS = 1, OR_GUESS_GIVEN = 2 };
 enum { OR_RECON_GRPREC = 0, OR_RECON_GRPRECNL = 1 };
 enum { OR_SOLVER_TT = 0, OR_SOLVER_DET = 1 };
+/* source term S(Q) (Section 2): none; advection S(q) = k q; Euler S = (0, -g rho, -g m) */
+enum { OR_SOURCE_NONE = 0, OR_SOURCE_LINEAR = 1, OR_SOURCE_GRAVITY = 2 };
 enum {
   OR_OK = 0,
   OR_NEWTON_NO_CONV = 1,
@@ -114,6 +116,21 @@ int or_run_solver(int system, double lambda, double gamma, int M, int recon, int
                   const int *bc, double newton_rtol, int newton_max_iter, int guess_kind, int dt_hold,
                   double *avg, double *iface, double *t, int *nstep, double *dt_prev, int *status,
                   int n_steps, double t_end, long long *stats, const double *dt_fixed, int n_threads);
+
+/* or_run_solver with a source term (eq. eq_finite_volume with S, Section 2):
+ * source = OR_SOURCE_LINEAR (advection, S = source_coef q) or
+ * OR_SOURCE_GRAVITY (Euler, S = (0, -g rho, -g m), g = source_coef), with the
+ * Toro-Titarev solver only.  Returns -1 for a combination it does not take. */
+int or_run_full(int system, double lambda, double gamma, int M, int recon, int solver, int source,
+                double source_coef, double cfl, int n_domains, const int *n_cells, const double *x_left,
+                const double *x_right, const int *bc, double newton_rtol, int newton_max_iter, int guess_kind,
+                int dt_hold, double *avg, double *iface, double *t, int *nstep, double *dt_prev, int *status,
+                int n_steps, double t_end, long long *stats, const double *dt_fixed, int n_threads);
+
+/* The Cauchy-Kovalevskaya series with a source term: qa0[a][c] = q_{a,0};
+ * qout[a][b][c] (M+1 x M+1 x C) for a + b <= M. */
+void or_ck_series_src(int system, double lambda, double gamma, int M, int source, double coef,
+                      const double *qa0, double *qout);
 
 #ifdef __cplusplus
 }

@@ -34,6 +34,7 @@ struct grp_ctx {
   double* pold = nullptr;        // pressure of the current averages (S_max pass)
   DomStep* ds = nullptr;         // per-domain time step of the current step
   double* det_ed = nullptr;      // DET: evolved edge values of every cell
+  double* srcv = nullptr;        // numerical source of every cell (source terms only)
   unsigned char *low = nullptr, *troubled = nullptr;
   double *t = nullptr, *dt_prev = nullptr;
   int *nstep = nullptr, *status = nullptr;
@@ -114,7 +115,7 @@ void free_all(grp_ctx* c)
   c->ev_free.clear();
   c->ev_pending.clear();
   void* ptrs[] = {c->cell_off, c->if_off, c->cell_dom, c->if_dom, c->dx, c->bc, c->avg[0], c->avg[1],
-                  c->ifc[0], c->ifc[1], c->flux, c->pold, c->ds, c->det_ed, c->low, c->troubled, c->t, c->dt_prev, c->nstep,
+                  c->ifc[0], c->ifc[1], c->flux, c->pold, c->ds, c->det_ed, c->srcv, c->low, c->troubled, c->t, c->dt_prev, c->nstep,
                   c->status, c->smax_bits, c->bad, c->inad, c->fail, c->any_bad, c->tlist0, c->tlist1,
                   c->ilist, c->lcount, c->stats,
                   c->scratch_norm, c->mlp, c->mlp_norm, c->grp};
@@ -172,6 +173,9 @@ StepArgs make_args(const grp_ctx* c, double t_end)
   a.harvest_count = c->harvest_count;
   a.harvest_cap = c->harvest_cap;
   a.harvest_log2_stride = c->harvest_log2_stride;
+  a.srcv = c->srcv;
+  a.ph.src = c->p.source;
+  a.ph.src_k = c->p.source_coef;
   return a;
 }
 
@@ -215,6 +219,7 @@ cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s)
 int launch_form(const grp_ctx* c)
 {
   if (c->p.solver == GRP_SOLVER_DET) return GRP_LAUNCH_FLAT;     // DET has the flat form only
+  if (c->p.source != GRP_SOURCE_NONE) return GRP_LAUNCH_FLAT;     // so do source terms
   if (c->mode != GRP_LAUNCH_AUTO) return c->mode;
   // auto: whole domains per block pay off when the batch has many short domains
   return c->D >= 1024 && c->max_cells <= 4096 ? GRP_LAUNCH_SPLIT : GRP_LAUNCH_FLAT;
@@ -328,7 +333,7 @@ int enqueue_step(grp_ctx* c, double t_end)
     CK(launch_det_step(a, c->det_ed, s));            // predictor (two phases), then the interface Riemann problems
     c->launches += 3;
   } else {
-    CK(launch_flux(a, s));
+    CK(c->p.source != GRP_SOURCE_NONE ? launch_flux_src(a, s) : launch_flux(a, s));
     c->launches++;
   }
   if (c->timing) {
@@ -408,6 +413,14 @@ int grp_create(grp_ctx** out, const grp_problem* p)
   if (p->dt_hold < 1) return GRP_E_INVALID_ARG;
   if (p->recon != GRP_RECON_GRPREC && p->recon != GRP_RECON_GRPRECNL) return GRP_E_INVALID_ARG;
   if (p->solver != GRP_SOLVER_TT && p->solver != GRP_SOLVER_DET) return GRP_E_INVALID_ARG;
+  if (p->source != GRP_SOURCE_NONE) {
+    // a source term: S = k q for advection, the constant acceleration for the
+    // Euler equations; it enters the Toro-Titarev series, with linear GRPrec
+    const bool kind_ok = (p->source == GRP_SOURCE_LINEAR && p->system == GRP_ADVECTION) ||
+                         (p->source == GRP_SOURCE_GRAVITY && p->system == GRP_EULER_IDEAL);
+    if (!kind_ok || !isfinite(p->source_coef) || p->solver != GRP_SOLVER_TT || p->recon != GRP_RECON_GRPREC)
+      return GRP_E_INVALID_ARG;
+  }
   grp_ctx* c = new grp_ctx();
   c->p = *p;
   c->p.n_cells = nullptr; c->p.x_left = nullptr; c->p.x_right = nullptr; c->p.bc = nullptr;
@@ -452,6 +465,7 @@ int grp_create(grp_ctx** out, const grp_problem* p)
   AL(status, D) AL(smax_bits, D) AL(bad, (MAX_REPAIR + 1) * D) AL(inad, D) AL(fail, D)
   AL(any_bad, MAX_REPAIR + 1) AL(stats, (long long)NSTATS * D) AL(scratch_norm, 3 * D)
   AL(tlist0, c->ncell) AL(tlist1, c->ncell) AL(ilist, c->nif) AL(lcount, 2 * (MAX_REPAIR + 1))
+  if (p->source != GRP_SOURCE_NONE) AL(srcv, (long long)C * c->ncell)
   if (p->solver == GRP_SOLVER_DET) {
     AL(det_ed, (long long)det_doubles(p->M, C, c->ncell))
     if (det_prepare(p->device) != 0) { free_all(c); delete c; return cuda_fail(cudaErrorUnknown, "DET tables"); }

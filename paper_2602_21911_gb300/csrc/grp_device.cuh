@@ -35,6 +35,10 @@ struct Phys {
   const float* mlp_w;
   const float* mlp_box;
   int features;          // compute the network features (learned guess or harvest)
+  // source term S(Q) of the balance law (Section 2): 0 none; 1 S = src_k q
+  // (advection); 2 S = (0, -src_k rho, -src_k m) (Euler, acceleration -src_k)
+  int src;
+  double src_k;
 };
 
 inline Phys make_phys(double lambda, double gamma, double rtol, int max_iter, int guess)
@@ -55,6 +59,8 @@ inline Phys make_phys(double lambda, double gamma, double rtol, int max_iter, in
   p.mlp_w = nullptr;
   p.mlp_box = nullptr;
   p.features = 0;
+  p.src = 0;
+  p.src_k = 0.0;
   return p;
 }
 
@@ -280,14 +286,27 @@ GRP_HD __forceinline__ void to_cons(const Phys& ph, Prim w, double Q[3])
   Q[2] = w.p * ph.i_gm1 + 0.5 * w.r * w.u * w.u;
 }
 
-// rho > 0 and p = (g-1)(E - m^2/(2 rho)) > 0, written without a division.
-// On the GPU rho > 0 is a signed-integer test of the bits (off the FP64 pipe:
-// true for positive values; a NaN rho passes it but fails the second test).
+// x > 0 for a double x, exactly (+inf included, NaN excluded).  On the GPU a
+// signed-integer test of the bits, off the FP64 pipe: positive doubles order
+// as their bit patterns, and negative values have negative patterns.
+GRP_HD __forceinline__ bool positive(double x)
+{
+#ifdef __CUDA_ARCH__
+  const long long b = __double_as_longlong(x);
+  return b > 0ll && b <= 0x7ff0000000000000ll;
+#else
+  return x > 0.0;
+#endif
+}
+
+// rho > 0 and p = (g-1)(E - m^2/(2 rho)) > 0, written without a division:
+// rho > 0 and 2 E rho - m^2 > 0 (one fused multiply-add; its sign is that of
+// the exact 2 E rho - fl(m^2)), both sign tests on the integer pipe.
 GRP_HD __forceinline__ bool admissible(double g, double r, double m, double E)
 {
   (void)g;
 #ifdef __CUDA_ARCH__
-  return __double_as_longlong(r) > 0ll && 2.0 * E * r > m * m;
+  return positive(r) && positive(fma(E + E, r, -(m * m)));
 #else
   return r > 0.0 && 2.0 * E * r > m * m;
 #endif
@@ -770,12 +789,30 @@ GRP_HD __forceinline__ void char_back(const Eig& e, const double w[3], double D[
   D[2] = (e.H - e.u * e.c) * w[0] + 0.5 * e.u * e.u * w[1] + (e.H + e.u * e.c) * w[2];
 }
 
+// Upwind weight theta of a field of speed lam in a derivative Riemann problem:
+// 0 when lam > tie (left data), 1 when lam < -tie (right data), 1/2 between (a
+// sonic field averages the two sides); tie >= 0.  On the GPU both tests are
+// integer compares of the bit patterns (exact for non-NaN values: -lam > tie
+// with the sign bit flipped), off the FP64 pipe.
+GRP_HD __forceinline__ double upwind_weight(double lam, double tie)
+{
+#ifdef __CUDA_ARCH__
+  const long long b = __double_as_longlong(lam), t = __double_as_longlong(tie);
+  if (b > t) return 0.0;
+  if ((b ^ (long long)0x8000000000000000ull) > t) return 1.0;
+  return 0.5;
+#else
+  return lam > tie ? 0.0 : (lam < -tie ? 1.0 : 0.5);
+#endif
+}
+
 // All M derivative Riemann problems of one interface at once:
 // D_k = DL_k - sum_j theta_j (l_j . J_k) r_j with J_k = DL_k - DR_k.  theta_j
 // depends on the field only, so a field that takes right data (theta_j != 0)
-// is applied to every order k in one branch; in smooth subsonic flow that is
-// one field of the three.  t[c][k]: Taylor coefficients of the traces;
-// D[k][c] for k = 1..M.
+// is applied to every order k in one branch, and its left eigenvector l_j
+// (row of R^{-1}) and right eigenvector r_j = (1, r1, r2) are formed only
+// there; in smooth subsonic flow that is one field of the three.
+// t[c][k]: Taylor coefficients of the traces; D[k][c] for k = 1..M.
 template <int M>
 GRP_HD __forceinline__ void deriv_rps(const Eig& e, const double tL[][M + 1], const double tR[][M + 1],
                                       double D[M + 1][3])
@@ -788,22 +825,27 @@ GRP_HD __forceinline__ void deriv_rps(const Eig& e, const double tL[][M + 1], co
       J[k][c] = tL[c][k] - tR[c][k];
       D[k][c] = tL[c][k];
     }
-  const double uc = e.u * e.ic, bu = e.b1 * e.u, uc2 = e.u * e.c;
-  // rows of R^{-1} (left eigenvectors) and the right eigenvectors (1, r1, r2)
-  const double Lr[3][3] = {{0.5 * (e.b2 + uc), -0.5 * (bu + e.ic), 0.5 * e.b1},
-                           {1.0 - e.b2, bu, -e.b1},
-                           {0.5 * (e.b2 - uc), -0.5 * (bu - e.ic), 0.5 * e.b1}};
-  const double Rr[3][2] = {{e.u - e.c, e.H - uc2}, {e.u, 0.5 * e.u * e.u}, {e.u + e.c, e.H + uc2}};
+  const double bu = e.b1 * e.u;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    const double th = e.lam[j] > e.tie ? 0.0 : (e.lam[j] < -e.tie ? 1.0 : 0.5);
+    const double th = upwind_weight(e.lam[j], e.tie);
     if (th != 0.0) {
+      double l0, l1, l2, r1, r2;
+      if (j == 1) {
+        l0 = 1.0 - e.b2; l1 = bu; l2 = -e.b1;
+        r1 = e.u; r2 = 0.5 * e.u * e.u;
+      } else {
+        const double sg = j == 0 ? 1.0 : -1.0;          // field u - c (j = 0) or u + c (j = 2)
+        const double uc = e.u * e.ic;
+        l0 = 0.5 * (e.b2 + sg * uc); l1 = -0.5 * (bu + sg * e.ic); l2 = 0.5 * e.b1;
+        r1 = e.lam[j]; r2 = e.H - sg * (e.u * e.c);
+      }
 #pragma unroll
       for (int k = 1; k <= M; ++k) {
-        const double w = th * (Lr[j][0] * J[k][0] + Lr[j][1] * J[k][1] + Lr[j][2] * J[k][2]);
+        const double w = th * (l0 * J[k][0] + l1 * J[k][1] + l2 * J[k][2]);
         D[k][0] -= w;
-        D[k][1] -= w * Rr[j][0];
-        D[k][2] -= w * Rr[j][1];
+        D[k][1] -= w * r1;
+        D[k][2] -= w * r2;
       }
     }
   }
@@ -824,9 +866,13 @@ struct Tri {
 // In: q0[c][idx(a,0)] filled for a = 0..M (others ignored).  Out: s[c][b] = q[0][b].
 // irho, u0, p0: 1/rho, velocity and pressure of the leading state (known to
 // the caller), the series' constant terms.
-template <int M>
+// SRC: with the constant-acceleration source S = (0, -g rho, -g m), in scaled
+// variables d_T Q + d_X F = dx S: q[a][b+1] gets hs/(b+1) (0, rho[a][b],
+// m[a][b]) added, hs = -g dx.
+template <int M, bool SRC = false>
 GRP_HD __forceinline__ void ck_euler(double g, double rho[Tri<M>::N], double m[Tri<M>::N],
-                                         double E[Tri<M>::N], double s[3][M + 1], double irho, double u0, double p0)
+                                         double E[Tri<M>::N], double s[3][M + 1], double irho, double u0, double p0,
+                                         double hs = 0.0)
 {
   using T = Tri<M>;
   double u[T::N], mu[T::N], Ep[T::N], F1[T::N], F2[T::N];
@@ -867,10 +913,16 @@ GRP_HD __forceinline__ void ck_euler(double g, double rho[Tri<M>::N], double m[T
 #pragma unroll
     for (int a = 0; a + b + 1 <= M; ++a) {
       const double f = -double(a + 1) / double(b + 1);
-      const int src = T::idx(a + 1, b), dst = T::idx(a, b + 1);
+      const int src = T::idx(a + 1, b), dst = T::idx(a, b + 1), here = T::idx(a, b);
       rho[dst] = f * m[src];
-      m[dst] = f * F1[src];
-      E[dst] = f * F2[src];
+      if (SRC) {
+        const double h = hs / double(b + 1);
+        m[dst] = fma(h, rho[here], f * F1[src]);
+        E[dst] = fma(h, m[here], f * F2[src]);
+      } else {
+        m[dst] = f * F1[src];
+        E[dst] = f * F2[src];
+      }
     }
   }
 #pragma unroll
@@ -930,17 +982,40 @@ GRP_HD __forceinline__ bool equal_data(const double QL[3], const double QR[3])
 // reconstructions at the interface, nu = dt/dx.  The interface datum for the
 // next step is the series at tau = dt.
 // ---------------------------------------------------------------------------
+// Advection with the source S = k q (SRC), scaled: d_T q + lam d_X q = hk q
+// with hk = k dx, so q[a][b+1] = (-lam (a+1) q[a+1][b] + hk q[a][b]) / (b+1).
 template <int M>
+GRP_HD __forceinline__ void ck_adv_src(double lam, double hk, double q[Tri<M>::N])
+{
+  using T = Tri<M>;
+#pragma unroll
+  for (int b = 0; b < M; ++b)
+#pragma unroll
+    for (int a = 0; a + b + 1 <= M; ++a)
+      q[T::idx(a, b + 1)] = (-lam * double(a + 1) * q[T::idx(a + 1, b)] + hk * q[T::idx(a, b)]) / double(b + 1);
+}
+
+template <int M, bool SRC = false>
 GRP_HD __forceinline__ void grp_adv(double lam, double nu, const double tL[M + 1], const double tR[M + 1],
-                                    double& F, double& gnew)
+                                    double& F, double& gnew, double hk = 0.0)
 {
   double s[M + 1];
 #pragma unroll
   for (int k = 0; k <= M; ++k) s[k] = lam > 0.0 ? tL[k] : (lam < 0.0 ? tR[k] : 0.5 * (tL[k] + tR[k]));
-  // CK for q_t + lam q_x = 0: q[0][b] = (-lam)^b q[b][0]
-  double sc = 1.0;
+  if (SRC) {
+    using T = Tri<M>;
+    double q[T::N];
 #pragma unroll
-  for (int k = 0; k <= M; ++k) { s[k] *= sc; sc *= -lam; }
+    for (int k = 0; k <= M; ++k) q[T::idx(k, 0)] = s[k];
+    ck_adv_src<M>(lam, hk, q);
+#pragma unroll
+    for (int b = 0; b <= M; ++b) s[b] = q[T::idx(0, b)];
+  } else {
+    // CK for q_t + lam q_x = 0: q[0][b] = (-lam)^b q[b][0]
+    double sc = 1.0;
+#pragma unroll
+    for (int k = 0; k <= M; ++k) { s[k] *= sc; sc *= -lam; }
+  }
   double acc = 0.0;
 #pragma unroll
   for (int al = 0; al < Gauss<M>::G; ++al) {
@@ -961,10 +1036,10 @@ GRP_HD __forceinline__ void grp_adv(double lam, double nu, const double tL[M + 1
 // then takes the first-order flux).  truncated: a state of the series at a
 // Gauss node or at dt was inadmissible, so the series was cut to its
 // leading term.
-template <int M, bool G75>
+template <int M, bool G75, bool SRC = false>
 GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[3][M + 1],
                                      const double tR[3][M + 1], double F[3], double gnew[3], int& iters,
-                                     bool& truncated, RSInfo* info = nullptr)
+                                     bool& truncated, RSInfo* info = nullptr, double hs = 0.0)
 {
   const double g = ph.gamma;
   const double QL[3] = {tL[0][0], tL[1][0], tL[2][0]}, QR[3] = {tR[0][0], tR[1][0], tR[2][0]};
@@ -1000,7 +1075,7 @@ GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[
     }
   }
   double s[3][M + 1];
-  ck_euler<M>(g, rho, m, E, s, ir0, W0.u, W0.p);
+  ck_euler<M, SRC>(g, rho, m, E, s, ir0, W0.u, W0.p, hs);
   // states at the Gauss nodes and at tau = dt; at a node one reciprocal
   // serves both the admissibility test and the flux, at dt (no flux) the
   // test is division-free
@@ -1017,10 +1092,13 @@ GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[
       for (int k = M - 1; k >= 0; --k) v = v * Tn + s[c][k];
       Qg[al][c] = v;
     }
+  }
+#pragma unroll
+  for (int al = 0; al <= G; ++al) {
     if (al < G) {
       ug[al] = Qg[al][1] * rcp64(Qg[al][0]);        // a non-positive density fails the test below
       pg[al] = (g - 1.0) * (Qg[al][2] - 0.5 * Qg[al][1] * ug[al]);
-      ok = ok && Qg[al][0] > 0.0 && pg[al] > 0.0;
+      ok = ok && positive(Qg[al][0]) && positive(pg[al]);
     } else {
       ok = ok && admissible(g, Qg[al][0], Qg[al][1], Qg[al][2]);
     }
@@ -1043,6 +1121,82 @@ GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[
   }
   gnew[0] = Qg[G][0]; gnew[1] = Qg[G][1]; gnew[2] = Qg[G][2];
   return ST_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Numerical source of a cell (eq. eq:source, Section 2): the space-time
+// average of S(Q) over the cell and [0, dt], with Q the cell's own evolution,
+// the Cauchy-Kovalevskaya series with the source at the cell centre from its
+// reconstruction.  S is linear here, so the average of S(Q) is S of the
+// average of the series, taken exactly from its moments: over xi in
+// [-1/2, 1/2] the average of xi^a is 2^-a / (a+1) for even a (0 for odd),
+// over T in [0, nu] that of T^b is nu^b / (b+1).  b: the zero-mean-basis
+// coefficients of the reconstruction (degree 0 after a fallback).
+// ---------------------------------------------------------------------------
+template <int M>
+GRP_HD __forceinline__ void centre_taylor(const double b[5], double t[M + 1])
+{
+  t[0] = b[0] - b[2] * (1.0 / 12.0) - b[4] * (1.0 / 80.0);
+#pragma unroll
+  for (int k = 1; k <= M; ++k) t[k] = b[k];
+}
+
+template <int M>
+GRP_HD __forceinline__ double series_average(const double q[Tri<M>::N], double nu)
+{
+  using T = Tri<M>;
+  double acc = 0.0;
+#pragma unroll
+  for (int a = 0; a <= M; a += 2) {
+    const double mx = a == 0 ? 1.0 : (a == 2 ? 1.0 / 12.0 : 1.0 / 80.0);
+    double v = q[T::idx(a, M - a)] * (1.0 / double(M - a + 1));
+#pragma unroll
+    for (int b = M - a - 1; b >= 0; --b) v = fma(v, nu, q[T::idx(a, b)] * (1.0 / double(b + 1)));
+    acc = fma(mx, v, acc);
+  }
+  return acc;
+}
+
+// advection, S = k q: returns S_i
+template <int M>
+GRP_HD __forceinline__ double cell_source_adv(const double b[5], double lam, double nu, double k, double dx)
+{
+  using T = Tri<M>;
+  double t[M + 1], q[T::N];
+  centre_taylor<M>(b, t);
+#pragma unroll
+  for (int a = 0; a <= M; ++a) q[T::idx(a, 0)] = t[a];
+  ck_adv_src<M>(lam, k * dx, q);
+  return k * series_average<M>(q, nu);
+}
+
+// Euler, S = (0, -g rho, -g m).  A centre state that is not admissible is
+// replaced by the cell average, held constant before the evolution.
+template <int M>
+GRP_HD __forceinline__ void cell_source_euler(const Phys& ph, const double b[3][5], double nu, double dx,
+                                              double S[3])
+{
+  using T = Tri<M>;
+  double t[3][M + 1];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) centre_taylor<M>(b[c], t[c]);
+  if (!admissible(ph.gamma, t[0][0], t[1][0], t[2][0])) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      t[c][0] = b[c][0];
+#pragma unroll
+      for (int k = 1; k <= M; ++k) t[c][k] = 0.0;
+    }
+  }
+  double rho[T::N], m[T::N], E[T::N], s[3][M + 1];
+#pragma unroll
+  for (int a = 0; a <= M; ++a) { rho[T::idx(a, 0)] = t[0][a]; m[T::idx(a, 0)] = t[1][a]; E[T::idx(a, 0)] = t[2][a]; }
+  const double ir = 1.0 / rho[0];
+  const double u0 = m[0] * ir, p0 = ph.gm1 * (E[0] - 0.5 * m[0] * u0);
+  ck_euler<M, true>(ph.gamma, rho, m, E, s, ir, u0, p0, -ph.src_k * dx);
+  S[0] = 0.0;
+  S[1] = -ph.src_k * series_average<M>(rho, nu);
+  S[2] = -ph.src_k * series_average<M>(m, nu);
 }
 
 }  // namespace grp

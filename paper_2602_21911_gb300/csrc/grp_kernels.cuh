@@ -47,6 +47,7 @@ struct StepArgs {
   const double* ifc;                 // current interface data [C][nif]
   double* ifc_new;                   // next interface data    [C][nif]
   double* flux;                      // scratch [C][nif]
+  double* srcv = nullptr;            // [C][ncell] numerical source of every cell this step, or null (S = 0)
   double* pold;                      // [ncell] pressure of the current averages, written with S_max
   DomStep* ds;                       // [D] this step's time step of every domain (k_dt or in-block)
   unsigned char* low;                // [nif] 0 high order; 1 first order (flux kernel); 2+r repaired in round r
@@ -436,21 +437,23 @@ __device__ __forceinline__ void harvest_record(const StepArgs& a, long long gj, 
 // The GRP at interface gj of an active domain d from the Taylor coefficients
 // of the two one-sided reconstructions (tL: left cell at its right edge, tR:
 // right cell at its left edge): flux, new interface datum, statistics.
-template <int SYS, int M, bool G75>
+// SRC: the GRP with the source term (eq. eq:GRP): its series carries dx S.
+template <int SYS, int M, bool G75, bool SRC = false>
 __device__ __forceinline__ void grp_at(const StepArgs& a, long long gj, int d, long long c0, int N, int bc, int j,
                                        const double tL[][M + 1], const double tR[][M + 1], unsigned st[8])
 {
   constexpr int C = SYS == SYS_EULER ? 3 : 1;
   a.low[gj] = 0;
   const double nu = a.ds[d].nu;
+  const double hsrc = SRC ? (SYS == SYS_ADV ? a.ph.src_k : -a.ph.src_k) * a.dx[d] : 0.0;
   double F[3] = {0.0, 0.0, 0.0}, gnew[3] = {0.0, 0.0, 0.0};
   if (SYS == SYS_ADV) {
-    grp_adv<M>(a.ph.lambda, nu, tL[0], tR[0], F[0], gnew[0]);
+    grp_adv<M, SRC>(a.ph.lambda, nu, tL[0], tR[0], F[0], gnew[0], hsrc);
   } else {
     int iters = 0;
     bool trunc = false;
     RSInfo info;
-    int rs_st = grp_euler<M, G75>(a.ph, nu, tL, tR, F, gnew, iters, trunc, &info);
+    int rs_st = grp_euler<M, G75, SRC>(a.ph, nu, tL, tR, F, gnew, iters, trunc, &info, hsrc);
     st[2] = 1;
     st[3] = trunc ? 1u : 0u;
     st[6] = info.guess == 1 ? 1u : 0u;
@@ -476,43 +479,6 @@ __device__ __forceinline__ void grp_at(const StepArgs& a, long long gj, int d, l
   }
 }
 
-// One interface, both neighbour cells reconstructed here (the block-local
-// batched kernel's form).
-template <int SYS, int M, bool G75, bool NL>
-__device__ __forceinline__ void flux_one(const StepArgs& a, long long gj, int d, unsigned st[8])
-{
-  const long long i0 = a.if_off[d], c0 = a.cell_off[d];
-  const int j = (int)(gj - i0);
-  const int N = (int)(a.cell_off[d + 1] - c0);
-  const int bc = a.bc[d];
-  constexpr int C = SYS == SYS_EULER ? 3 : 1;
-  if (!a.ds[d].active) {
-#pragma unroll
-    for (int c = 0; c < C; ++c) a.ifc_new[c * a.nif + gj] = a.ifc[c * a.nif + gj];
-    return;
-  }
-  // cells on both sides (transmissive ends: a ghost with the boundary average)
-  int cl, cr;
-  if (bc == 0) { cl = j == 0 ? N - 1 : j - 1; cr = j; }
-  else { cl = j - 1; cr = j == N ? -1 : j; }
-
-  double tL[C][M + 1], tR[C][M + 1], tx[C][M + 1];
-  if (cl >= 0) {
-    bool fb;
-    cell_edges<SYS, M, NL>(a, c0, i0, N, bc, cl, tx, tL, fb);
-    st[5] = fb ? 1u : 0u;                      // counted once per cell: at its right interface
-  } else {
-    ghost_edge<SYS, M>(a, c0, 0, tL);
-  }
-  if (cr >= 0) {
-    bool fb;
-    cell_edges<SYS, M, NL>(a, c0, i0, N, bc, cr, tR, tx, fb);
-  } else {
-    ghost_edge<SYS, M>(a, c0, N - 1, tR);
-  }
-  grp_at<SYS, M, G75>(a, gj, d, c0, N, bc, j, tL, tR, st);
-}
-
 // Warps overlap by one interface: warp w owns interfaces 31 w .. 31 w + 30.
 // Every lane reconstructs the left cell of its interface; the right cell of
 // an interface is the left cell of the next one, so its left-edge expansion
@@ -530,12 +496,47 @@ __host__ __device__ constexpr long long flux_threads(long long nif) { return (ni
 #ifndef GRP_FLUX_MIN_BLOCKS
 #define GRP_FLUX_MIN_BLOCKS 3
 #endif
-template <int SYS, int M, bool G75, bool NL>
-__global__ void __launch_bounds__(128, GRP_FLUX_MIN_BLOCKS) k_flux(StepArgs a)
+// The numerical source of cell `cell` (SRC kernels): its reconstruction
+// coefficients again (linear GRPrec; degree 0 when its traces were
+// inadmissible), then the source average of its own evolution.
+template <int SYS, int M>
+__device__ __forceinline__ void cell_source(const StepArgs& a, long long c0, long long i0, int N, int bc, int cell,
+                                            bool fb, int d)
+{
+  constexpr int C = SYS == SYS_EULER ? 3 : 1;
+  int im, ip;
+  nbr(cell, N, bc, im, ip);
+  const int jl = cell, jr = (bc == 0) ? (cell == N - 1 ? 0 : cell + 1) : cell + 1;
+  double b[3][5];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const double* A = a.avg + c * a.ncell + c0;
+    const double* G = a.ifc + c * a.nif + i0;
+    const double qm = (M >= 3) ? A[im] : 0.0, qp = (M >= 3) ? A[ip] : 0.0;
+    grprec_coeffs<M>(qm, A[cell], qp, G[jl], G[jr], b[c]);
+    if (fb) b[c][1] = b[c][2] = b[c][3] = b[c][4] = 0.0;
+  }
+  const double nu = a.ds[d].nu, dx = a.dx[d];
+  if (SYS == SYS_ADV) {
+    a.srcv[c0 + cell] = cell_source_adv<M>(b[0], a.ph.lambda, nu, a.ph.src_k, dx);
+  } else {
+    double S[3];
+    cell_source_euler<M>(a.ph, b, nu, dx, S);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.srcv[c * a.ncell + c0 + cell] = S[c];
+  }
+}
+
+// The flux phase of one warp: the interfaces gbase .. gbase + 30 (lanes
+// 0..30), lane 31 supplying the reconstruction of the cell left of
+// gbase + 31; interfaces at or beyond gend are not this call's.  All 32 lanes
+// of the warp call it (shuffles and warp statistics).
+template <int SYS, int M, bool G75, bool NL, bool SRC>
+__device__ __forceinline__ void flux_warp(const StepArgs& a, long long gbase, long long gend)
 {
   constexpr int C = SYS == SYS_EULER ? 3 : 1;
   const int lane = lane_id();
-  const long long gj = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 31 + lane;
+  const long long gj = gbase + lane;
   // st: newton sum, newton max, RS calls, truncated, first order, recon fallback,
   //     learned guess used, learned guess rejected
   unsigned st[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
@@ -547,7 +548,7 @@ __global__ void __launch_bounds__(128, GRP_FLUX_MIN_BLOCKS) k_flux(StepArgs a)
   for (int c = 0; c < C; ++c)
 #pragma unroll
     for (int k = 0; k <= M; ++k) em[c][k] = ep[c][k] = 0.0;
-  if (gj < a.nif) {
+  if (gj < gend) {
     d = a.if_dom[gj];
     i0 = a.if_off[d];
     c0 = a.cell_off[d];
@@ -557,6 +558,9 @@ __global__ void __launch_bounds__(128, GRP_FLUX_MIN_BLOCKS) k_flux(StepArgs a)
     active = a.ds[d].active != 0;
     cl = bc == 0 ? (j == 0 ? N - 1 : j - 1) : j - 1;
     if (active && cl >= 0) cell_edges<SYS, M, NL>(a, c0, i0, N, bc, cl, em, ep, fb);
+    // each cell is the left cell of exactly one interface (lane 31 supplies a
+    // reconstruction only; its interface is the next warp's lane 0)
+    if (SRC && active && cl >= 0 && lane < 31) cell_source<SYS, M>(a, c0, i0, N, bc, cl, fb, d);
   }
   // the next lane's left cell at its left edge: this interface's right trace
   double rm[C][M + 1];
@@ -564,7 +568,7 @@ __global__ void __launch_bounds__(128, GRP_FLUX_MIN_BLOCKS) k_flux(StepArgs a)
   for (int c = 0; c < C; ++c)
 #pragma unroll
     for (int k = 0; k <= M; ++k) rm[c][k] = __shfl_down_sync(0xffffffffu, em[c][k], 1);
-  if (lane < 31 && gj < a.nif) {
+  if (lane < 31 && gj < gend) {
     if (!active) {
 #pragma unroll
       for (int c = 0; c < C; ++c) a.ifc_new[c * a.nif + gj] = a.ifc[c * a.nif + gj];
@@ -599,7 +603,7 @@ __global__ void __launch_bounds__(128, GRP_FLUX_MIN_BLOCKS) k_flux(StepArgs a)
 #pragma unroll
         for (int k = 1; k <= M; ++k) tR[c][k] = ghost_r ? 0.0 : rm[c][k];
       }
-      grp_at<SYS, M, G75>(a, gj, d, c0, N, bc, j, tL, tR, st);
+      grp_at<SYS, M, G75, SRC>(a, gj, d, c0, N, bc, j, tL, tR, st);
     }
   } else {
     d = -1;
@@ -608,6 +612,12 @@ __global__ void __launch_bounds__(128, GRP_FLUX_MIN_BLOCKS) k_flux(StepArgs a)
   if (SYS == SYS_EULER) {
     warp_flux_stats(a.stats, d, st, a.ph.guess == 2);
   }
+}
+
+template <int SYS, int M, bool G75, bool NL, bool SRC = false>
+__global__ void __launch_bounds__(128, GRP_FLUX_MIN_BLOCKS) k_flux(StepArgs a)
+{
+  flux_warp<SYS, M, G75, NL, SRC>(a, (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 31, a.nif);
 }
 
 // ------------------------------------------------------------------ update
@@ -646,6 +656,7 @@ __device__ __forceinline__ int update_one(const StepArgs& a, long long gi, int d
 #pragma unroll
   for (int c = 0; c < C; ++c) {
     Q[c] = a.avg[c * a.ncell + gi] - r * (a.flux[c * a.nif + i0 + jr] - a.flux[c * a.nif + i0 + jl]);
+    if (a.srcv) Q[c] = fma(dt, a.srcv[c * a.ncell + gi], Q[c]);    // + dt S_i (eq. eq_finite_volume)
     a.avg_new[c * a.ncell + gi] = Q[c];
   }
   if (SYS != SYS_EULER) return 0;
@@ -905,19 +916,10 @@ __global__ void __launch_bounds__(256, 2) k_batch(StepArgs a, const int* __restr
     __syncthreads();
     for (int d = d0 + tid; d < d1; d += bt) compute_domain_step(w, d);
     __syncthreads();
-    for (long long base = ib; base < ie; base += bt) {
-      const long long gj = base + tid;
-      unsigned st[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-      int d = -1;
-      if (gj < ie) {
-        d = a.if_dom[gj];
-        flux_one<SYS, M, G75, NL>(w, gj, d, st);
-      }
-      __syncwarp();
-      if (SYS == SYS_EULER) {
-        warp_flux_stats(w.stats, d, st, w.ph.guess == 2);
-      }
-    }
+    // the flux kernel's warp form: warps overlapping by one interface, each
+    // cell reconstructed once per warp
+    for (long long base = ib + 31ll * (tid >> 5); base < ie; base += 31ll * (bt >> 5))
+      flux_warp<SYS, M, G75, NL, false>(w, base, ie);
     __syncthreads();
     for (long long gi = cb + tid; gi < ce; gi += bt)
       if (update_one<SYS>(w, gi, a.cell_dom[gi], -1) & 1) s_any[0] = 1;

@@ -37,6 +37,9 @@ cudaError_t launch_batch_euler_m2(const BatchLaunch& L, cudaStream_t s);
 cudaError_t launch_batch_euler_m3(const BatchLaunch& L, cudaStream_t s);
 cudaError_t launch_batch_euler_m4(const BatchLaunch& L, cudaStream_t s);
 cudaError_t launch_post_adv(const BatchLaunch& L, cudaStream_t s);
+// flux kernels with a source term (grp_flux_src.cu, grp_flux_src_m34.cu)
+cudaError_t launch_flux_src(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_flux_src_m34(const StepArgs& a, cudaStream_t s);
 
 // DET solver (grp_det.cu): constant tables of the device (once), the size of
 // the edge-value scratch, and the two launches of a step's GRP phase

@@ -31,7 +31,8 @@ class grp_problem(ctypes.Structure):
                 ("x_right", ctypes.POINTER(ctypes.c_double)), ("bc", ctypes.POINTER(ctypes.c_int)),
                 ("newton_rtol", ctypes.c_double), ("newton_max_iter", ctypes.c_int),
                 ("guess", ctypes.c_int), ("dt_hold", ctypes.c_int), ("device", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("recon", ctypes.c_int), ("solver", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("recon", ctypes.c_int), ("solver", ctypes.c_int),
+                ("source", ctypes.c_int), ("source_coef", ctypes.c_double)]
 
 
 class GrpError(RuntimeError):
@@ -100,6 +101,7 @@ def grp_probe_fp64_peak(device=0):
 GRP_NOALLOC_MAX_CELLS = 65536
 GRP_RECON_GRPREC, GRP_RECON_GRPRECNL = 0, 1
 GRP_SOLVER_TT, GRP_SOLVER_DET = 0, 1
+GRP_SOURCE_NONE, GRP_SOURCE_LINEAR, GRP_SOURCE_GRAVITY = 0, 1, 2
 GRP_MLP_NPARAM = 4673
 
 
@@ -252,6 +254,8 @@ class Solver:
         p.stream = stream
         p.recon = int(prob.get("recon", GRP_RECON_GRPREC))
         p.solver = int(prob.get("solver", GRP_SOLVER_TT))
+        p.source = int(prob.get("source", GRP_SOURCE_NONE))
+        p.source_coef = float(prob.get("source_coef", 0.0))
         self.prob = prob
         self.C = 3 if p.system == GRP_EULER_IDEAL else 1
         self.D = p.n_domains

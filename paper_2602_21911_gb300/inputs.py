@@ -196,6 +196,57 @@ def riemann_problem(N, WL, WR, M=2, cfl=0.9, xc=0.5, gamma=1.4, x0=0.0, x1=1.0):
 
 
 # --------------------------------------------------------------------------
+# Source terms (Section 2, S(Q) of the balance law).
+# --------------------------------------------------------------------------
+SOURCE_NONE, SOURCE_LINEAR, SOURCE_GRAVITY = 0, 1, 2
+
+
+def advection_sine_source(N, kappa, M=2, cfl=0.9):
+    """q_t + q_x = kappa q on periodic [0, 1], q0 = sin(2 pi x); the exact
+    solution is exp(kappa t) sin(2 pi (x - t))."""
+    prob, avg, lm, lp = advection_sine(N, M=M, cfl=cfl)
+    return dict(prob, source=SOURCE_LINEAR, source_coef=kappa), avg, lm, lp
+
+
+def advection_sine_source_exact(N, kappa, t):
+    return np.exp(kappa * t) * advection_sine_exact(N, t)
+
+
+def euler_uniform(N, M, rho=1.3, u=0.4, p=0.9, g=0.0, gamma=1.4, cfl=0.9):
+    """A uniform state on periodic [0, 1], under the constant acceleration -g
+    when g != 0 (exact solution: rho and p constant, u = u0 - g t)."""
+    e, dx = _edges(0.0, 1.0, N)
+    Q = _cons(np.float64(rho), np.float64(u), np.float64(p), gamma)
+    avg = np.repeat(Q[:, None], N, axis=1)
+    lim = np.repeat(Q[:, None], N, axis=1)
+    prob = _problem(EULER, M, cfl, [N], [0.0], [1.0], [PERIODIC], gamma=gamma)
+    if g != 0.0:
+        prob = dict(prob, source=SOURCE_GRAVITY, source_coef=g)
+    return prob, avg, lim, lim.copy()
+
+
+def hydrostatic_polytrope(N, M, g=1.0, K=1.0, rho0=2.0, cfl=0.9, bc=TRANSMISSIVE):
+    """Gas at rest in equilibrium with the constant acceleration -g on [0, 1]
+    for gamma = 2 and p = K rho^2: dp/dx = -g rho gives the linear density
+    rho = rho0 - g x / (2 K), and E = p / (gamma - 1) = K rho^2 is quadratic:
+    a steady state of polynomial degree 2 (exact averages, point values at
+    the interfaces)."""
+    gamma = 2.0
+    e, dx = _edges(0.0, 1.0, N)
+    slope = -g / (2.0 * K)
+    xc = 0.5 * (e[:-1] + e[1:])
+    rho_avg = rho0 + slope * xc
+    E_avg = K * (rho_avg ** 2 + (slope * dx) ** 2 / 12.0)      # average of K rho^2 over a cell
+    avg = np.stack([rho_avg, np.zeros(N), E_avg])
+    xi = e if bc == TRANSMISSIVE else e[:-1]
+    rho_i = rho0 + slope * xi
+    lim = np.stack([rho_i, np.zeros_like(rho_i), K * rho_i ** 2])
+    prob = dict(_problem(EULER, M, cfl, [N], [0.0], [1.0], [bc], gamma=gamma),
+                source=SOURCE_GRAVITY, source_coef=g)
+    return prob, avg, lim, lim.copy()
+
+
+# --------------------------------------------------------------------------
 # Counter-based random numbers: SplitMix64 (Steele, Lea, Flood 2014) applied
 # to (seed, domain, draw).  Used only to draw workload parameters.
 # --------------------------------------------------------------------------

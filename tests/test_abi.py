@@ -40,6 +40,23 @@ def test_invalid_problem_is_rejected_on_the_host():
         grprec.Solver(dict(prob, n_cells=[0]))
 
 
+def test_source_combinations_are_rejected_on_the_host():
+    """A source term needs its system (S = k q: advection; the acceleration:
+    Euler), the Toro-Titarev solver, linear GRPrec and a finite coefficient."""
+    from paper_2602_21911_gb300 import grprec, inputs
+    prob, *_ = inputs.sod(20, M=2)
+    for bad in (dict(source=inputs.SOURCE_LINEAR, source_coef=1.0),
+                dict(source=inputs.SOURCE_GRAVITY, source_coef=1.0, solver=1),
+                dict(source=inputs.SOURCE_GRAVITY, source_coef=1.0, recon=1),
+                dict(source=inputs.SOURCE_GRAVITY, source_coef=float("nan")),
+                dict(source=7, source_coef=1.0)):
+        with pytest.raises(grprec.GrpError, match="invalid"):
+            grprec.Solver(dict(prob, **bad))
+    adv, *_ = inputs.advection_sine(8)
+    with pytest.raises(grprec.GrpError, match="invalid"):
+        grprec.Solver(dict(adv, source=inputs.SOURCE_GRAVITY, source_coef=1.0))
+
+
 class _FakeCuda:
     """Stands in for a torch CUDA tensor: only the attributes the buffer
     checks of the allocation-free step read (no GPU, no library call)."""
