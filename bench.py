@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--M", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other", action="store_true", help="skip the single-domain workloads")
-    ap.add_argument("--launch", default="tune", choices=["tune", "auto", "flat", "fused", "split"],
+    ap.add_argument("--launch", default="tune", choices=["tune", "auto", "flat", "fused", "split", "tiled"],
                     help="launch configuration: autotuned (default), library default, or forced")
     ap.add_argument("--guess", default="learned", choices=["learned", "pvrs"])
     ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
@@ -73,6 +73,14 @@ def parse():
     ap.add_argument("--plain-domains", type=int, default=128, help="sample size of the plain form (0: skip)")
     ap.add_argument("--plain-steps", type=int, default=60)
     ap.add_argument("--no-l1", action="store_true", help="skip the L1 errors against exact solutions")
+    ap.add_argument("--workload", default="batched", choices=["batched", "sod"],
+                    help="the batch (default) or Sod's shock tube on --cells cells (profiling and context)")
+    ap.add_argument("--cells", type=int, default=1 << 22)
+    ap.add_argument("--recon", default="grprec", choices=["grprec", "nl"])
+    ap.add_argument("--solver", default="tt", choices=["tt", "det"])
+    ap.add_argument("--dt-hold", type=int, default=1, help="recompute dt every k steps (1: the paper's rule)")
+    ap.add_argument("--cfl", type=float, default=0.9)
+    ap.add_argument("--tile-cells", type=int, default=512, help="--launch tiled: owned cells per tile")
     return ap.parse_args()
 
 
@@ -156,10 +164,16 @@ def workload(args, rank, world):
     Strong scaling: the ranks split one batch (seed 2602) by longest-first
     balancing of the cell counts."""
     from paper_2602_21911_gb300 import dist as D, inputs as I
+    extra = dict(recon=1 if args.recon == "nl" else 0, solver=1 if args.solver == "det" else 0, dt_hold=args.dt_hold)
+    if args.workload == "sod":
+        prob, avg, lm, lp = I.sod(args.cells, M=args.M, cfl=args.cfl)
+        return (dict(prob, **extra), avg, lm, lp)
     if args.scaling == "strong" and world > 1:
         part = D.lpt_partition(I.batched_params(args.domains, 2602)["n"], world)[rank]
-        return I.batched(args.domains, seed=2602, M=args.M, domains=part)
-    return I.batched(args.domains, seed=2602 + rank, M=args.M)
+        prob, avg, lm, lp = I.batched(args.domains, seed=2602, M=args.M, domains=part)
+    else:
+        prob, avg, lm, lp = I.batched(args.domains, seed=2602 + rank, M=args.M, cfl=args.cfl)
+    return (dict(prob, **extra), avg, lm, lp)
 
 
 def train_guess(args, device):
@@ -167,12 +181,18 @@ def train_guess(args, device):
     train the network with the library's kernels; returns (weights, box, info)."""
     from paper_2602_21911_gb300 import inputs as I, learned
     t0 = time.perf_counter()
-    runs = [(*I.batched(args.domains, seed=2603, M=args.M), 500), (*I.sod(4096, M=args.M), 400)]
-    rec = learned.harvest(runs, capacity=2_000_000, log2_stride=0, device=device)
-    w, box, info = learned.fit_from_records(rec)
+    # the shock tube on 2^16 cells (about t = 0.2) and the batch of another
+    # seed: every strong-data Riemann problem with a shock of the flux kernel
+    # and of the repair rounds
+    runs = [(*I.sod(1 << 16, M=args.M), 30000), (*I.batched(args.domains, seed=2603, M=args.M), 700)]
+    rec = learned.harvest(runs, capacity=12_000_000, log2_stride=0, device=device)
+    t1 = time.perf_counter()
+    w, box, info = learned.fit_from_records(rec, max_records=12_000_000, batch=4096, max_steps=60_000)
     return w, box, {"records": int(rec.shape[0]), "trained_on": info["n_train"], "val_rms": info["val_rms"],
-                    "target_std": float(rec[:, 6].std().item()), "seconds": time.perf_counter() - t0,
-                    "harvest": "batched seed 2603 x 500 steps + Sod 4096 x 400 steps"}
+                    "target_std": float(rec[:, 6].std().item()), "harvest_seconds": t1 - t0,
+                    "train_seconds": time.perf_counter() - t1,
+                    "harvest": "Sod 2^16 cells x 30000 steps + batched seed 2603 x 700 steps, flux kernel and "
+                               "repair rounds"}
 
 
 def plain_arm(args, device, stream, w, box):
@@ -203,6 +223,25 @@ def plain_arm(args, device, stream, w, box):
     plain_state = np.concatenate([sj.get_state()[0] for sj in solvers], axis=1)
     for sj in solvers:
         sj.close()
+    # the same plain form with each solver's steps replayed from CUDA graphs
+    # (launch overhead removed; still one small domain per launch sequence)
+    solvers = []
+    for pj, aj, mj, qj in doms:
+        sj = grprec.Solver(pj, device=device, stream=stream.cuda_stream)
+        sj.set_launch(grprec.GRP_LAUNCH_FLAT)
+        sj.set_graph(args.plain_steps)
+        sj.set_initial(aj, mj, qj)
+        sj.step(args.plain_steps)                     # captures the graph of plain_steps steps
+        sj.set_initial(aj, mj, qj)
+        solvers.append(sj)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for sj in solvers:
+        sj.step(args.plain_steps)
+    torch.cuda.synchronize()
+    el_g = time.perf_counter() - t0
+    for sj in solvers:
+        sj.close()
     # the batched forms on the same sample, same number of steps
     diffs = {}
     forms = [("batched_pvrs", grprec.GRP_GUESS_PVRS)]
@@ -220,7 +259,11 @@ def plain_arm(args, device, stream, w, box):
     return {"value": upd / el, "unit": UNIT,
             "sample": "%d domains evenly spread over the batch (%d cells) x %d steps, one solver per domain, "
                       "flat kernels, direct launches, PVRS start" % (len(ids), int(prob["n_cells"].sum()),
-                                                                     args.plain_steps)}, diffs
+                                                                     args.plain_steps),
+            "graphs": {"value": float(prob["n_cells"].sum()) * args.plain_steps / el_g, "unit": UNIT,
+                       "note": "the same, each solver's steps replayed from one CUDA graph"},
+            "note": "one small domain per launch sequence: bound by launch and kernel latency, not by the "
+                    "method's arithmetic"}, diffs
 
 
 def other_workloads(local, stream):
@@ -270,6 +313,21 @@ def other_workloads(local, stream):
     out["sod_N4194304_M2"] = {"cell_updates_per_s": (1 << 22) / (ms * 1e-3), "ms_per_step": ms,
                               "window": "steps 9..72 of t_end = 0.2"}
     s.close()
+    # temporal blocking: dt held over 4 steps (C = 0.6, so that the held step
+    # stays below the Courant limit while the shock forms), the flat form and
+    # the tiled form (tiles of 512 cells in shared memory, 4 steps per launch:
+    # the same results)
+    for name, tiled in (("sod_N4194304_M2_C0.6_dthold4_flat", False), ("sod_N4194304_M2_C0.6_dthold4_tiled", True)):
+        s = grprec.Solver(dict(prob, dt_hold=4, cfl=0.6), device=local, stream=stream.cuda_stream)
+        if tiled:
+            s.set_launch(grprec.GRP_LAUNCH_TILED, 128, 512, 4)
+        else:
+            s.set_launch(grprec.GRP_LAUNCH_FLAT)
+        s.set_initial(avg, lm, lp)
+        ms = timed(s, 64)
+        out[name] = {"cell_updates_per_s": (1 << 22) / (ms * 1e-3), "ms_per_step": ms,
+                     "launch": s.get_launch(), "window": "steps 9..72"}
+        s.close()
     # GRPrecNL (Sections 3.3-3.4): the batch and the shock tube
     prob, avg, lm, lp = I.batched(65536, seed=2602, M=2)
     s = grprec.Solver(dict(prob, recon=grprec.GRP_RECON_GRPRECNL), device=local, stream=stream.cuda_stream)
@@ -457,6 +515,18 @@ def l1_measurements(args, device, stream, w, box):
     for a, b in zip(sod[:-1], sod[1:]):
         b["order"] = float(np.log2(a["l1_rho"] / b["l1_rho"]))
     out["sod_t0.2"] = sod
+    # the time step held over 4 steps at C = 0.6 (the tiled form's reading; its
+    # results equal the flat form's with the same dt_hold): L1 beside the above
+    N = 1 << 18
+    prob, avg, lm, lp = I.sod(N, M=args.M, cfl=0.6)
+    s = grprec.Solver(dict(prob, dt_hold=4), device=device, stream=stream.cuda_stream)
+    s.set_initial(avg, lm, lp)
+    s.advance_to(0.2)
+    ex = exact_riemann_averages((np.ones(1), np.zeros(1), np.ones(1)), (np.full(1, 0.125), np.zeros(1),
+                                np.full(1, 0.1)), 0.5, 0.2, np.linspace(0.0, 1.0, N + 1)[None, :])[0]
+    out["sod_t0.2_C0.6_dthold4_N262144"] = {"l1_rho": float(s.error_norms(ex)[0][0]),
+                                       "steps": int(s.get_stats()[0][0, 0])}
+    s.close()
     return out
 
 
@@ -543,6 +613,8 @@ def main():
         s.set_launch(grprec.GRP_LAUNCH_FUSED)
     elif args.launch == "split":
         s.set_launch(grprec.GRP_LAUNCH_SPLIT)
+    elif args.launch == "tiled":
+        s.set_launch(grprec.GRP_LAUNCH_TILED, 128, args.tile_cells, args.dt_hold)
     launch = s.get_launch()
     # CUDA graphs of exactly W steps, with the flux kernel's timing events, so
     # that the W warm-up steps capture and instantiate the graph (a one-time
@@ -627,9 +699,15 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tmax / max(args.steps, 1), "higher_is_better": True,
             "scaling": args.scaling, "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batched Euler: %d domains x log-uniform 4..512 cells, M=%d, CFL 0.9, "
-                                   "transmissive, %s" % (args.domains, args.M,
-                                                         "learned p* guess" if learned else "PVRS p* guess"),
+            "config": {"workload": ("batched Euler: %d domains x log-uniform 4..512 cells, M=%d, CFL 0.9, "
+                                    "transmissive, %s" % (args.domains, args.M,
+                                                          "learned p* guess" if learned else "PVRS p* guess")
+                                    if args.workload == "batched" else
+                                    "Sod shock tube, %d cells, M=%d, CFL %g, transmissive" % (args.cells, args.M,
+                                                                                               args.cfl))
+                                   + ("" if args.recon == "grprec" else ", GRPrecNL")
+                                   + ("" if args.solver == "tt" else ", DET solver")
+                                   + ("" if args.dt_hold == 1 else ", dt held over %d steps" % args.dt_hold),
                        "seed": 2602, "cells": int(prob["n_cells"].sum()), "launch": launch,
                        "l2": "state larger than L2 (no flush needed)"},
             "e2e": {"value": upd_e2e / e2e_s, "unit": UNIT,
@@ -643,7 +721,11 @@ def main():
                             "note": "final averages of the plain sample vs the batched forms on the same "
                                     "domains and steps"} if equal else None,
             "learned_guess": dict(guess_info or {}, **guess_stats) if learned else None}
-    if launch["form"] == grprec.GRP_LAUNCH_FUSED:
+    default_path = (args.workload == "batched" and args.recon == "grprec" and args.solver == "tt" and args.dt_hold == 1
+                    and args.cfl == 0.9)
+    if not default_path:
+        flops, kname, per_launch_updates = None, None, None     # the op counts are of the default path
+    elif launch["form"] == grprec.GRP_LAUNCH_FUSED:
         flops = STEP_FLOPS_PER_UPDATE.get(("batched", args.M))
         kname = "k_batch<Euler,M=%d> (%d steps per launch)" % (args.M, launch["steps_per_launch"])
         per_launch_updates = (upd / world) / args.steps * launch["steps_per_launch"]

@@ -47,7 +47,8 @@ typedef struct grp_ctx grp_ctx;   /* opaque, library-owned */
 enum { GRP_ADVECTION = 0, GRP_EULER_IDEAL = 1 };                 /* system (Sections 4.2, 4.3) */
 enum { GRP_BC_PERIODIC = 0, GRP_BC_TRANSMISSIVE = 1 };            /* per-domain boundary */
 enum { GRP_GUESS_PVRS = 0, GRP_GUESS_TRRS = 1, GRP_GUESS_MLP = 2 };/* Newton initial guess for p* */
-enum { GRP_LAUNCH_AUTO = 0, GRP_LAUNCH_FLAT = 1, GRP_LAUNCH_FUSED = 2, GRP_LAUNCH_SPLIT = 3 }; /* grp_set_launch */
+enum { GRP_LAUNCH_AUTO = 0, GRP_LAUNCH_FLAT = 1, GRP_LAUNCH_FUSED = 2, GRP_LAUNCH_SPLIT = 3,
+       GRP_LAUNCH_TILED = 4 };                                                              /* grp_set_launch */
 enum { GRP_RECON_GRPREC = 0, GRP_RECON_GRPRECNL = 1 };            /* reconstruction (Sections 3.1, 3.3-3.4) */
 enum { GRP_SOLVER_TT = 0, GRP_SOLVER_DET = 1 };                   /* GRP solver (Section 2, Section 4.1) */
 enum { GRP_SOURCE_NONE = 0, GRP_SOURCE_LINEAR = 1, GRP_SOURCE_GRAVITY = 2 };  /* source term S(Q) (Section 2) */
@@ -200,6 +201,19 @@ int grp_error_norms(grp_ctx *ctx, const double *exact_averages, int ptr_is_devic
  *   GRP_LAUNCH_SPLIT: two launches per step: the grid-wide flux kernel, then a
  *                     per-domain-group kernel for update, repair, bookkeeping
  *                     and the next step's S_max.
+ *   GRP_LAUNCH_TILED: temporal blocking: tiles of cells_per_block cells held in
+ *                     shared memory with a halo of steps_per_launch x
+ *                     (reach + 4) + 1 cells (reach 1 for GRPrec of degree
+ *                     <= 2, else 2; 4 repair rounds), each block advancing its
+ *                     tile steps_per_launch steps with dt held over them.  Runs
+ *                     only when dt_hold == steps_per_launch, for grp_step with
+ *                     an infinite t_end, from a step count that is a multiple
+ *                     of steps_per_launch; other steps take the FLAT form.
+ *                     Results equal the FLAT form's; a domain that fails inside
+ *                     a launch is frozen at the end of that launch.  Not with
+ *                     DET or a source term.  A domain that fits one region is
+ *                     one tile.  Rejected when a region does not fit 227 KB of
+ *                     shared memory.
  *   GRP_LAUNCH_AUTO:  SPLIT for >= 1024 domains of <= 4096 cells, else FLAT.
  * threads: 128 or 256 per block (FUSED, SPLIT); cells_per_block in [64, 2^20];
  * steps_per_launch in [1, 1024] (FUSED).  Synchronises the stream.  Defaults:
@@ -251,8 +265,10 @@ int grp_set_graph(grp_ctx *ctx, int steps_per_graph);
  * device (ptr_is_device); copied, not kept.  Synchronises.
  *
  * grp_set_harvest: record (6 inputs, the target v = ln(p* / p_TR) /
- * (-0.005 s^3), Newton iterations) of one network-served interface in
- * 2^log2_stride, by a hash of (interface, step),
+ * (-0.005 s^3), Newton iterations) of one strong-data Riemann problem with a
+ * shock (those the network serves) in 2^log2_stride, by a hash of
+ * (interface, step), from the flux kernel and from the repair rounds of the
+ * flat form (whose first-order problems start from the classical estimate),
  * into the caller's device buffer records[capacity][8] during later steps;
  * *count (device, caller-zeroed) counts the offered records and may exceed
  * capacity (the excess is dropped).  records = NULL stops harvesting.

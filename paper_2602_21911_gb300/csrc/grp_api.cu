@@ -9,6 +9,7 @@
 
 #include "grp_kernels.cuh"
 #include "grp_launch.h"
+#include "grp_tile.cuh"
 #include "grprec.h"
 
 using namespace grp;
@@ -23,6 +24,7 @@ struct grp_ctx {
   long long launches = 0;
   std::vector<long long> h_cell_off, h_if_off;
   std::vector<double> h_dx;
+  std::vector<unsigned char> h_bc;
   // device
   long long *cell_off = nullptr, *if_off = nullptr;
   int *cell_dom = nullptr, *if_dom = nullptr;
@@ -53,6 +55,12 @@ struct grp_ctx {
   int max_cells = 0;
   int* grp = nullptr;            // device [n_blocks + 1] first domain of each block
   int n_blocks = 0;
+  // tiled form: tiles, the tile view's zero domain map, per-domain flags
+  TileInfo* tiles = nullptr;
+  int n_tiles = 0, tile_rmax = 0;
+  int* tile_zeros = nullptr;
+  int* tile_flag = nullptr;
+  long long host_steps = 0;      // steps since grp_set_initial (every active domain takes them with t_end = inf)
   bool smax_ready = false;       // S_max of the current state already reduced (split form)
   // optional CUDA-event timing of the flux kernel launches
   bool timing = false;
@@ -65,6 +73,7 @@ struct grp_ctx {
     bool smax_ready = false;
     unsigned long long t_end_bits = 0;
     int steps = 0;
+    int cur_end = 0;                 // buffer parity after the graph
     long long launches = 0;
     std::vector<cudaGraphNode_t> ev_nodes;   // event-record nodes of the flux timing, in pair order
   };
@@ -118,7 +127,7 @@ void free_all(grp_ctx* c)
                   c->ifc[0], c->ifc[1], c->flux, c->pold, c->ds, c->det_ed, c->srcv, c->low, c->troubled, c->t, c->dt_prev, c->nstep,
                   c->status, c->smax_bits, c->bad, c->inad, c->fail, c->any_bad, c->tlist0, c->tlist1,
                   c->ilist, c->lcount, c->stats,
-                  c->scratch_norm, c->mlp, c->mlp_norm, c->grp};
+                  c->scratch_norm, c->mlp, c->mlp_norm, c->grp, c->tiles, c->tile_zeros, c->tile_flag};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -220,6 +229,8 @@ int launch_form(const grp_ctx* c)
 {
   if (c->p.solver == GRP_SOLVER_DET) return GRP_LAUNCH_FLAT;     // DET has the flat form only
   if (c->p.source != GRP_SOURCE_NONE) return GRP_LAUNCH_FLAT;     // so do source terms
+  // the tiled form holds dt over its steps: dt_hold must equal the steps per launch
+  if (c->mode == GRP_LAUNCH_TILED) return c->p.dt_hold == c->steps_per_launch ? GRP_LAUNCH_TILED : GRP_LAUNCH_FLAT;
   if (c->mode != GRP_LAUNCH_AUTO) return c->mode;
   // auto: whole domains per block pay off when the batch has many short domains
   return c->D >= 1024 && c->max_cells <= 4096 ? GRP_LAUNCH_SPLIT : GRP_LAUNCH_FLAT;
@@ -271,6 +282,7 @@ int enqueue_batch(grp_ctx* c, int nsteps, double t_end)
     c->ev_pending.push_back(e1);
   }
   c->cur ^= (nsteps & 1);
+  c->host_steps += nsteps;
   return GRP_OK;
 }
 
@@ -306,6 +318,99 @@ int enqueue_split(grp_ctx* c, double t_end)
   CK(c->p.system == GRP_ADVECTION ? launch_post_adv(L, s) : launch_post_euler(L, s));
   c->launches++;
   c->cur ^= 1;
+  c->host_steps += 1;
+  return GRP_OK;
+}
+
+// Tiles of cells_per_block owned cells with a halo of
+// steps_per_launch x (reach + MAX_REPAIR) + 1 cells; a domain that fits in one
+// region is one tile holding the whole domain.
+int tile_halo(const grp_ctx* c)
+{
+  const int reach = (c->p.recon == GRP_RECON_GRPRECNL || c->p.M >= 3) ? 2 : 1;
+  return c->steps_per_launch * (reach + MAX_REPAIR) + 1;
+}
+
+int build_tiles(grp_ctx* c)
+{
+  const int T = c->cells_per_block, H = tile_halo(c);
+  std::vector<TileInfo> v;
+  int rmax = 0;
+  for (int d = 0; d < c->D; ++d) {
+    const int N = (int)(c->h_cell_off[d + 1] - c->h_cell_off[d]);
+    if (N <= T + 2 * H) {
+      v.push_back(TileInfo{d, 0, N, 0, N, 1});
+      rmax = N > rmax ? N : rmax;
+      continue;
+    }
+    for (int o0 = 0; o0 < N; o0 += T) {
+      const int o1 = o0 + T < N ? o0 + T : N;
+      int r0 = o0 - H, r1 = o1 + H;
+      if (c->h_bc[d] != GRP_BC_PERIODIC) { r0 = r0 < 0 ? 0 : r0; r1 = r1 > N ? N : r1; }
+      v.push_back(TileInfo{d, o0, o1, r0, r1, 0});
+      rmax = r1 - r0 > rmax ? r1 - r0 : rmax;
+    }
+  }
+  if (c->tiles) cudaFree(c->tiles);
+  if (c->tile_zeros) cudaFree(c->tile_zeros);
+  if (c->tile_flag) cudaFree(c->tile_flag);
+  c->tiles = nullptr; c->tile_zeros = nullptr; c->tile_flag = nullptr;
+  CK(cudaMalloc((void**)&c->tiles, sizeof(TileInfo) * v.size()));
+  CK(cudaMemcpy(c->tiles, v.data(), sizeof(TileInfo) * v.size(), cudaMemcpyHostToDevice));
+  CK(cudaMalloc((void**)&c->tile_zeros, sizeof(int) * (rmax + 1)));
+  CK(cudaMemset(c->tile_zeros, 0, sizeof(int) * (rmax + 1)));
+  CK(cudaMalloc((void**)&c->tile_flag, sizeof(int) * c->D));
+  CK(cudaMemset(c->tile_flag, 0, sizeof(int) * c->D));
+  c->n_tiles = (int)v.size();
+  c->tile_rmax = rmax;
+  // the tile kernel's shared-memory limit, raised here, outside any capture
+  TileArgs T0{};
+  CK(launch_tile(make_args(c, INFINITY), T0, 0u, tile_smem_bytes(c->C, rmax), c->stream));
+  return GRP_OK;
+}
+
+// steps_per_launch steps of every domain in one tile launch (t_end = inf)
+int enqueue_tiled(grp_ctx* c)
+{
+  if (!c->tiles) { const int rc = build_tiles(c); if (rc) return rc; }
+  c->smax_ready = false;
+  const StepArgs a = make_args(c, INFINITY);
+  cudaStream_t s = c->stream;
+  if (c->p.system == GRP_EULER_IDEAL) {
+    k_smax<<<blocks(c->ncell, 256), 256, 0, s>>>(a);
+    c->launches++;
+  }
+  k_dt<<<blocks(c->D, 128), 128, 0, s>>>(a);
+  c->launches++;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->timing) {
+    for (cudaEvent_t* e : {&e0, &e1}) {
+      if (!c->ev_free.empty()) { *e = c->ev_free.back(); c->ev_free.pop_back(); }
+      else CK(cudaEventCreate(e));
+    }
+    CK(record(c, e0));
+  }
+  TileArgs T;
+  T.tiles = c->tiles;
+  T.nsteps = c->steps_per_launch;
+  T.rmax = c->tile_rmax;
+  T.A = c->avg[c->cur];
+  T.An = c->avg[c->cur ^ 1];
+  T.I = c->ifc[c->cur];
+  T.In = c->ifc[c->cur ^ 1];
+  T.zeros = c->tile_zeros;
+  T.dflag = c->tile_flag;
+  CK(launch_tile(a, T, (unsigned)c->n_tiles, tile_smem_bytes(c->C, c->tile_rmax), s));   // (attribute set by build_tiles)
+  c->launches++;
+  if (c->timing) {
+    CK(record(c, e1));
+    c->ev_pending.push_back(e0);
+    c->ev_pending.push_back(e1);
+  }
+  CK(launch_tile_finish(a, c->tile_flag, c->steps_per_launch, s));
+  c->launches++;
+  c->cur ^= 1;
+  c->host_steps += c->steps_per_launch;
   return GRP_OK;
 }
 
@@ -359,6 +464,7 @@ int enqueue_step(grp_ctx* c, double t_end)
   c->launches++;
   CK(cudaGetLastError());
   c->cur ^= 1;
+  c->host_steps += 1;
   return GRP_OK;
 }
 
@@ -431,6 +537,7 @@ int grp_create(grp_ctx** out, const grp_problem* p)
   c->h_if_off.assign(c->D + 1, 0);
   c->h_dx.assign(c->D, 0.0);
   std::vector<unsigned char> hbc(c->D);
+  c->h_bc.assign(c->D, 0);
   for (int d = 0; d < c->D; ++d) {
     const int N = p->n_cells[d];
     if (N < 1 || (p->bc[d] != GRP_BC_PERIODIC && p->bc[d] != GRP_BC_TRANSMISSIVE) ||
@@ -442,6 +549,7 @@ int grp_create(grp_ctx** out, const grp_problem* p)
     c->h_if_off[d + 1] = c->h_if_off[d] + N + (p->bc[d] == GRP_BC_TRANSMISSIVE ? 1 : 0);
     c->h_dx[d] = (p->x_right[d] - p->x_left[d]) / N;
     hbc[d] = (unsigned char)p->bc[d];
+    c->h_bc[d] = hbc[d];
     if (N > c->max_cells) c->max_cells = N;
   }
   c->ncell = c->h_cell_off[c->D];
@@ -534,6 +642,7 @@ int grp_set_initial(grp_ctx* c, const double* averages, const double* lim_minus,
   CK(cudaMemsetAsync(c->inad, 0, sizeof(int) * D, s));
   CK(cudaMemsetAsync(c->fail, 0, sizeof(int) * D, s));
   c->initialized = true;
+  c->host_steps = 0;
   c->smax_ready = false;
   return GRP_OK;
 }
@@ -549,10 +658,18 @@ int grp_step(grp_ctx* c, int n_steps, double t_end)
 
 int grp_set_launch(grp_ctx* c, int mode, int threads, int cells_per_block, int steps_per_launch)
 {
-  if (!c || mode < GRP_LAUNCH_AUTO || mode > GRP_LAUNCH_SPLIT) return GRP_E_INVALID_ARG;
+  if (!c || mode < GRP_LAUNCH_AUTO || mode > GRP_LAUNCH_TILED) return GRP_E_INVALID_ARG;
   if (threads != 128 && threads != 256) return GRP_E_INVALID_ARG;
   if (cells_per_block < 64 || cells_per_block > (1 << 20) || steps_per_launch < 1 || steps_per_launch > 1024)
     return GRP_E_INVALID_ARG;
+  if (mode == GRP_LAUNCH_TILED) {
+    // the largest region of a tile must fit the shared memory of a block
+    grp_ctx probe = grp_ctx();
+    probe.p = c->p;
+    probe.steps_per_launch = steps_per_launch;
+    const long long rmax = (long long)cells_per_block + 2ll * tile_halo(&probe);
+    if (rmax > (1 << 20) || tile_smem_bytes(c->C, (int)rmax) > 227u * 1024u) return GRP_E_INVALID_ARG;
+  }
   CK(cudaSetDevice(c->p.device));
   CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
   drop_graphs(c);
@@ -562,6 +679,7 @@ int grp_set_launch(grp_ctx* c, int mode, int threads, int cells_per_block, int s
   c->cells_per_block = cells_per_block;
   c->steps_per_launch = steps_per_launch;
   if (regroup && c->grp) { cudaFree(c->grp); c->grp = nullptr; }
+  if (c->tiles) { cudaFree(c->tiles); c->tiles = nullptr; }       // rebuilt for the new tile and depth
   return GRP_OK;
 }
 
@@ -589,14 +707,33 @@ int grp_get_launch(const grp_ctx* c, int* batched, int* threads, int* cells_per_
 
 namespace {
 // steps one launch unit of the current form advances
-int unit_steps(const grp_ctx* c) { return launch_form(c) == GRP_LAUNCH_FUSED ? c->steps_per_launch : 1; }
+// the tiled form serves steps without an end time, in whole units that start
+// where dt is recomputed (every steps_per_launch steps)
+bool tiled_now(const grp_ctx* c, double t_end)
+{
+  return launch_form(c) == GRP_LAUNCH_TILED && isinf(t_end) && t_end > 0 &&
+         c->host_steps % c->steps_per_launch == 0;
+}
+
+int unit_steps(const grp_ctx* c, double t_end)
+{
+  const int form = launch_form(c);
+  if (form == GRP_LAUNCH_FUSED) return c->steps_per_launch;
+  if (form == GRP_LAUNCH_TILED && tiled_now(c, t_end)) return c->steps_per_launch;
+  return 1;
+}
 
 int enqueue_unit(grp_ctx* c, int k, double t_end)
 {
   const int form = launch_form(c);
   if (form == GRP_LAUNCH_FUSED) return enqueue_batch(c, k, t_end);
   if (form == GRP_LAUNCH_SPLIT) return enqueue_split(c, t_end);
-  return enqueue_step(c, t_end);
+  if (form == GRP_LAUNCH_TILED && k == c->steps_per_launch && tiled_now(c, t_end)) return enqueue_tiled(c);
+  for (int i = 0; i < k; ++i) {
+    const int rc = enqueue_step(c, t_end);
+    if (rc) return rc;
+  }
+  return GRP_OK;
 }
 
 unsigned long long bits_of(double x)
@@ -614,8 +751,12 @@ int capture_graph(grp_ctx* c, int steps, double t_end, grp_ctx::Graph& out)
 {
   if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   // the domain groups are built (allocation, copy) before capture begins
-  if (launch_form(c) != GRP_LAUNCH_FLAT && !c->grp) {
+  if ((launch_form(c) == GRP_LAUNCH_FUSED || launch_form(c) == GRP_LAUNCH_SPLIT) && !c->grp) {
     const int rc = build_groups(c);
+    if (rc) return rc;
+  }
+  if (launch_form(c) == GRP_LAUNCH_TILED && !c->tiles) {
+    const int rc = build_tiles(c);
     if (rc) return rc;
   }
   // timing events are created before capture begins
@@ -639,13 +780,16 @@ int capture_graph(grp_ctx* c, int steps, double t_end, grp_ctx::Graph& out)
   c->stream = c->cap_stream;
   c->capturing = true;
   int rc = GRP_OK;
-  const int k = unit_steps(c);
+  const long long hs0 = c->host_steps;
+  const int k = unit_steps(c, t_end);
   for (int i = 0; i < steps && rc == GRP_OK; i += k) rc = enqueue_unit(c, k, t_end);
   cudaGraph_t g = nullptr;
   const cudaError_t e_end = cudaStreamEndCapture(c->cap_stream, &g);
   c->stream = user;
   c->capturing = false;
   out.launches = c->launches - launches0;
+  out.cur_end = c->cur;
+  c->host_steps = hs0;
   // the timing events recorded during capture become nodes of the graph
   std::vector<cudaEvent_t> evs(c->ev_pending.begin() + ev0, c->ev_pending.end());
   c->ev_pending.resize(ev0);
@@ -706,7 +850,8 @@ int replay_graph(grp_ctx* c, double t_end)
   }
   CK(cudaGraphLaunch(G->x, c->stream));
   c->launches += G->launches;
-  c->cur ^= (G->steps & 1);
+  c->cur = G->cur_end;
+  c->host_steps += G->steps;
   if (launch_form(c) == GRP_LAUNCH_SPLIT) c->smax_ready = true;
   else c->smax_ready = false;
   return GRP_OK;
@@ -726,8 +871,9 @@ int step_n(grp_ctx* c, int n_steps, double t_end)
       if (done) break;
       since_check = 0;
     }
-    int k = unit_steps(c);
-    if (c->graph_steps > 0 && n_steps - i >= c->graph_steps && c->graph_steps % k == 0) {
+    int k = unit_steps(c, t_end);
+    if (c->graph_steps > 0 && n_steps - i >= c->graph_steps && c->graph_steps % k == 0 &&
+        (launch_form(c) != GRP_LAUNCH_TILED || tiled_now(c, t_end) || !isinf(t_end))) {
       const int rc = replay_graph(c, t_end);
       if (rc) return rc;
       k = c->graph_steps;

@@ -332,7 +332,10 @@ __device__ __forceinline__ void cell_coeffs(const StepArgs& a, long long c0, lon
 // longer than the Newton iterations it saves, and the repair kernels are
 // bound by that latency.
 template <bool G75>
-static __device__ int first_order(const StepArgs& a, long long c0, int N, int bc, int j, double F[3], double Q0[3], int& iters)
+// info (harvest): the network features and the two-rarefaction base of
+// strong data are recorded on the way (the start stays the classical one).
+static __device__ int first_order(const StepArgs& a, long long c0, int N, int bc, int j, double F[3], double Q0[3], int& iters,
+                                  RSInfo* info = nullptr)
 {
   int cl, cr;
   if (bc == 0) { cl = j == 0 ? N - 1 : j - 1; cr = j; }
@@ -343,7 +346,8 @@ static __device__ int first_order(const StepArgs& a, long long c0, int N, int bc
   Prim W;
   Phys ph = a.ph;
   ph.guess = GUESS_ADAPTIVE;
-  const int st = riemann_state<G75>(ph, QL, QR, true, Q0, W, iters);
+  ph.features = info ? 1 : 0;
+  const int st = riemann_state<G75>(ph, QL, QR, true, Q0, W, iters, info);
   if (st != ST_OK && st != ST_VACUUM) return st;
   if (Q0[0] > 0.0) euler_flux(a.ph.gamma, Q0[0], Q0[1], Q0[2], F);
   else F[0] = F[1] = F[2] = 0.0;
@@ -531,8 +535,11 @@ __device__ __forceinline__ void cell_source(const StepArgs& a, long long c0, lon
 // 0..30), lane 31 supplying the reconstruction of the cell left of
 // gbase + 31; interfaces at or beyond gend are not this call's.  All 32 lanes
 // of the warp call it (shuffles and warp statistics).
+// own0 <= gj < own1: the interfaces whose statistics count (a tile's halo
+// interfaces are computed but counted by the tile that owns them).
 template <int SYS, int M, bool G75, bool NL, bool SRC>
-__device__ __forceinline__ void flux_warp(const StepArgs& a, long long gbase, long long gend)
+__device__ __forceinline__ void flux_warp(const StepArgs& a, long long gbase, long long gend, long long own0 = 0,
+                                          long long own1 = 0x7fffffffffffffffll)
 {
   constexpr int C = SYS == SYS_EULER ? 3 : 1;
   const int lane = lane_id();
@@ -610,7 +617,7 @@ __device__ __forceinline__ void flux_warp(const StepArgs& a, long long gbase, lo
   }
   __syncwarp();
   if (SYS == SYS_EULER) {
-    warp_flux_stats(a.stats, d, st, a.ph.guess == 2);
+    warp_flux_stats(a.stats, gj >= own0 && gj < own1 ? d : -1, st, a.ph.guess == 2);
   }
 }
 
@@ -738,7 +745,11 @@ __device__ __forceinline__ void repair_iface(const StepArgs& a, int pass, long l
   const int N = (int)(a.cell_off[d + 1] - c0);
   double F[3], Q0[3];
   int iters = 0;
-  const int rs = first_order<G75>(a, c0, N, a.bc[d], (int)(gj - i0), F, Q0, iters);
+  RSInfo info;
+  const int rs = first_order<G75>(a, c0, N, a.bc[d], (int)(gj - i0), F, Q0, iters, a.harvest ? &info : nullptr);
+  // harvest: the strong data with a shock of the repair rounds (the network's
+  // domain) are recorded as the flux kernel records its own
+  if (a.harvest && rs == ST_OK && info.has_x) harvest_record(a, gj, d, info, iters);
   unsigned long long* S = a.stats + (long long)d * NSTATS;
   atomicAdd(S + S_NEWTON_SUM, (unsigned long long)iters);
   atomicMax(S + S_NEWTON_MAX, (unsigned long long)iters);

@@ -37,6 +37,11 @@ cudaError_t launch_batch_euler_m2(const BatchLaunch& L, cudaStream_t s);
 cudaError_t launch_batch_euler_m3(const BatchLaunch& L, cudaStream_t s);
 cudaError_t launch_batch_euler_m4(const BatchLaunch& L, cudaStream_t s);
 cudaError_t launch_post_adv(const BatchLaunch& L, cudaStream_t s);
+// temporally blocked tiles (grp_tile.cu, grp_tile_m34.cu)
+struct TileArgs;
+cudaError_t launch_tile(const StepArgs& a, const TileArgs& T, unsigned blocks, size_t smem, cudaStream_t s);
+cudaError_t launch_tile_m34(const StepArgs& a, const TileArgs& T, unsigned blocks, size_t smem, cudaStream_t s);
+cudaError_t launch_tile_finish(const StepArgs& a, int* dflag, int nsteps, cudaStream_t s);
 // flux kernels with a source term (grp_flux_src.cu, grp_flux_src_m34.cu)
 cudaError_t launch_flux_src(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_flux_src_m34(const StepArgs& a, cudaStream_t s);

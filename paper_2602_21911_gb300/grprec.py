@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 GRP_ADVECTION, GRP_EULER_IDEAL = 0, 1
 GRP_BC_PERIODIC, GRP_BC_TRANSMISSIVE = 0, 1
 GRP_GUESS_PVRS, GRP_GUESS_TRRS, GRP_GUESS_MLP = 0, 1, 2
-GRP_LAUNCH_AUTO, GRP_LAUNCH_FLAT, GRP_LAUNCH_FUSED, GRP_LAUNCH_SPLIT = 0, 1, 2, 3
+GRP_LAUNCH_AUTO, GRP_LAUNCH_FLAT, GRP_LAUNCH_FUSED, GRP_LAUNCH_SPLIT, GRP_LAUNCH_TILED = 0, 1, 2, 3, 4
 GRP_OK = 0
 GRP_NSTATS = 9
 (STAT_STEPS, STAT_NEWTON_SUM, STAT_NEWTON_MAX, STAT_RECON_FB, STAT_FLUX_FB, STAT_RS_CALLS,

@@ -1,6 +1,7 @@
 """Learned Newton initial guess: harvest, training and loading (marshalling only).
 
-1. harvest: run the scheme with grp_set_harvest on; the flux kernel records the
+1. harvest: run the scheme (flat form) with grp_set_harvest on; the flux
+   kernel and the repair rounds record the
    network inputs and the converged FP64 target v = ln(p*/p_TR) / (-0.005 s^3)
    (the correction of the two-rarefaction estimate p_TR, normalised by the cube
    of the shock strength s = ln(p_TR / min(pL, pR))) at the interfaces the
@@ -33,6 +34,7 @@ def harvest(runs, capacity=2_000_000, log2_stride=2, device=0):
         rec = torch.empty((left, 8), dtype=torch.float32, device=dev)
         cnt = torch.zeros(1, dtype=torch.int64, device=dev)
         s = grprec.Solver(prob, device=device)
+        s.set_launch(grprec.GRP_LAUNCH_FLAT)        # the flat form's repair rounds record too
         s.set_harvest(rec, cnt, log2_stride)
         s.set_initial(avg, lm, lp)
         s.step(n_steps)
