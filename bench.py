@@ -184,15 +184,16 @@ def train_guess(args, device):
     # the shock tube on 2^16 cells (about t = 0.2) and the batch of another
     # seed: every strong-data Riemann problem with a shock of the flux kernel
     # and of the repair rounds
-    runs = [(*I.sod(1 << 16, M=args.M), 30000), (*I.batched(args.domains, seed=2603, M=args.M), 700)]
+    runs = [(*I.sod(1 << 16, M=args.M), 30000), (*I.batched(args.domains, seed=2603, M=args.M), 1000),
+            (*I.batched(args.domains, seed=2605, M=args.M), 1000)]
     rec = learned.harvest(runs, capacity=12_000_000, log2_stride=0, device=device)
     t1 = time.perf_counter()
     w, box, info = learned.fit_from_records(rec, max_records=12_000_000, batch=4096, max_steps=60_000)
     return w, box, {"records": int(rec.shape[0]), "trained_on": info["n_train"], "val_rms": info["val_rms"],
                     "target_std": float(rec[:, 6].std().item()), "harvest_seconds": t1 - t0,
                     "train_seconds": time.perf_counter() - t1,
-                    "harvest": "Sod 2^16 cells x 30000 steps + batched seed 2603 x 700 steps, flux kernel and "
-                               "repair rounds"}
+                    "harvest": "Sod 2^16 cells x 30000 steps + batched seeds 2603 and 2605 x 1000 steps, flux "
+                               "kernel and repair rounds"}
 
 
 def plain_arm(args, device, stream, w, box):

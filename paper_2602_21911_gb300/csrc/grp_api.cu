@@ -177,7 +177,8 @@ StepArgs make_args(const grp_ctx* c, double t_end)
   a.stats = c->stats;
   a.ph.mlp_w = c->mlp;
   a.ph.mlp_box = c->mlp_norm;
-  a.ph.features = (c->p.guess == GRP_GUESS_MLP && c->mlp) || c->harvest ? 1 : 0;
+  // 2: harvest (the records' targets in FP64); 1: the learned start alone
+  a.ph.features = c->harvest ? 2 : (c->p.guess == GRP_GUESS_MLP && c->mlp ? 1 : 0);
   a.harvest = c->harvest;
   a.harvest_count = c->harvest_count;
   a.harvest_cap = c->harvest_cap;

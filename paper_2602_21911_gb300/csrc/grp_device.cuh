@@ -34,7 +34,8 @@ struct Phys {
   // learned Newton guess: FP32 weights (MLP_NPARAM) and input box lo[6], hi[6]
   const float* mlp_w;
   const float* mlp_box;
-  int features;          // compute the network features (learned guess or harvest)
+  int features;          // the learned-guess path for strong data: 0 off; 1 the learned start; 2 harvest
+                         // (the records' targets in FP64)
   // source term S(Q) of the balance law (Section 2): 0 none; 1 S = src_k q
   // (advection); 2 S = (0, -src_k rho, -src_k m) (Euler, acceleration -src_k)
   int src;
@@ -602,17 +603,30 @@ GRP_HD __forceinline__ bool strong_data(const Phys& ph, const Side& L, const Sid
          du2 * du2 * (L.r * R.r) > g2 * g2 * ph.gamma * ph.gamma * (L.p * R.p);
 }
 
-// Features x[6] and pbar of strong data.
-GRP_HD __forceinline__ void mlp_features(const Phys& ph, const Side& L, const Side& R, float x[6], double& pbar)
+// Features x[6] of strong data, in FP32 (the network's precision; off the
+// FP64 pipe, which the lanes around this one keep busy).
+GRP_HD __forceinline__ void mlp_features(const Phys& ph, const Side& L, const Side& R, float x[6])
 {
-  const float lp = logf((float)(L.p * R.ip));
-  const float lr = logf((float)(L.r * R.ir));
-  pbar = sqrt(L.p * R.p);
-  const double cbar = sqrt(ph.gamma * pbar * sqrt(L.ir * R.ir));
-  const float du = (float)((R.u - L.u) / cbar);
+  const float pl = (float)L.p, pr = (float)R.p, rl = (float)L.r, rr = (float)R.r;
+  const float lp = logf(pl / pr);
+  const float lr = logf(rl / rr);
+  const float cbar = sqrtf((float)ph.gamma * sqrtf(pl) * sqrtf(pr) / (sqrtf(rl) * sqrtf(rr)));
+  const float du = ((float)R.u - (float)L.u) / cbar;
   x[0] = 0.5f * lr; x[1] = -0.5f * lr;
   x[2] = 0.5f * lp; x[3] = -0.5f * lp;
   x[4] = -0.5f * du; x[5] = 0.5f * du;
+}
+
+// The two-rarefaction estimate in FP32, as a Newton start (Newton takes any
+// start to the same p*; the network's correction multiplies it).  0 when the
+// data generate vacuum.
+GRP_HD __forceinline__ float trrs_f32(const Phys& ph, const Side& L, const Side& R)
+{
+  const float cl = (float)L.c, cr = (float)R.c, gm1 = (float)ph.gm1, z = (float)ph.gm1_2g;
+  const float num = cl + cr - 0.5f * gm1 * ((float)R.u - (float)L.u);
+  if (!(num > 0.0f)) return 0.0f;
+  const float q = num / (cl * powf((float)L.p, -z) + cr * powf((float)R.p, -z));
+  return powf(q, 1.0f / z);
 }
 
 // The hidden activations live in local memory (the loops over neurons are not
@@ -635,19 +649,30 @@ GRP_HD inline float mlp_eval(const float* __restrict__ w, const float x[6])
     for (int i = 0; i < MLP_NIN; ++i) z = fmaf(x[i], W1[i * MLP_NH + j], z);
     h1[j] = fast_tanh(z);
   }
+  // the second layer eight outputs at a time: eight independent accumulation
+  // chains (each in the order j = 0..63, as a one-output loop would add) keep
+  // the chain's latency, not its length, on the critical path
   float y = b3;
 #pragma unroll 1
-  for (int k = 0; k < MLP_NH; ++k) {
-    float z = b2[k];
-#pragma unroll 4
-    for (int j = 0; j < MLP_NH; ++j) z = fmaf(h1[j], W2[j * MLP_NH + k], z);
-    y = fmaf(fast_tanh(z), w3[k], y);
+  for (int k0 = 0; k0 < MLP_NH; k0 += 8) {
+    float z[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) z[q] = b2[k0 + q];
+#pragma unroll 2
+    for (int j = 0; j < MLP_NH; ++j) {
+      const float h = h1[j];
+      const float* Wr = W2 + j * MLP_NH + k0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) z[q] = fmaf(h, Wr[q], z[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) y = fmaf(fast_tanh(z[q]), w3[k0 + q], y);
   }
   return y;
 }
 
 struct RSInfo {
-  double ps = 0.0, pbar = 0.0;   // star pressure; pbar of the features
+  double ps = 0.0;               // star pressure
   double base = 0.0;             // two-rarefaction estimate (the base of the learned correction)
   double s3 = 0.0;               // cube of the shock strength ln(p_TR / min(pL, pR))
   float x[6];                    // features (valid when has_x)
@@ -670,28 +695,54 @@ inline
 int learned_start(const Phys& ph, const Side& L, const Side& R, RSInfo& info, double& ps, double& us, int& iters)
 {
   int st = -1;
-  mlp_features(ph, L, R, info.x, info.pbar);
-  const double base = trrs<G75>(ph, L, R);
-  const bool ok = base > 0.0 && isfinite(base);
-  // shock strength s = ln(p_TR / min(pL, pR)); s <= 0: two rarefactions, and
-  // p_TR is p* up to rounding; s < MLP_S_MIN: |ln(p*/p_TR)| < 1e-11
-  const double sh = ok ? log(base / fmin(L.p, R.p)) : 0.0;
-  info.base = base;
-  info.s3 = sh * sh * sh;
-  info.has_x = ok && sh >= MLP_S_MIN;
-  if (ph.guess == 2 && ph.mlp_w && ok) {
-    double p0 = base;
-    bool go = true;
-    info.guess = 2;
-    if (info.has_x) {
+  mlp_features(ph, L, R, info.x);
+  double p0 = 0.0;
+  bool ok, go = true;
+  float v = 0.0f;
+  if (ph.features == 2) {
+    // harvest: the record's target ln(p*/p_TR) / (MLP_T_SCALE s^3) needs p_TR
+    // and the strength in FP64 (for weak shocks the correction is ~1e-12)
+    const double base = trrs<G75>(ph, L, R);
+    ok = base > 0.0 && isfinite(base);
+    // shock strength s = ln(p_TR / min(pL, pR)); s <= 0: two rarefactions, and
+    // p_TR is p* up to rounding; s < MLP_S_MIN: |ln(p*/p_TR)| < 1e-11
+    const double sh = ok ? log(base / fmin(L.p, R.p)) : 0.0;
+    info.base = base;
+    info.s3 = sh * sh * sh;
+    info.has_x = ok && sh >= MLP_S_MIN;
+    p0 = base;
+    if (ph.guess == 2 && ph.mlp_w && ok && info.has_x) {
       bool inbox = true;
 #pragma unroll
       for (int i = 0; i < 6; ++i) inbox = inbox && info.x[i] >= ph.mlp_box[i] && info.x[i] <= ph.mlp_box[6 + i];
-      const float v = inbox ? mlp_eval(ph.mlp_w, info.x) : 0.0f;
+      v = inbox ? mlp_eval(ph.mlp_w, info.x) : 0.0f;
       const double y = MLP_T_SCALE * info.s3 * (double)v;
       go = inbox && v == v && fabsf(v) <= MLP_VMAX && fabs(y) <= MLP_YMAX;
       p0 = base * exp(y);
     }
+  } else {
+    // inference: the start in FP32 (the same decisions and correction; Newton
+    // converges from it to the same p*)
+    const float base = trrs_f32(ph, L, R);
+    ok = base > 0.0f && isfinite(base);
+    const float sh = ok ? logf(base / fminf((float)L.p, (float)R.p)) : 0.0f;
+    const float s3 = sh * sh * sh;
+    info.base = base;
+    info.s3 = s3;
+    info.has_x = ok && sh >= (float)MLP_S_MIN;
+    p0 = base;
+    if (ph.guess == 2 && ph.mlp_w && ok && info.has_x) {
+      bool inbox = true;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) inbox = inbox && info.x[i] >= ph.mlp_box[i] && info.x[i] <= ph.mlp_box[6 + i];
+      v = inbox ? mlp_eval(ph.mlp_w, info.x) : 0.0f;
+      const float y = (float)MLP_T_SCALE * s3 * v;
+      go = inbox && v == v && fabsf(v) <= MLP_VMAX && fabsf(y) <= (float)MLP_YMAX;
+      p0 = (double)(base * expf(y));
+    }
+  }
+  if (ph.guess == 2 && ph.mlp_w && ok) {
+    info.guess = 2;
     if (go) {
       Phys pg = ph;
       pg.max_iter = ph.max_iter < MLP_GUESS_MAX_ITER ? ph.max_iter : MLP_GUESS_MAX_ITER;

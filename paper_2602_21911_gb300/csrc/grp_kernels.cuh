@@ -346,7 +346,7 @@ static __device__ int first_order(const StepArgs& a, long long c0, int N, int bc
   Prim W;
   Phys ph = a.ph;
   ph.guess = GUESS_ADAPTIVE;
-  ph.features = info ? 1 : 0;
+  ph.features = info ? 2 : 0;
   const int st = riemann_state<G75>(ph, QL, QR, true, Q0, W, iters, info);
   if (st != ST_OK && st != ST_VACUUM) return st;
   if (Q0[0] > 0.0) euler_flux(a.ph.gamma, Q0[0], Q0[1], Q0[2], F);
