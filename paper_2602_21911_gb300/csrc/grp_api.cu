@@ -37,6 +37,10 @@ struct grp_ctx {
   DomStep* ds = nullptr;         // per-domain time step of the current step
   double* det_ed = nullptr;      // DET: evolved edge values of every cell
   double* srcv = nullptr;        // numerical source of every cell (source terms only)
+  double* hard_tr = nullptr;     // flux kernel's deferred interfaces: traces, index, counters
+  long long* hard_idx = nullptr;
+  unsigned* hard_count = nullptr;
+  long long hard_cap = 0;
   unsigned char *low = nullptr, *troubled = nullptr;
   double *t = nullptr, *dt_prev = nullptr;
   int *nstep = nullptr, *status = nullptr;
@@ -127,7 +131,8 @@ void free_all(grp_ctx* c)
                   c->ifc[0], c->ifc[1], c->flux, c->pold, c->ds, c->det_ed, c->srcv, c->low, c->troubled, c->t, c->dt_prev, c->nstep,
                   c->status, c->smax_bits, c->bad, c->inad, c->fail, c->any_bad, c->tlist0, c->tlist1,
                   c->ilist, c->lcount, c->stats,
-                  c->scratch_norm, c->mlp, c->mlp_norm, c->grp, c->tiles, c->tile_zeros, c->tile_flag};
+                  c->scratch_norm, c->mlp, c->mlp_norm, c->grp, c->tiles, c->tile_zeros, c->tile_flag,
+                  c->hard_tr, c->hard_idx, c->hard_count};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -184,6 +189,10 @@ StepArgs make_args(const grp_ctx* c, double t_end)
   a.harvest_cap = c->harvest_cap;
   a.harvest_log2_stride = c->harvest_log2_stride;
   a.srcv = c->srcv;
+  a.hard_tr = c->hard_tr;
+  a.hard_idx = c->hard_idx;
+  a.hard_count = c->hard_count;
+  a.hard_cap = (int)c->hard_cap;
   a.ph.src = c->p.source;
   a.ph.src_k = c->p.source_coef;
   return a;
@@ -308,7 +317,7 @@ int enqueue_split(grp_ctx* c, double t_end)
     CK(record(c, e0));
   }
   CK(launch_flux(a, s));
-  c->launches++;
+  c->launches += flux_defers(a) ? 2 : 1;
   if (c->timing) {
     CK(record(c, e1));
     c->ev_pending.push_back(e0);
@@ -440,7 +449,7 @@ int enqueue_step(grp_ctx* c, double t_end)
     c->launches += 3;
   } else {
     CK(c->p.source != GRP_SOURCE_NONE ? launch_flux_src(a, s) : launch_flux(a, s));
-    c->launches++;
+    c->launches += flux_defers(a) ? 2 : 1;
   }
   if (c->timing) {
     CK(record(c, e1));
@@ -575,6 +584,14 @@ int grp_create(grp_ctx** out, const grp_problem* p)
   AL(any_bad, MAX_REPAIR + 1) AL(stats, (long long)NSTATS * D) AL(scratch_norm, 3 * D)
   AL(tlist0, c->ncell) AL(tlist1, c->ncell) AL(ilist, c->nif) AL(lcount, 2 * (MAX_REPAIR + 1))
   if (p->source != GRP_SOURCE_NONE) AL(srcv, (long long)C * c->ncell)
+  if (p->system == GRP_EULER_IDEAL && p->recon == GRP_RECON_GRPREC && p->solver != GRP_SOLVER_DET &&
+      p->source == GRP_SOURCE_NONE && (p->M == 2 || p->M == 4)) {
+    c->hard_cap = hard_list_cap(c->nif);
+    AL(hard_tr, (long long)hard_doubles_per_slot(p->M) * c->hard_cap) AL(hard_idx, c->hard_cap) AL(hard_count, 2)
+    if ((e = cudaMemset(c->hard_count, 0, 2 * sizeof(unsigned))) != cudaSuccess) {
+      free_all(c); delete c; return cuda_fail(e, "cudaMemset hard_count");
+    }
+  }
   if (p->solver == GRP_SOLVER_DET) {
     AL(det_ed, (long long)det_doubles(p->M, C, c->ncell))
     if (det_prepare(p->device) != 0) { free_all(c); delete c; return cuda_fail(cudaErrorUnknown, "DET tables"); }

@@ -6,12 +6,28 @@
 #include "grp_kernels.cuh"
 #include "grp_launch.h"
 
+namespace grp {
+// the second pass of the flux kernel, where the first defers interfaces
+template <int MM, bool NLV>
+inline void launch_flux_hard(const StepArgs& a, cudaStream_t s)
+{
+  if constexpr (flux_defers_at<SYS_EULER, MM, NLV, false>()) {
+    if (a.hard_cap > 0) {
+      const unsigned gh = hard_blocks(a.hard_cap);
+      if (a.ph.gamma == 1.4) k_flux_hard<MM, true><<<gh, GRP_FLUX_TPB, 0, s>>>(a);
+      else k_flux_hard<MM, false><<<gh, GRP_FLUX_TPB, 0, s>>>(a);
+    }
+  }
+}
+}  // namespace grp
+
 #define GRP_DEFINE_EULER_LAUNCHERS(MM, NLV, SUFFIX)                                                          \
   cudaError_t launch_flux_euler_##SUFFIX(const StepArgs& a, cudaStream_t s)                                  \
   {                                                                                                          \
-    const unsigned g = (unsigned)((flux_threads(a.nif) + 127) / 128);                                         \
-    if (a.ph.gamma == 1.4) k_flux<SYS_EULER, MM, true, NLV><<<g, 128, 0, s>>>(a);                            \
-    else k_flux<SYS_EULER, MM, false, NLV><<<g, 128, 0, s>>>(a);                                             \
+    const unsigned g = (unsigned)((flux_threads(a.nif) + GRP_FLUX_TPB - 1) / GRP_FLUX_TPB);                  \
+    if (a.ph.gamma == 1.4) k_flux<SYS_EULER, MM, true, NLV><<<g, GRP_FLUX_TPB, 0, s>>>(a);                   \
+    else k_flux<SYS_EULER, MM, false, NLV><<<g, GRP_FLUX_TPB, 0, s>>>(a);                                    \
+    launch_flux_hard<MM, NLV>(a, s);                                                                         \
     return cudaGetLastError();                                                                               \
   }                                                                                                          \
   cudaError_t launch_batch_euler_##SUFFIX(const BatchLaunch& L, cudaStream_t s)                              \
@@ -28,12 +44,12 @@
 #define GRP_DEFINE_ADV_LAUNCHERS(NLV, SUFFIX)                                                                \
   cudaError_t launch_flux_adv##SUFFIX(const StepArgs& a, cudaStream_t s)                                     \
   {                                                                                                          \
-    const unsigned g = (unsigned)((flux_threads(a.nif) + 127) / 128);                                         \
+    const unsigned g = (unsigned)((flux_threads(a.nif) + GRP_FLUX_TPB - 1) / GRP_FLUX_TPB);                                         \
     switch (a.M) {                                                                                           \
-      case 1: k_flux<SYS_ADV, 1, false, NLV><<<g, 128, 0, s>>>(a); break;                                    \
-      case 2: k_flux<SYS_ADV, 2, false, NLV><<<g, 128, 0, s>>>(a); break;                                    \
-      case 3: k_flux<SYS_ADV, 3, false, NLV><<<g, 128, 0, s>>>(a); break;                                    \
-      case 4: k_flux<SYS_ADV, 4, false, NLV><<<g, 128, 0, s>>>(a); break;                                    \
+      case 1: k_flux<SYS_ADV, 1, false, NLV><<<g, GRP_FLUX_TPB, 0, s>>>(a); break;                                    \
+      case 2: k_flux<SYS_ADV, 2, false, NLV><<<g, GRP_FLUX_TPB, 0, s>>>(a); break;                                    \
+      case 3: k_flux<SYS_ADV, 3, false, NLV><<<g, GRP_FLUX_TPB, 0, s>>>(a); break;                                    \
+      case 4: k_flux<SYS_ADV, 4, false, NLV><<<g, GRP_FLUX_TPB, 0, s>>>(a); break;                                    \
       default: return cudaErrorInvalidValue;                                                                 \
     }                                                                                                        \
     return cudaGetLastError();                                                                               \

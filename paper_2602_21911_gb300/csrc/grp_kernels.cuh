@@ -69,6 +69,13 @@ struct StepArgs {
   int* lcount;                       // [2 (MAX_REPAIR+1)]: troubled cells after pass p-1 at [p];
                                      //   interfaces repaired in round r at [MAX_REPAIR + 1 + r]
   unsigned long long* stats;         // [D][NSTATS]
+  // interfaces of the flux kernel deferred to k_flux_hard (Riemann data that
+  // are not equal data, at the interpolating degrees): their traces and index,
+  // solved in a second pass with dense warps; hard_cap = 0 defers nothing
+  double* hard_tr = nullptr;         // [2 C (M+1)][hard_cap]: tL then tR, coefficient-major
+  long long* hard_idx = nullptr;     // [hard_cap] interface
+  unsigned* hard_count = nullptr;    // [2]: interfaces offered this step, blocks of k_flux_hard done
+  int hard_cap = 0;
   // harvest of (features, ln(p*/pbar), iterations) records, may be null
   float* harvest;                    // [harvest_cap][8]
   unsigned long long* harvest_count; // records offered (may exceed the capacity)
@@ -500,6 +507,9 @@ __host__ __device__ constexpr long long flux_threads(long long nif) { return (ni
 #ifndef GRP_FLUX_MIN_BLOCKS
 #define GRP_FLUX_MIN_BLOCKS 3
 #endif
+#ifndef GRP_FLUX_TPB
+#define GRP_FLUX_TPB 128
+#endif
 // The numerical source of cell `cell` (SRC kernels): its reconstruction
 // coefficients again (linear GRPrec; degree 0 when its traces were
 // inadmissible), then the source average of its own evolution.
@@ -537,7 +547,10 @@ __device__ __forceinline__ void cell_source(const StepArgs& a, long long c0, lon
 // of the warp call it (shuffles and warp statistics).
 // own0 <= gj < own1: the interfaces whose statistics count (a tile's halo
 // interfaces are computed but counted by the tile that owns them).
-template <int SYS, int M, bool G75, bool NL, bool SRC>
+// DEFER: an interface whose two traces are not equal data (a Newton solve,
+// in one or two lanes of a warp while the others wait) is written to the
+// hard list instead, when a slot is left, and solved by k_flux_hard.
+template <int SYS, int M, bool G75, bool NL, bool SRC, bool DEFER = false>
 __device__ __forceinline__ void flux_warp(const StepArgs& a, long long gbase, long long gend, long long own0 = 0,
                                           long long own1 = 0x7fffffffffffffffll)
 {
@@ -575,6 +588,8 @@ __device__ __forceinline__ void flux_warp(const StepArgs& a, long long gbase, lo
   for (int c = 0; c < C; ++c)
 #pragma unroll
     for (int k = 0; k <= M; ++k) rm[c][k] = __shfl_down_sync(0xffffffffu, em[c][k], 1);
+  double tL[C][M + 1], tR[C][M + 1];
+  bool solve = false, hard = false;
   if (lane < 31 && gj < gend) {
     if (!active) {
 #pragma unroll
@@ -582,7 +597,6 @@ __device__ __forceinline__ void flux_warp(const StepArgs& a, long long gbase, lo
     } else {
       // both traces by register moves (ghost states at transmissive ends), so
       // that the lanes of a warp reach the one GRP below together
-      double tL[C][M + 1], tR[C][M + 1];
       if (cl >= 0) st[5] = fb ? 1u : 0u;       // counted once per cell: at its right interface
       const double* gl = a.avg + c0;                 // the ghost left of cell 0
       const double* gr = a.avg + c0 + N - 1;         // the ghost right of cell N - 1
@@ -610,21 +624,121 @@ __device__ __forceinline__ void flux_warp(const StepArgs& a, long long gbase, lo
 #pragma unroll
         for (int k = 1; k <= M; ++k) tR[c][k] = ghost_r ? 0.0 : rm[c][k];
       }
-      grp_at<SYS, M, G75, SRC>(a, gj, d, c0, N, bc, j, tL, tR, st);
+      solve = true;
+      if (DEFER && a.hard_cap > 0) {
+        const double QL[3] = {tL[0][0], tL[1][0], tL[2][0]}, QR[3] = {tR[0][0], tR[1][0], tR[2][0]};
+        hard = !equal_data(QL, QR);
+      }
     }
   } else {
     d = -1;
   }
+  if (DEFER) {
+    // warp-aggregated slots of the hard list (consecutive per warp)
+    const unsigned bal = __ballot_sync(0xffffffffu, hard);
+    if (bal) {
+      const int lead = __ffs(bal) - 1;
+      unsigned base = 0;
+      if (lane == lead) base = atomicAdd(a.hard_count, (unsigned)__popc(bal));
+      base = __shfl_sync(0xffffffffu, base, lead);
+      const unsigned slot = base + (unsigned)__popc(bal & ((1u << lane) - 1u));
+      if (hard && slot < (unsigned)a.hard_cap) {
+        double* R = a.hard_tr + slot;
+        const long long cap = a.hard_cap;
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+          for (int k = 0; k <= M; ++k) {
+            R[(c * (M + 1) + k) * cap] = tL[c][k];
+            R[(C * (M + 1) + c * (M + 1) + k) * cap] = tR[c][k];
+          }
+        a.hard_idx[slot] = gj;
+        solve = false;
+      }
+    }
+  }
+  if (solve) grp_at<SYS, M, G75, SRC>(a, gj, d, c0, N, bc, j, tL, tR, st);
   __syncwarp();
   if (SYS == SYS_EULER) {
     warp_flux_stats(a.stats, gj >= own0 && gj < own1 ? d : -1, st, a.ph.guess == 2);
   }
 }
 
-template <int SYS, int M, bool G75, bool NL, bool SRC = false>
-__global__ void __launch_bounds__(128, GRP_FLUX_MIN_BLOCKS) k_flux(StepArgs a)
+// Interfaces are deferred at the interpolating degrees (2 and 4) of the
+// linear reconstruction, where all but a few interfaces have equal data.
+template <int SYS, int M, bool NL, bool SRC>
+__host__ __device__ constexpr bool flux_defers_at()
 {
-  flux_warp<SYS, M, G75, NL, SRC>(a, (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 31, a.nif);
+  return SYS == SYS_EULER && !NL && !SRC && (M == 2 || M == 4);
+}
+
+template <int SYS, int M, bool G75, bool NL, bool SRC = false>
+__global__ void __launch_bounds__(GRP_FLUX_TPB, GRP_FLUX_MIN_BLOCKS) k_flux(StepArgs a)
+{
+  flux_warp<SYS, M, G75, NL, SRC, flux_defers_at<SYS, M, NL, SRC>()>(
+      a, (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 31, a.nif);
+}
+
+// Capacity and grid of the hard list, and whether a step's flux phase is two
+// launches.  The list holds a quarter of the interfaces (plus 1024): the
+// interfaces left over when it is full are solved in the first pass.
+inline long long hard_list_cap(long long nif) { return nif / 4 + 1024; }
+inline size_t hard_doubles_per_slot(int M) { return (size_t)2 * 3 * (M + 1); }
+inline unsigned hard_blocks(long long cap)
+{
+  const long long b = (cap + GRP_FLUX_TPB - 1) / GRP_FLUX_TPB;
+  return (unsigned)(b < 2048 ? b : 2048);
+}
+inline bool flux_defers(const StepArgs& a)
+{
+  return a.sys == SYS_EULER && a.recon == 0 && !a.srcv && (a.M == 2 || a.M == 4) && a.hard_cap > 0;
+}
+
+// The second pass of the flux kernel: the deferred interfaces, one per lane
+// (warps stride over the list together, so the warp statistics see full
+// warps).  The last block to finish resets the list for the next step; every
+// block has read the count before it counts itself done.
+template <int M, bool G75>
+__global__ void __launch_bounds__(GRP_FLUX_TPB, GRP_FLUX_MIN_BLOCKS) k_flux_hard(StepArgs a)
+{
+  constexpr int C = 3;
+  const unsigned offered = a.hard_count[0];
+  const long long n = offered < (unsigned)a.hard_cap ? offered : a.hard_cap;
+  const int lane = lane_id();
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long b = w0 * 32; b < n; b += nw * 32) {
+    const long long i = b + lane;
+    unsigned st[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    int d = -1;
+    if (i < n) {
+      const long long gj = a.hard_idx[i];
+      d = a.if_dom[gj];
+      const long long i0 = a.if_off[d], c0 = a.cell_off[d];
+      const int N = (int)(a.cell_off[d + 1] - c0);
+      double tL[C][M + 1], tR[C][M + 1];
+      const double* R = a.hard_tr + i;
+      const long long cap = a.hard_cap;
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int k = 0; k <= M; ++k) {
+          tL[c][k] = R[(c * (M + 1) + k) * cap];
+          tR[c][k] = R[(C * (M + 1) + c * (M + 1) + k) * cap];
+        }
+      grp_at<SYS_EULER, M, G75, false>(a, gj, d, c0, N, a.bc[d], (int)(gj - i0), tL, tR, st);
+    }
+    __syncwarp();
+    warp_flux_stats(a.stats, d, st, a.ph.guess == 2);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(a.hard_count + 1, 1u) == gridDim.x - 1) {
+      a.hard_count[0] = 0u;
+      a.hard_count[1] = 0u;
+    }
+  }
 }
 
 // ------------------------------------------------------------------ update

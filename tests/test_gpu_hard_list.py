@@ -1,0 +1,48 @@
+"""The flux kernel's second pass (degrees 2 and 4 of the Euler equations).
+
+Interfaces whose Riemann data are not equal data are deferred by the first
+pass to a list of nif/4 + 1024 interfaces and solved by a second kernel; when
+the list is full, the rest are solved in the first pass.  These runs make the
+list overflow: smooth transmissive domains of 4 to 5 cells, whose two boundary
+interfaces (the trace against the ghost cell) never have equal data, so more
+than a third of all interfaces are deferred.  Parity with the oracle and the
+per-domain counters must hold across both paths."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2602_21911_gb300 import inputs as I
+
+from parity import DISC_TOL, check_parity
+
+pytestmark = pytest.mark.gpu
+
+
+def _tiny_smooth_ids():
+    P = I.batched_params()
+    return np.flatnonzero(P["smooth"] & (P["n"] <= 5))
+
+
+@pytest.mark.parametrize("M", [2, 4])
+def test_overflowing_hard_list_matches_the_oracle(M):
+    ids = _tiny_smooth_ids()
+    prob, avg, lm, lp = I.batched(M=M, domains=ids)
+    nif = I.n_ifaces(prob)
+    # the precondition of the overflow: two deferred interfaces per domain
+    # exceed the list's capacity
+    assert 2 * len(ids) > nif // 4 + 1024
+    S, (a, g, t, stats, status), rd = check_parity(prob, avg, lm, lp, 40, DISC_TOL)
+    ok = S.status == 0
+    for k in (O.ST_RS_CALLS, O.ST_RECON_FB, O.ST_LOW_ORDER, O.ST_FLUX_FB):
+        assert np.array_equal(stats[ok, k].astype(np.int64), S.stats[ok, k]), k
+
+
+def test_hard_list_mixed_with_long_domains():
+    """Tiny smooth domains between long shock tubes of the batch: deferred and
+    first-pass interfaces of the same warps, list overflowing."""
+    tiny = _tiny_smooth_ids()
+    P = I.batched_params()
+    long_rp = np.flatnonzero(~P["smooth"] & (P["n"] >= 300))[:40]
+    ids = np.sort(np.concatenate([tiny, long_rp]))
+    prob, avg, lm, lp = I.batched(M=2, domains=ids)
+    check_parity(prob, avg, lm, lp, 30, DISC_TOL)
