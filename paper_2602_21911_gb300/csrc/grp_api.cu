@@ -587,8 +587,8 @@ int grp_create(grp_ctx** out, const grp_problem* p)
   if (p->system == GRP_EULER_IDEAL && p->recon == GRP_RECON_GRPREC && p->solver != GRP_SOLVER_DET &&
       p->source == GRP_SOURCE_NONE && (p->M == 2 || p->M == 4)) {
     c->hard_cap = hard_list_cap(c->nif);
-    AL(hard_tr, (long long)hard_doubles_per_slot(p->M) * c->hard_cap) AL(hard_idx, c->hard_cap) AL(hard_count, 2)
-    if ((e = cudaMemset(c->hard_count, 0, 2 * sizeof(unsigned))) != cudaSuccess) {
+    AL(hard_tr, (long long)hard_doubles_per_slot(p->M) * c->hard_cap) AL(hard_idx, c->hard_cap) AL(hard_count, 3)
+    if ((e = cudaMemset(c->hard_count, 0, 3 * sizeof(unsigned))) != cudaSuccess) {
       free_all(c); delete c; return cuda_fail(e, "cudaMemset hard_count");
     }
   }

@@ -13,9 +13,14 @@ inline void launch_flux_hard(const StepArgs& a, cudaStream_t s)
 {
   if constexpr (flux_defers_at<SYS_EULER, MM, NLV, false>()) {
     if (a.hard_cap > 0) {
-      const unsigned gh = hard_blocks(a.hard_cap);
-      if (a.ph.gamma == 1.4) k_flux_hard<MM, true><<<gh, GRP_FLUX_TPB, 0, s>>>(a);
-      else k_flux_hard<MM, false><<<gh, GRP_FLUX_TPB, 0, s>>>(a);
+      static int sms[64] = {0};
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (dev < 0 || dev >= 64) dev = 0;
+      if (!sms[dev]) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+      const unsigned gh = hard_blocks(a.hard_cap, sms[dev] > 0 ? sms[dev] : 1);
+      if (a.ph.gamma == 1.4) k_flux_hard<MM, true><<<gh, GRP_HARD_TPB, 0, s>>>(a);
+      else k_flux_hard<MM, false><<<gh, GRP_HARD_TPB, 0, s>>>(a);
     }
   }
 }

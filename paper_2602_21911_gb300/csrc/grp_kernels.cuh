@@ -74,7 +74,8 @@ struct StepArgs {
   // solved in a second pass with dense warps; hard_cap = 0 defers nothing
   double* hard_tr = nullptr;         // [2 C (M+1)][hard_cap]: tL then tR, coefficient-major
   long long* hard_idx = nullptr;     // [hard_cap] interface
-  unsigned* hard_count = nullptr;    // [2]: interfaces offered this step, blocks of k_flux_hard done
+  unsigned* hard_count = nullptr;    // [3]: interfaces offered this step, blocks of k_flux_hard done,
+                                     //   interfaces taken by k_flux_hard
   int hard_cap = 0;
   // harvest of (features, ln(p*/pbar), iterations) records, may be null
   float* harvest;                    // [harvest_cap][8]
@@ -679,36 +680,50 @@ __global__ void __launch_bounds__(GRP_FLUX_TPB, GRP_FLUX_MIN_BLOCKS) k_flux(Step
       a, (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 31, a.nif);
 }
 
-// Capacity and grid of the hard list, and whether a step's flux phase is two
-// launches.  The list holds a quarter of the interfaces (plus 1024): the
-// interfaces left over when it is full are solved in the first pass.
+// Capacity of the hard list and whether a step's flux phase is two launches.
+// The list holds a quarter of the interfaces (plus 1024): the interfaces left
+// over when it is full are solved in the first pass.
 inline long long hard_list_cap(long long nif) { return nif / 4 + 1024; }
 inline size_t hard_doubles_per_slot(int M) { return (size_t)2 * 3 * (M + 1); }
-inline unsigned hard_blocks(long long cap)
-{
-  const long long b = (cap + GRP_FLUX_TPB - 1) / GRP_FLUX_TPB;
-  return (unsigned)(b < 2048 ? b : 2048);
-}
 inline bool flux_defers(const StepArgs& a)
 {
   return a.sys == SYS_EULER && a.recon == 0 && !a.srcv && (a.M == 2 || a.M == 4) && a.hard_cap > 0;
 }
 
+// The second pass runs one warp per block, so that a warp that finishes frees
+// its slot at once (the pass is bound by the latency of its longest Newton
+// chains, not by the FP64 pipe), and the warps take chunks of 32 interfaces
+// from a counter until the list is done.
+#ifndef GRP_HARD_TPB
+#define GRP_HARD_TPB 32
+#endif
+#ifndef GRP_HARD_MIN_BLOCKS
+#define GRP_HARD_MIN_BLOCKS 12
+#endif
+inline unsigned hard_blocks(long long cap, int sms)
+{
+  const long long need = (cap + GRP_HARD_TPB - 1) / GRP_HARD_TPB;
+  const long long fill = 2ll * sms * GRP_HARD_MIN_BLOCKS;
+  return (unsigned)(need < fill ? need : fill);
+}
+
 // The second pass of the flux kernel: the deferred interfaces, one per lane
-// (warps stride over the list together, so the warp statistics see full
-// warps).  The last block to finish resets the list for the next step; every
-// block has read the count before it counts itself done.
+// (a warp takes its chunk together, so the warp statistics see full warps).
+// The last block to finish resets the list for the next step; every block
+// has read the count before it counts itself done.
 template <int M, bool G75>
-__global__ void __launch_bounds__(GRP_FLUX_TPB, GRP_FLUX_MIN_BLOCKS) k_flux_hard(StepArgs a)
+__global__ void __launch_bounds__(GRP_HARD_TPB, GRP_HARD_MIN_BLOCKS) k_flux_hard(StepArgs a)
 {
   constexpr int C = 3;
   const unsigned offered = a.hard_count[0];
   const long long n = offered < (unsigned)a.hard_cap ? offered : a.hard_cap;
   const int lane = lane_id();
-  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long b = w0 * 32; b < n; b += nw * 32) {
-    const long long i = b + lane;
+  for (;;) {
+    unsigned b = 0;
+    if (lane == 0) b = atomicAdd(a.hard_count + 2, 32u);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if ((long long)b >= n) break;
+    const long long i = (long long)b + lane;
     unsigned st[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     int d = -1;
     if (i < n) {
@@ -737,6 +752,7 @@ __global__ void __launch_bounds__(GRP_FLUX_TPB, GRP_FLUX_MIN_BLOCKS) k_flux_hard
     if (atomicAdd(a.hard_count + 1, 1u) == gridDim.x - 1) {
       a.hard_count[0] = 0u;
       a.hard_count[1] = 0u;
+      a.hard_count[2] = 0u;
     }
   }
 }
