@@ -671,6 +671,41 @@ GRP_HD inline float mlp_eval(const float* __restrict__ w, const float x[6])
   return y;
 }
 
+// The network for one input x (the same in every lane of the warp), evaluated
+// by the whole warp: each lane computes hidden units lane and lane + 32 of
+// both layers, the output is a warp sum.  hs: 64 floats of shared memory of
+// this warp.  Called by all 32 lanes, converged.
+__device__ __forceinline__ float mlp_eval_warp(const float* __restrict__ w, const float x[6], float* hs)
+{
+  const float* W1 = w;
+  const float* b1 = W1 + MLP_NIN * MLP_NH;
+  const float* W2 = b1 + MLP_NH;
+  const float* b2 = W2 + MLP_NH * MLP_NH;
+  const float* w3 = b2 + MLP_NH;
+  const int l = threadIdx.x & 31;
+  float z0 = b1[l], z1 = b1[l + 32];
+#pragma unroll
+  for (int i = 0; i < MLP_NIN; ++i) {
+    z0 = fmaf(x[i], W1[i * MLP_NH + l], z0);
+    z1 = fmaf(x[i], W1[i * MLP_NH + l + 32], z1);
+  }
+  hs[l] = fast_tanh(z0);
+  hs[l + 32] = fast_tanh(z1);
+  __syncwarp();
+  float y0 = b2[l], y1 = b2[l + 32];
+#pragma unroll 8
+  for (int j = 0; j < MLP_NH; ++j) {
+    const float h = hs[j];
+    y0 = fmaf(h, W2[j * MLP_NH + l], y0);
+    y1 = fmaf(h, W2[j * MLP_NH + l + 32], y1);
+  }
+  float y = fmaf(fast_tanh(y0), w3[l], fast_tanh(y1) * w3[l + 32]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) y += __shfl_xor_sync(0xffffffffu, y, off);
+  __syncwarp();                                  // hs is reused by the next call
+  return y + w3[MLP_NH];
+}
+
 struct RSInfo {
   double ps = 0.0;               // star pressure
   double base = 0.0;             // two-rarefaction estimate (the base of the learned correction)
@@ -679,6 +714,31 @@ struct RSInfo {
   bool has_x = false;            // strong data with a shock of strength >= MLP_S_MIN
   int guess = 0;                 // 0 not tried, 1 network start used, 2 rejected, 3 p_TR start (two rarefactions)
 };
+
+// The inference form's decisions for strong data, in FP32 (features x, the
+// two-rarefaction base, the cube of the shock strength): whether the start
+// comes from the network (the returned value) and the input-box test.
+struct LearnedPrep {
+  float base, s3;
+  bool ok, has_x, inbox;
+};
+
+GRP_HD __forceinline__ bool learned_prep_f32(const Phys& ph, const Side& L, const Side& R, float x[6],
+                                             LearnedPrep& q)
+{
+  mlp_features(ph, L, R, x);
+  q.base = trrs_f32(ph, L, R);
+  q.ok = q.base > 0.0f && isfinite(q.base);
+  const float sh = q.ok ? logf(q.base / fminf((float)L.p, (float)R.p)) : 0.0f;
+  q.s3 = sh * sh * sh;
+  q.has_x = q.ok && sh >= (float)MLP_S_MIN;
+  q.inbox = true;
+  if (ph.guess == 2 && ph.mlp_w && q.has_x) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) q.inbox = q.inbox && x[i] >= ph.mlp_box[i] && x[i] <= ph.mlp_box[6 + i];
+  }
+  return ph.guess == 2 && ph.mlp_w && q.has_x && q.inbox;
+}
 
 // The learned-guess path of riemann_state for strong data: features, the
 // two-rarefaction base and, for data with a shock, the network; Newton from
@@ -692,14 +752,15 @@ __device__ __noinline__
 #else
 inline
 #endif
-int learned_start(const Phys& ph, const Side& L, const Side& R, RSInfo& info, double& ps, double& us, int& iters)
+int learned_start(const Phys& ph, const Side& L, const Side& R, RSInfo& info, double& ps, double& us, int& iters,
+                  const float* vpre)
 {
   int st = -1;
-  mlp_features(ph, L, R, info.x);
   double p0 = 0.0;
   bool ok, go = true;
   float v = 0.0f;
   if (ph.features == 2) {
+    mlp_features(ph, L, R, info.x);
     // harvest: the record's target ln(p*/p_TR) / (MLP_T_SCALE s^3) needs p_TR
     // and the strength in FP64 (for weak shocks the correction is ~1e-12)
     const double base = trrs<G75>(ph, L, R);
@@ -722,23 +783,20 @@ int learned_start(const Phys& ph, const Side& L, const Side& R, RSInfo& info, do
     }
   } else {
     // inference: the start in FP32 (the same decisions and correction; Newton
-    // converges from it to the same p*)
-    const float base = trrs_f32(ph, L, R);
-    ok = base > 0.0f && isfinite(base);
-    const float sh = ok ? logf(base / fminf((float)L.p, (float)R.p)) : 0.0f;
-    const float s3 = sh * sh * sh;
-    info.base = base;
-    info.s3 = s3;
-    info.has_x = ok && sh >= (float)MLP_S_MIN;
-    p0 = base;
+    // converges from it to the same p*).  vpre: the network's output for these
+    // features, evaluated beforehand by the whole warp (learned_warp_outputs)
+    LearnedPrep q;
+    learned_prep_f32(ph, L, R, info.x, q);
+    ok = q.ok;
+    info.base = q.base;
+    info.s3 = q.s3;
+    info.has_x = q.has_x;
+    p0 = q.base;
     if (ph.guess == 2 && ph.mlp_w && ok && info.has_x) {
-      bool inbox = true;
-#pragma unroll
-      for (int i = 0; i < 6; ++i) inbox = inbox && info.x[i] >= ph.mlp_box[i] && info.x[i] <= ph.mlp_box[6 + i];
-      v = inbox ? mlp_eval(ph.mlp_w, info.x) : 0.0f;
-      const float y = (float)MLP_T_SCALE * s3 * v;
-      go = inbox && v == v && fabsf(v) <= MLP_VMAX && fabsf(y) <= (float)MLP_YMAX;
-      p0 = (double)(base * expf(y));
+      v = q.inbox ? (vpre ? *vpre : mlp_eval(ph.mlp_w, info.x)) : 0.0f;
+      const float y = (float)MLP_T_SCALE * q.s3 * v;
+      go = q.inbox && v == v && fabsf(v) <= MLP_VMAX && fabsf(y) <= (float)MLP_YMAX;
+      p0 = (double)(q.base * expf(y));
     }
   }
   if (ph.guess == 2 && ph.mlp_w && ok) {
@@ -761,16 +819,14 @@ int learned_start(const Phys& ph, const Side& L, const Side& R, RSInfo& info, do
 // convergence within MLP_GUESS_MAX_ITER iterations falls back to PVRS
 // (iterations add up).
 template <bool G75>
-static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double QR[3], bool allow_vacuum,
-                                double Q[3], Prim& W, int& iters, RSInfo* info = nullptr)
+static GRP_HD int riemann_sides(const Phys& ph, const Side& L, const Side& R, bool allow_vacuum, double Q[3],
+                                Prim& W, int& iters, RSInfo* info, const float* vpre = nullptr)
 {
-  const Side L = make_side(ph, QL);
-  const Side R = make_side(ph, QR);
   double ps = 0.0, us = 0.0;
   int st = -1;
   iters = 0;
   // the learned-guess path (out of line) only for strong data
-  if (ph.features && info && strong_data(ph, L, R)) st = learned_start<G75>(ph, L, R, *info, ps, us, iters);
+  if (ph.features && info && strong_data(ph, L, R)) st = learned_start<G75>(ph, L, R, *info, ps, us, iters, vpre);
   if (st != ST_OK && st != ST_VACUUM) {
     int it2 = 0;
     Phys pv = ph;
@@ -789,6 +845,24 @@ static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double
   to_cons(ph, W, Q);
   return ST_OK;
 }
+
+template <bool G75>
+static GRP_HD int riemann_state(const Phys& ph, const double QL[3], const double QR[3], bool allow_vacuum,
+                                double Q[3], Prim& W, int& iters, RSInfo* info = nullptr)
+{
+  const Side L = make_side(ph, QL);
+  const Side R = make_side(ph, QR);
+  return riemann_sides<G75>(ph, L, R, allow_vacuum, Q, W, iters, info);
+}
+
+// A leading Riemann problem solved before its GRP (the second flux pass solves
+// them with the network's starts evaluated by whole warps).
+struct Lead {
+  int st, iters;
+  double Q0[3];
+  Prim W0;
+  RSInfo info;
+};
 
 // ---------------------------------------------------------------------------
 // Derivative Riemann problem (Toro-Titarev, Section 2): the linear system
@@ -1090,7 +1164,8 @@ GRP_HD __forceinline__ void grp_adv(double lam, double nu, const double tL[M + 1
 template <int M, bool G75, bool SRC = false>
 GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[3][M + 1],
                                      const double tR[3][M + 1], double F[3], double gnew[3], int& iters,
-                                     bool& truncated, RSInfo* info = nullptr, double hs = 0.0)
+                                     bool& truncated, RSInfo* info = nullptr, double hs = 0.0,
+                                     const Lead* lead = nullptr)
 {
   const double g = ph.gamma;
   const double QL[3] = {tL[0][0], tL[1][0], tL[2][0]}, QR[3] = {tR[0][0], tR[1][0], tR[2][0]};
@@ -1098,7 +1173,15 @@ GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[
   Prim W0;
   double ir0;
   truncated = false;
-  if (equal_data(QL, QR)) {
+  if (lead) {
+    // the leading Riemann problem solved by the caller
+    iters = lead->iters;
+    if (info) *info = lead->info;
+    if (lead->st != ST_OK) return lead->st;
+    Q0[0] = lead->Q0[0]; Q0[1] = lead->Q0[1]; Q0[2] = lead->Q0[2];
+    W0 = lead->W0;
+    ir0 = rcp64(W0.r);
+  } else if (equal_data(QL, QR)) {
     // equal data: the exact solution is the constant state, no Newton (the
     // traces are admissible: an inadmissible one sends its cell to degree 0)
     Q0[0] = QL[0]; Q0[1] = QL[1]; Q0[2] = QL[2];

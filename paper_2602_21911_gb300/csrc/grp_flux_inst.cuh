@@ -19,8 +19,14 @@ inline void launch_flux_hard(const StepArgs& a, cudaStream_t s)
       if (dev < 0 || dev >= 64) dev = 0;
       if (!sms[dev]) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
       const unsigned gh = hard_blocks(a.hard_cap, sms[dev] > 0 ? sms[dev] : 1);
-      if (a.ph.gamma == 1.4) k_flux_hard<MM, true><<<gh, GRP_HARD_TPB, 0, s>>>(a);
-      else k_flux_hard<MM, false><<<gh, GRP_HARD_TPB, 0, s>>>(a);
+      const bool net = flux_hard_net(a);
+      if (a.ph.gamma == 1.4) {
+        if (net) k_flux_hard<MM, true, true><<<gh, GRP_HARD_TPB, 0, s>>>(a);
+        else k_flux_hard<MM, true, false><<<gh, GRP_HARD_TPB, 0, s>>>(a);
+      } else {
+        if (net) k_flux_hard<MM, false, true><<<gh, GRP_HARD_TPB, 0, s>>>(a);
+        else k_flux_hard<MM, false, false><<<gh, GRP_HARD_TPB, 0, s>>>(a);
+      }
     }
   }
 }

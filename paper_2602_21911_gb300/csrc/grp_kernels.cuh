@@ -450,9 +450,11 @@ __device__ __forceinline__ void harvest_record(const StepArgs& a, long long gj, 
 // of the two one-sided reconstructions (tL: left cell at its right edge, tR:
 // right cell at its left edge): flux, new interface datum, statistics.
 // SRC: the GRP with the source term (eq. eq:GRP): its series carries dx S.
+// lead: the leading Riemann problem, solved by the caller (or null).
 template <int SYS, int M, bool G75, bool SRC = false>
 __device__ __forceinline__ void grp_at(const StepArgs& a, long long gj, int d, long long c0, int N, int bc, int j,
-                                       const double tL[][M + 1], const double tR[][M + 1], unsigned st[8])
+                                       const double tL[][M + 1], const double tR[][M + 1], unsigned st[8],
+                                       const Lead* lead = nullptr)
 {
   constexpr int C = SYS == SYS_EULER ? 3 : 1;
   a.low[gj] = 0;
@@ -465,7 +467,7 @@ __device__ __forceinline__ void grp_at(const StepArgs& a, long long gj, int d, l
     int iters = 0;
     bool trunc = false;
     RSInfo info;
-    int rs_st = grp_euler<M, G75, SRC>(a.ph, nu, tL, tR, F, gnew, iters, trunc, &info, hsrc);
+    int rs_st = grp_euler<M, G75, SRC>(a.ph, nu, tL, tR, F, gnew, iters, trunc, &info, hsrc, lead);
     st[2] = 1;
     st[3] = trunc ? 1u : 0u;
     st[6] = info.guess == 1 ? 1u : 0u;
@@ -685,6 +687,7 @@ __global__ void __launch_bounds__(GRP_FLUX_TPB, GRP_FLUX_MIN_BLOCKS) k_flux(Step
 // over when it is full are solved in the first pass.
 inline long long hard_list_cap(long long nif) { return nif / 4 + 1024; }
 inline size_t hard_doubles_per_slot(int M) { return (size_t)2 * 3 * (M + 1); }
+inline bool flux_hard_net(const StepArgs& a) { return a.ph.features == 1 && a.ph.guess == 2 && a.ph.mlp_w; }
 inline bool flux_defers(const StepArgs& a)
 {
   return a.sys == SYS_EULER && a.recon == 0 && !a.srcv && (a.M == 2 || a.M == 4) && a.hard_cap > 0;
@@ -711,13 +714,17 @@ inline unsigned hard_blocks(long long cap, int sms)
 // (a warp takes its chunk together, so the warp statistics see full warps).
 // The last block to finish resets the list for the next step; every block
 // has read the count before it counts itself done.
-template <int M, bool G75>
+// NET: the learned start's network is evaluated by the whole warp for each
+// lane that wants it (inference with a model; harvest and the classical starts
+// take the plain instantiation).
+template <int M, bool G75, bool NET>
 __global__ void __launch_bounds__(GRP_HARD_TPB, GRP_HARD_MIN_BLOCKS) k_flux_hard(StepArgs a)
 {
   constexpr int C = 3;
   const unsigned offered = a.hard_count[0];
   const long long n = offered < (unsigned)a.hard_cap ? offered : a.hard_cap;
   const int lane = lane_id();
+  __shared__ float hs[NET ? GRP_HARD_TPB / 32 : 1][MLP_NH];
   for (;;) {
     unsigned b = 0;
     if (lane == 0) b = atomicAdd(a.hard_count + 2, 32u);
@@ -726,12 +733,11 @@ __global__ void __launch_bounds__(GRP_HARD_TPB, GRP_HARD_MIN_BLOCKS) k_flux_hard
     const long long i = (long long)b + lane;
     unsigned st[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     int d = -1;
+    long long gj = 0;
+    double tL[C][M + 1], tR[C][M + 1];
     if (i < n) {
-      const long long gj = a.hard_idx[i];
+      gj = a.hard_idx[i];
       d = a.if_dom[gj];
-      const long long i0 = a.if_off[d], c0 = a.cell_off[d];
-      const int N = (int)(a.cell_off[d + 1] - c0);
-      double tL[C][M + 1], tR[C][M + 1];
       const double* R = a.hard_tr + i;
       const long long cap = a.hard_cap;
 #pragma unroll
@@ -741,6 +747,38 @@ __global__ void __launch_bounds__(GRP_HARD_TPB, GRP_HARD_MIN_BLOCKS) k_flux_hard
           tL[c][k] = R[(c * (M + 1) + k) * cap];
           tR[c][k] = R[(C * (M + 1) + c * (M + 1) + k) * cap];
         }
+    }
+    if (NET) {
+      Side L, R;
+      float x[6], v = 0.0f;
+      bool want = false;
+      if (d >= 0) {
+        const double QL[3] = {tL[0][0], tL[1][0], tL[2][0]}, QR[3] = {tR[0][0], tR[1][0], tR[2][0]};
+        L = make_side(a.ph, QL);
+        R = make_side(a.ph, QR);
+        LearnedPrep q;
+        want = strong_data(a.ph, L, R) && learned_prep_f32(a.ph, L, R, x, q);
+      }
+      unsigned m = __ballot_sync(0xffffffffu, want);
+      while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1u;
+        float xs[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) xs[k] = __shfl_sync(0xffffffffu, x[k], src);
+        const float y = mlp_eval_warp(a.ph.mlp_w, xs, hs[threadIdx.x >> 5]);
+        if (lane == src) v = y;
+      }
+      if (d >= 0) {
+        Lead ld;
+        ld.st = riemann_sides<G75>(a.ph, L, R, false, ld.Q0, ld.W0, ld.iters, &ld.info, &v);
+        const long long i0 = a.if_off[d], c0 = a.cell_off[d];
+        const int N = (int)(a.cell_off[d + 1] - c0);
+        grp_at<SYS_EULER, M, G75, false>(a, gj, d, c0, N, a.bc[d], (int)(gj - i0), tL, tR, st, &ld);
+      }
+    } else if (d >= 0) {
+      const long long i0 = a.if_off[d], c0 = a.cell_off[d];
+      const int N = (int)(a.cell_off[d + 1] - c0);
       grp_at<SYS_EULER, M, G75, false>(a, gj, d, c0, N, a.bc[d], (int)(gj - i0), tL, tR, st);
     }
     __syncwarp();
