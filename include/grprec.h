@@ -214,7 +214,7 @@ int grp_error_norms(grp_ctx *ctx, const double *exact_averages, int ptr_is_devic
  *                     DET or a source term.  A domain that fits one region is
  *                     one tile.  Rejected when a region does not fit 227 KB of
  *                     shared memory.
- *   GRP_LAUNCH_AUTO:  SPLIT for >= 1024 domains of <= 4096 cells, else FLAT.
+ *   GRP_LAUNCH_AUTO:  FLAT (DET solver and source terms: always FLAT).
  * threads: 128 or 256 per block (FUSED, SPLIT); cells_per_block in [64, 2^20];
  * steps_per_launch in [1, 1024] (FUSED).  Synchronises the stream.  Defaults:
  * AUTO, 256, 2048, 8.  grp_get_launch reports the form grp_step will take

@@ -242,8 +242,9 @@ int launch_form(const grp_ctx* c)
   // the tiled form holds dt over its steps: dt_hold must equal the steps per launch
   if (c->mode == GRP_LAUNCH_TILED) return c->p.dt_hold == c->steps_per_launch ? GRP_LAUNCH_TILED : GRP_LAUNCH_FLAT;
   if (c->mode != GRP_LAUNCH_AUTO) return c->mode;
-  // auto: whole domains per block pay off when the batch has many short domains
-  return c->D >= 1024 && c->max_cells <= 4096 ? GRP_LAUNCH_SPLIT : GRP_LAUNCH_FLAT;
+  // auto: the flat form (on the batched workload it measured fastest of the
+  // four: its grid-wide kernels and compacted lists keep warps full)
+  return GRP_LAUNCH_FLAT;
 }
 
 bool use_batch(const grp_ctx* c) { return launch_form(c) != GRP_LAUNCH_FLAT; }

@@ -23,15 +23,27 @@ def _tiny_smooth_ids():
     return np.flatnonzero(P["smooth"] & (P["n"] <= 5))
 
 
+def _solver(prob, form):
+    from paper_2602_21911_gb300 import grprec
+    s = grprec.Solver(prob)
+    s.set_launch(form)
+    return s
+
+
+@pytest.mark.parametrize("form", ["flat", "split"])
 @pytest.mark.parametrize("M", [2, 4])
-def test_overflowing_hard_list_matches_the_oracle(M):
+def test_overflowing_hard_list_matches_the_oracle(M, form):
+    """flat: the flux phase, then the grid-wide update and repair kernels;
+    split: the flux phase, then the per-group kernel."""
+    from paper_2602_21911_gb300 import grprec
     ids = _tiny_smooth_ids()
     prob, avg, lm, lp = I.batched(M=M, domains=ids)
     nif = I.n_ifaces(prob)
     # the precondition of the overflow: two deferred interfaces per domain
     # exceed the list's capacity
     assert 2 * len(ids) > nif // 4 + 1024
-    S, (a, g, t, stats, status), rd = check_parity(prob, avg, lm, lp, 40, DISC_TOL)
+    f = grprec.GRP_LAUNCH_FLAT if form == "flat" else grprec.GRP_LAUNCH_SPLIT
+    S, (a, g, t, stats, status), rd = check_parity(prob, avg, lm, lp, 40, DISC_TOL, solver=_solver(prob, f))
     ok = S.status == 0
     for k in (O.ST_RS_CALLS, O.ST_RECON_FB, O.ST_LOW_ORDER, O.ST_FLUX_FB):
         assert np.array_equal(stats[ok, k].astype(np.int64), S.stats[ok, k]), k
@@ -46,3 +58,22 @@ def test_hard_list_mixed_with_long_domains():
     ids = np.sort(np.concatenate([tiny, long_rp]))
     prob, avg, lm, lp = I.batched(M=2, domains=ids)
     check_parity(prob, avg, lm, lp, 30, DISC_TOL)
+
+
+@pytest.mark.parametrize("M", [2, 4])
+def test_flat_form_with_graphs_equals_direct_launches(M):
+    """Both passes of the flux phase replayed from a CUDA graph give the same
+    bits as direct launches."""
+    from paper_2602_21911_gb300 import grprec
+    ids = np.arange(0, 65536, 97)[:400]
+    prob, avg, lm, lp = I.batched(M=M, domains=ids)
+    out = []
+    for graph in (0, 4):
+        s = _solver(prob, grprec.GRP_LAUNCH_FLAT)
+        s.set_graph(graph)
+        s.set_initial(avg, lm, lp)
+        s.step(24)
+        out.append(s.get_state())
+        s.close()
+    for x, y in zip(out[0], out[1]):
+        assert np.array_equal(x, y)
