@@ -132,6 +132,11 @@ typedef struct {
 /*
  * Create a context for the problem *p (copied; the arrays are read during the
  * call only).  Allocates the device state.  *out receives the context.
+ * Euler equations with GRPrec of degree 2 or 4, the TT solver and no source:
+ * the flux phase solves the Riemann problems that are not equal data in a
+ * second kernel, from a list of n_if / 4 + 1024 interfaces (n_if = the total
+ * interface count) held by the context, (6 (M + 1) + 1) x 8 bytes each;
+ * interfaces beyond it are solved in the first kernel.
  * Errors: GRP_E_INVALID_ARG for any field outside its range, GRP_E_CUDA.
  */
 int grp_create(grp_ctx **out, const grp_problem *p);
