@@ -300,6 +300,54 @@ GRP_HD __forceinline__ bool positive(double x)
 #endif
 }
 
+// More tests on the bits (integer pipe), equal to the IEEE comparisons for
+// arguments that are not NaN (-0 included): x >= 0, x <= 0, x < 0, and
+// a > b, a < b, max(a, b) for a, b >= 0 (non-negative doubles order as their
+// bit patterns do; max(a, b) also when only b is known to be positive).
+GRP_HD __forceinline__ bool ge0(double x)
+{
+#ifdef __CUDA_ARCH__
+  const long long b = __double_as_longlong(x);
+  return b >= 0ll || b == (long long)0x8000000000000000ull;
+#else
+  return x >= 0.0;
+#endif
+}
+GRP_HD __forceinline__ bool le0(double x)
+{
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(x) <= 0ll;
+#else
+  return x <= 0.0;
+#endif
+}
+GRP_HD __forceinline__ bool lt0(double x)
+{
+#ifdef __CUDA_ARCH__
+  const long long b = __double_as_longlong(x);
+  return b < 0ll && b != (long long)0x8000000000000000ull;
+#else
+  return x < 0.0;
+#endif
+}
+GRP_HD __forceinline__ bool gt_nn(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(a) > __double_as_longlong(b);
+#else
+  return a > b;
+#endif
+}
+GRP_HD __forceinline__ double max_nn(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+  const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return __longlong_as_double(x > y ? x : y);
+#else
+  return fmax(a, b);
+#endif
+}
+
 // rho > 0 and p = (g-1)(E - m^2/(2 rho)) > 0, written without a division:
 // rho > 0 and 2 E rho - m^2 > 0 (one fused multiply-add; its sign is that of
 // the exact 2 E rho - fl(m^2)), both sign tests on the integer pipe.
@@ -362,7 +410,7 @@ GRP_HD __forceinline__ Side make_side(const Phys& ph, const double Q[3])
 template <bool G75>
 GRP_HD __forceinline__ void pressure_fn(const Phys& ph, double p, const Side& K, double& f, double& df)
 {
-  if (p > K.p) {
+  if (gt_nn(p, K.p)) {                            // p, pK > 0
     const double t = rsqrt(p + K.B);             // (p + B)^(-1/2)
     const double s = K.sA * t;                    // sqrt(A / (p + B))
     f = (p - K.p) * s;
@@ -386,7 +434,7 @@ template <bool G75>
 GRP_HD __forceinline__ double trrs(const Phys& ph, const Side& L, const Side& R)
 {
   const double num = L.c + R.c - 0.5 * ph.gm1 * (R.u - L.u);
-  if (!(num > 0.0)) return 0.0;
+  if (!positive(num)) return 0.0;
   if (G75) {                                        // z = 1/7: p^-z by a 7th root, ^(1/z) = ^7
     const double q = num / (L.c * inv_root7(L.p) + R.c * inv_root7(R.p));
     const double q2 = q * q, q4 = q2 * q2;
@@ -400,7 +448,7 @@ GRP_HD __forceinline__ double trrs(const Phys& ph, const Side& L, const Side& R)
 GRP_HD __forceinline__ double pvrs(const Side& L, const Side& R)
 {
   const double ppv = 0.5 * (L.p + R.p) - 0.125 * (R.u - L.u) * (L.r + R.r) * (L.c + R.c);
-  return fmax(ppv, 1e-14 * fmax(L.p, R.p));
+  return max_nn(ppv, 1e-14 * max_nn(L.p, R.p));    // the floor is positive
 }
 
 // Two-shock estimate of the star pressure from the pressure p0 (the PVRS
@@ -428,7 +476,7 @@ static GRP_HD int star_pressure(const Phys& ph, const Side& L, const Side& R, do
   const double du = R.u - L.u;
   iters = 0;
   if (ph.c2_gm1 * (L.c + R.c) <= du) return ST_VACUUM;
-  const double pfloor = 1e-14 * fmax(L.p, R.p);
+  const double pfloor = 1e-14 * max_nn(L.p, R.p);
   double p;
   if (p0 > 0.0 && isfinite(p0)) {
     p = p0;
@@ -442,7 +490,7 @@ static GRP_HD int star_pressure(const Phys& ph, const Side& L, const Side& R, do
   } else {
     p = pvrs(L, R);
   }
-  if (!(p > pfloor)) p = pfloor;
+  if (!gt_nn(p, pfloor) || !positive(p)) p = pfloor;
   bool conv = false, done = false;
   int it = 0;
   while (it < ph.max_iter) {
@@ -451,9 +499,9 @@ static GRP_HD int star_pressure(const Phys& ph, const Side& L, const Side& R, do
     pressure_fn<G75>(ph, p, R, fR, dfR);
     double step = -(fL + fR + du) * rcp_newton_step(dfL + dfR);
     double pn = p + step;
-    for (int h = 0; h < 64 && !(pn > 0.0); ++h) { step *= 0.5; pn = p + step; }
+    for (int h = 0; h < 64 && !positive(pn); ++h) { step *= 0.5; pn = p + step; }
     ++it;
-    const bool small = 2.0 * fabs(pn - p) < ph.rtol * (pn + p);   // relative change < rtol
+    const bool small = gt_nn(ph.rtol * (pn + p), 2.0 * fabs(pn - p));   // relative change < rtol
     if (conv) {
       // the extra iteration after convergence: its step is at the rounding
       // level, so the pressure functions at the new iterate are those at p
@@ -515,28 +563,28 @@ static GRP_HD Prim sample_zero(const Phys& ph, const Side& L, const Side& R, dou
   const Prim WL{L.r, L.u, L.p}, WR{R.r, R.u, R.p};
   if (us >= -TIE * (L.c + R.c)) {
     const double ratio = ps * L.ip;
-    if (ps > L.p) {
+    if (gt_nn(ps, L.p)) {
       const double S = L.u - L.c * sqrt(ph.gp1_2g * ratio + g1);
-      if (S >= 0.0) return WL;
+      if (ge0(S)) return WL;
       return Prim{L.r * (ratio + g6) / (g6 * ratio + 1.0), us, ps};
     }
-    if (L.u - L.c >= 0.0) return WL;
+    if (ge0(L.u - L.c)) return WL;
     double rho, cs;
     rarefied<G75>(ph, L, ratio, rho, cs);
-    if (us - cs < 0.0) return Prim{rho, us, ps};
+    if (lt0(us - cs)) return Prim{rho, us, ps};
     const double c0 = ph.c2_gp1 * (L.c + 0.5 * ph.gm1 * L.u);
     return sonic<G75>(ph, L, c0, c0);
   }
   const double ratio = ps * R.ip;
-  if (ps > R.p) {
+  if (gt_nn(ps, R.p)) {
     const double S = R.u + R.c * sqrt(ph.gp1_2g * ratio + g1);
-    if (S <= 0.0) return WR;
+    if (le0(S)) return WR;
     return Prim{R.r * (ratio + g6) / (g6 * ratio + 1.0), us, ps};
   }
-  if (R.u + R.c <= 0.0) return WR;
+  if (le0(R.u + R.c)) return WR;
   double rho, cs;
   rarefied<G75>(ph, R, ratio, rho, cs);
-  if (us + cs > 0.0) return Prim{rho, us, ps};
+  if (positive(us + cs)) return Prim{rho, us, ps};
   const double c0 = ph.c2_gp1 * (R.c - 0.5 * ph.gm1 * R.u);
   return sonic<G75>(ph, R, c0, -c0);
 }
@@ -919,15 +967,17 @@ GRP_HD __forceinline__ void char_back(const Eig& e, const double w[3], double D[
 // sonic field averages the two sides); tie >= 0.  On the GPU both tests are
 // integer compares of the bit patterns (exact for non-NaN values: -lam > tie
 // with the sign bit flipped), off the FP64 pipe.
-GRP_HD __forceinline__ double upwind_weight(double lam, double tie)
+// As twice the weight (0, 1 or 2), so that the test for a field that takes
+// right data is an integer one too.
+GRP_HD __forceinline__ int upwind_weight2(double lam, double tie)
 {
 #ifdef __CUDA_ARCH__
   const long long b = __double_as_longlong(lam), t = __double_as_longlong(tie);
-  if (b > t) return 0.0;
-  if ((b ^ (long long)0x8000000000000000ull) > t) return 1.0;
-  return 0.5;
+  if (b > t) return 0;
+  if ((b ^ (long long)0x8000000000000000ull) > t) return 2;
+  return 1;
 #else
-  return lam > tie ? 0.0 : (lam < -tie ? 1.0 : 0.5);
+  return lam > tie ? 0 : (lam < -tie ? 2 : 1);
 #endif
 }
 
@@ -953,8 +1003,9 @@ GRP_HD __forceinline__ void deriv_rps(const Eig& e, const double tL[][M + 1], co
   const double bu = e.b1 * e.u;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    const double th = upwind_weight(e.lam[j], e.tie);
-    if (th != 0.0) {
+    const int th2 = upwind_weight2(e.lam[j], e.tie);
+    if (th2 != 0) {
+      const double th = th2 == 2 ? 1.0 : 0.5;
       double l0, l1, l2, r1, r2;
       if (j == 1) {
         l0 = 1.0 - e.b2; l1 = bu; l2 = -e.b1;

@@ -213,9 +213,11 @@ __device__ __forceinline__ void smax_cell(const StepArgs& a, long long gi, bool 
     const double p = (g - 1.0) * (E - 0.5 * m * u);
     a.pold[gi] = p;                                // for the discrete maximum principle of the update
     const double c2 = g * p * ir;
-    double sp = fabs(u) + (c2 > 0.0 ? c2 * rsqrt(c2) : 0.0);
-    if (!(sp >= 0.0)) sp = 0.0;
-    bits = (unsigned long long)__double_as_longlong(sp);
+    // c2 <= 0 or not a number: no sound speed; |u| + c not a number: 0
+    // (both tests on the bits, off the FP64 pipe)
+    const double sp = fabs(u) + (positive(c2) ? c2 * rsqrt(c2) : 0.0);
+    const long long sb = __double_as_longlong(sp);
+    bits = sb >= 0ll && sb <= 0x7ff0000000000000ll ? (unsigned long long)sb : 0ull;
   }
   const int d0 = __shfl_sync(0xffffffffu, d, 0);
   if (__all_sync(0xffffffffu, d == d0 && d >= 0)) {
