@@ -338,6 +338,15 @@ GRP_HD __forceinline__ bool gt_nn(double a, double b)
   return a > b;
 #endif
 }
+GRP_HD __forceinline__ bool finite_positive(double x)
+{
+#ifdef __CUDA_ARCH__
+  const long long b = __double_as_longlong(x);
+  return b > 0ll && b < 0x7ff0000000000000ll;
+#else
+  return x > 0.0 && isfinite(x);
+#endif
+}
 GRP_HD __forceinline__ double max_nn(double a, double b)
 {
 #ifdef __CUDA_ARCH__
@@ -478,14 +487,16 @@ static GRP_HD int star_pressure(const Phys& ph, const Side& L, const Side& R, do
   if (ph.c2_gm1 * (L.c + R.c) <= du) return ST_VACUUM;
   const double pfloor = 1e-14 * max_nn(L.p, R.p);
   double p;
-  if (p0 > 0.0 && isfinite(p0)) {
+  if (finite_positive(p0)) {
     p = p0;
   } else if (ph.guess == 1) {
     p = trrs<G75>(ph, L, R);
   } else if (ph.guess == GUESS_ADAPTIVE) {
-    const double ppv = pvrs(L, R), pmin = fmin(L.p, R.p), pmax = fmax(L.p, R.p);
-    if (pmax < 2.0 * pmin && ppv >= pmin && ppv <= pmax) p = ppv;
-    else if (ppv < pmin) p = trrs<G75>(ph, L, R);
+    // pL, pR > 0 and ppv is floored at a positive value: integer tests
+    const double ppv = pvrs(L, R), pmax = max_nn(L.p, R.p);
+    const double pmin = gt_nn(L.p, R.p) ? R.p : L.p;
+    if (gt_nn(2.0 * pmin, pmax) && !gt_nn(pmin, ppv) && !gt_nn(ppv, pmax)) p = ppv;
+    else if (gt_nn(pmin, ppv)) p = trrs<G75>(ph, L, R);
     else p = tsrs(L, R, ppv);
   } else {
     p = pvrs(L, R);

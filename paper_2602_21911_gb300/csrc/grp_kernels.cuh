@@ -359,7 +359,7 @@ static __device__ int first_order(const StepArgs& a, long long c0, int N, int bc
   ph.features = info ? 2 : 0;
   const int st = riemann_state<G75>(ph, QL, QR, true, Q0, W, iters, info);
   if (st != ST_OK && st != ST_VACUUM) return st;
-  if (Q0[0] > 0.0) euler_flux(a.ph.gamma, Q0[0], Q0[1], Q0[2], F);
+  if (positive(Q0[0])) euler_flux(a.ph.gamma, Q0[0], Q0[1], Q0[2], F);
   else F[0] = F[1] = F[2] = 0.0;
   return ST_OK;
 }
