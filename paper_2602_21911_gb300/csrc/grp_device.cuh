@@ -1016,20 +1016,23 @@ GRP_HD __forceinline__ void deriv_rps(const Eig& e, const double tL[][M + 1], co
   for (int j = 0; j < 3; ++j) {
     const int th2 = upwind_weight2(e.lam[j], e.tie);
     if (th2 != 0) {
-      const double th = th2 == 2 ? 1.0 : 0.5;
+      // theta_j l_j: theta is 1 or 1/2, a power of two, so folding it into
+      // the row changes no bit of the products
       double l0, l1, l2, r1, r2;
       if (j == 1) {
         l0 = 1.0 - e.b2; l1 = bu; l2 = -e.b1;
+        if (th2 == 1) { l0 *= 0.5; l1 *= 0.5; l2 *= 0.5; }
         r1 = e.u; r2 = 0.5 * e.u * e.u;
       } else {
         const double sg = j == 0 ? 1.0 : -1.0;          // field u - c (j = 0) or u + c (j = 2)
+        const double h = th2 == 2 ? 0.5 : 0.25;         // theta / 2
         const double uc = e.u * e.ic;
-        l0 = 0.5 * (e.b2 + sg * uc); l1 = -0.5 * (bu + sg * e.ic); l2 = 0.5 * e.b1;
+        l0 = h * (e.b2 + sg * uc); l1 = -h * (bu + sg * e.ic); l2 = h * e.b1;
         r1 = e.lam[j]; r2 = e.H - sg * (e.u * e.c);
       }
 #pragma unroll
       for (int k = 1; k <= M; ++k) {
-        const double w = th * (l0 * J[k][0] + l1 * J[k][1] + l2 * J[k][2]);
+        const double w = l0 * J[k][0] + l1 * J[k][1] + l2 * J[k][2];
         D[k][0] -= w;
         D[k][1] -= w * r1;
         D[k][2] -= w * r2;
