@@ -933,6 +933,7 @@ struct Lead {
 // ---------------------------------------------------------------------------
 struct Eig {
   double u, c, H, b1, b2, ic, tie;
+  double k;                // u^2 / 2
   double lam[3];
 };
 
@@ -945,7 +946,8 @@ GRP_HD __forceinline__ Eig make_eig(const Phys& ph, const double Q0[3], Prim w, 
   e.c = c2 * e.ic;
   e.H = (Q0[2] + w.p) * ir;
   e.b1 = ph.gm1 * e.ic * e.ic;
-  e.b2 = 0.5 * e.u * e.u * e.b1;
+  e.k = 0.5 * e.u * e.u;
+  e.b2 = e.k * e.b1;
   e.lam[0] = e.u - e.c; e.lam[1] = e.u; e.lam[2] = e.u + e.c;
   e.tie = TIE * (fabs(e.u) + e.c);
   return e;
@@ -970,7 +972,7 @@ GRP_HD __forceinline__ void char_back(const Eig& e, const double w[3], double D[
 {
   D[0] = w[0] + w[1] + w[2];
   D[1] = (e.u - e.c) * w[0] + e.u * w[1] + (e.u + e.c) * w[2];
-  D[2] = (e.H - e.u * e.c) * w[0] + 0.5 * e.u * e.u * w[1] + (e.H + e.u * e.c) * w[2];
+  D[2] = (e.H - e.u * e.c) * w[0] + e.k * w[1] + (e.H + e.u * e.c) * w[2];
 }
 
 // Upwind weight theta of a field of speed lam in a derivative Riemann problem:
@@ -1022,7 +1024,7 @@ GRP_HD __forceinline__ void deriv_rps(const Eig& e, const double tL[][M + 1], co
       if (j == 1) {
         l0 = 1.0 - e.b2; l1 = bu; l2 = -e.b1;
         if (th2 == 1) { l0 *= 0.5; l1 *= 0.5; l2 *= 0.5; }
-        r1 = e.u; r2 = 0.5 * e.u * e.u;
+        r1 = e.u; r2 = e.k;
       } else {
         const double sg = j == 0 ? 1.0 : -1.0;          // field u - c (j = 0) or u + c (j = 2)
         const double h = th2 == 2 ? 0.5 : 0.25;         // theta / 2
@@ -1054,19 +1056,19 @@ struct Tri {
 };
 
 // In: q0[c][idx(a,0)] filled for a = 0..M (others ignored).  Out: s[c][b] = q[0][b].
+// gm1: gamma - 1.
 // irho, u0, p0: 1/rho, velocity and pressure of the leading state (known to
 // the caller), the series' constant terms.
 // SRC: with the constant-acceleration source S = (0, -g rho, -g m), in scaled
 // variables d_T Q + d_X F = dx S: q[a][b+1] gets hs/(b+1) (0, rho[a][b],
 // m[a][b]) added, hs = -g dx.
 template <int M, bool SRC = false>
-GRP_HD __forceinline__ void ck_euler(double g, double rho[Tri<M>::N], double m[Tri<M>::N],
+GRP_HD __forceinline__ void ck_euler(double gm1, double rho[Tri<M>::N], double m[Tri<M>::N],
                                          double E[Tri<M>::N], double s[3][M + 1], double irho, double u0, double p0,
                                          double hs = 0.0)
 {
   using T = Tri<M>;
   double u[T::N], mu[T::N], Ep[T::N], F1[T::N], F2[T::N];
-  const double gm1 = g - 1.0;
 #pragma unroll
   for (int b = 0; b < M; ++b) {
 #pragma unroll
@@ -1274,7 +1276,7 @@ GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[
     }
   }
   double s[3][M + 1];
-  ck_euler<M, SRC>(g, rho, m, E, s, ir0, W0.u, W0.p, hs);
+  ck_euler<M, SRC>(ph.gm1, rho, m, E, s, ir0, W0.u, W0.p, hs);
   // states at the Gauss nodes and at tau = dt; at a node one reciprocal
   // serves both the admissibility test and the flux, at dt (no flux) the
   // test is division-free
@@ -1296,7 +1298,7 @@ GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[
   for (int al = 0; al <= G; ++al) {
     if (al < G) {
       ug[al] = Qg[al][1] * rcp64(Qg[al][0]);        // a non-positive density fails the test below
-      pg[al] = (g - 1.0) * (Qg[al][2] - 0.5 * Qg[al][1] * ug[al]);
+      pg[al] = ph.gm1 * (Qg[al][2] - 0.5 * Qg[al][1] * ug[al]);
       ok = ok && positive(Qg[al][0]) && positive(pg[al]);
     } else {
       ok = ok && admissible(g, Qg[al][0], Qg[al][1], Qg[al][2]);
@@ -1392,7 +1394,7 @@ GRP_HD __forceinline__ void cell_source_euler(const Phys& ph, const double b[3][
   for (int a = 0; a <= M; ++a) { rho[T::idx(a, 0)] = t[0][a]; m[T::idx(a, 0)] = t[1][a]; E[T::idx(a, 0)] = t[2][a]; }
   const double ir = 1.0 / rho[0];
   const double u0 = m[0] * ir, p0 = ph.gm1 * (E[0] - 0.5 * m[0] * u0);
-  ck_euler<M, true>(ph.gamma, rho, m, E, s, ir, u0, p0, -ph.src_k * dx);
+  ck_euler<M, true>(ph.gm1, rho, m, E, s, ir, u0, p0, -ph.src_k * dx);
   S[0] = 0.0;
   S[1] = -ph.src_k * series_average<M>(rho, nu);
   S[2] = -ph.src_k * series_average<M>(m, nu);
