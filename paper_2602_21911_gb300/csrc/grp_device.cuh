@@ -258,10 +258,27 @@ GRP_HD __forceinline__ void grprec_nl_coeffs(const double d[7], double dx, doubl
 template <int M>
 GRP_HD __forceinline__ void edge_taylor(const double b[5], double side, double t[M + 1])
 {
-  // p(xi) = b0 + b1 xi + b2 (xi^2 - 1/12) + b3 xi^3 + b4 (xi^4 - 1/80)
-  t[0] = b[0] + side * 0.5 * b[1] + b[2] * (1.0 / 6.0) + side * 0.125 * b[3] + b[4] * 0.05;
-  if (M >= 1) t[1] = b[1] + side * b[2] + 0.75 * b[3] + side * 0.5 * b[4];
-  if (M >= 2) t[2] = b[2] + side * 1.5 * b[3] + 1.5 * b[4];
+  // p(xi) = b0 + b1 xi + b2 (xi^2 - 1/12) + b3 xi^3 + b4 (xi^4 - 1/80).
+  // Coefficients above the degree M are zero and their terms are left out
+  // (adding a +0.0 is an instruction the compiler must keep).
+  double t0 = b[0] + side * 0.5 * b[1];
+  if (M >= 2) t0 = t0 + b[2] * (1.0 / 6.0);
+  if (M >= 3) t0 = t0 + side * 0.125 * b[3];
+  if (M >= 4) t0 = t0 + b[4] * 0.05;
+  t[0] = t0;
+  if (M >= 1) {
+    double t1 = b[1];
+    if (M >= 2) t1 = t1 + side * b[2];
+    if (M >= 3) t1 = t1 + 0.75 * b[3];
+    if (M >= 4) t1 = t1 + side * 0.5 * b[4];
+    t[1] = t1;
+  }
+  if (M >= 2) {
+    double t2 = b[2];
+    if (M >= 3) t2 = t2 + side * 1.5 * b[3];
+    if (M >= 4) t2 = t2 + 1.5 * b[4];
+    t[2] = t2;
+  }
   if (M >= 3) t[3] = b[3] + side * 2.0 * b[4];
   if (M >= 4) t[4] = b[4];
 }
