@@ -30,7 +30,7 @@ struct Phys {
   int max_iter;
   int guess;  // 0 PVRS, 1 TRRS, 2 learned
   // gamma-dependent constants, computed once on the host (make_phys)
-  double gm1, i_gm1, c2_gm1, c2_gp1, gm1_gp1, gm1_2g, gp1_2g, c2g_gm1, i_g, sqrt_c2_gp1;
+  double gm1, i_gm1, c2_gm1, c2_gp1, gm1_gp1, gm1_2g, gp1_2g, c2g_gm1, i_g, sqrt_c2_gp1, h_gm1;
   // learned Newton guess: FP32 weights (MLP_NPARAM) and input box lo[6], hi[6]
   const float* mlp_w;
   const float* mlp_box;
@@ -57,6 +57,7 @@ inline Phys make_phys(double lambda, double gamma, double rtol, int max_iter, in
   p.c2g_gm1 = 2.0 * g / (g - 1.0);
   p.i_g = 1.0 / g;
   p.sqrt_c2_gp1 = sqrt(2.0 / (g + 1.0));
+  p.h_gm1 = 0.5 * (g - 1.0);
   p.mlp_w = nullptr;
   p.mlp_box = nullptr;
   p.features = 0;

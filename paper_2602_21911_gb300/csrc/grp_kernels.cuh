@@ -210,7 +210,7 @@ __device__ __forceinline__ void smax_cell(const StepArgs& a, long long gi, bool 
     // ulp or two from the correctly rounded divisions and root)
     const double ir = rcp64(r);
     const double u = m * ir;
-    const double p = (g - 1.0) * (E - 0.5 * m * u);
+    const double p = a.ph.gm1 * (E - 0.5 * m * u);
     a.pold[gi] = p;                                // for the discrete maximum principle of the update
     const double c2 = g * p * ir;
     // c2 <= 0 or not a number: no sound speed; |u| + c not a number: 0
@@ -837,8 +837,10 @@ __device__ __forceinline__ int update_one(const StepArgs& a, long long gi, int d
     a.avg_new[c * a.ncell + gi] = Q[c];
   }
   if (SYS != SYS_EULER) return 0;
-  const double g = a.ph.gamma;
-  const bool adm = admissible(g, Q[0], Q[1], Q[2]);
+  // admissible: rho > 0 and 2 E rho - m^2 = 2 rho p / (g - 1) > 0 (the
+  // latter also gives the candidate's rho p below)
+  const double a2 = fma(Q[2] + Q[2], Q[0], -(Q[1] * Q[1]));
+  const bool adm = positive(Q[0]) && positive(a2);
   bool ok = adm;
   if (adm) {
     int im, ip;
@@ -861,13 +863,14 @@ __device__ __forceinline__ int update_one(const StepArgs& a, long long gi, int d
     const double plo = __longlong_as_double(lo1), phi = __longlong_as_double(hi1);
     // the candidate pressure p = (g-1)(E - m^2/(2 rho)) against its bounds,
     // multiplied through by rho > 0 (admissible): no division
-    const double rp = (g - 1.0) * (Q[2] * Q[0] - 0.5 * Q[1] * Q[1]);
-    const double d0 = DMP_REL * rhi, d1 = DMP_REL * phi;
-    // Q[0] and rp are positive here, so each bound test is a signed-integer
-    // compare of the bits (exact: a negative bound has a negative pattern)
+    const double rp = a.ph.h_gm1 * a2;
+    // the band [lo - DMP_REL hi, hi + DMP_REL hi], each end one fma.  Q[0] and
+    // rp are positive here, so each bound test is a signed-integer compare of
+    // the bits (exact: a negative bound has a negative pattern)
     const long long q0 = __double_as_longlong(Q[0]), rq = __double_as_longlong(rp);
-    ok = q0 >= __double_as_longlong(rlo - d0) && q0 <= __double_as_longlong(rhi + d0) &&
-         rq >= __double_as_longlong((plo - d1) * Q[0]) && rq <= __double_as_longlong((phi + d1) * Q[0]);
+    ok = q0 >= __double_as_longlong(fma(-DMP_REL, rhi, rlo)) && q0 <= __double_as_longlong(fma(DMP_REL, rhi, rhi)) &&
+         rq >= __double_as_longlong(fma(-DMP_REL, phi, plo) * Q[0]) &&
+         rq <= __double_as_longlong(fma(DMP_REL, phi, phi) * Q[0]);
   }
   const unsigned char flag = adm ? (ok ? 0 : 1) : 2;
   const unsigned char before = pass < 0 ? 0 : a.troubled[gi];
