@@ -676,8 +676,9 @@ GRP_HD __forceinline__ bool strong_data(const Phys& ph, const Side& L, const Sid
 {
   const double pr = L.p * R.ip, dun = R.u - L.u, du2 = dun * dun;
   const double g2 = (double)MLP_GATE * (double)MLP_GATE;
-  return pr > MLP_GATE_EXP || pr * MLP_GATE_EXP < 1.0 ||
-         du2 * du2 * (L.r * R.r) > g2 * g2 * ph.gamma * ph.gamma * (L.p * R.p);
+  // all three compare non-negative doubles: integer tests of the bits
+  return gt_nn(pr, MLP_GATE_EXP) || gt_nn(1.0, pr * MLP_GATE_EXP) ||
+         gt_nn(du2 * du2 * (L.r * R.r), g2 * g2 * ph.gamma * ph.gamma * (L.p * R.p));
 }
 
 // Features x[6] of strong data, in FP32 (the network's precision; off the
@@ -800,6 +801,15 @@ struct LearnedPrep {
   bool ok, has_x, inbox;
 };
 
+// The decisions and features of strong data worked out before the solve (the
+// second flux pass), with the network's output v (valid when the network was
+// wanted), so that the solve does not repeat them.
+struct LearnedPre {
+  LearnedPrep q;
+  float x[6];
+  float v;
+};
+
 GRP_HD __forceinline__ bool learned_prep_f32(const Phys& ph, const Side& L, const Side& R, float x[6],
                                              LearnedPrep& q)
 {
@@ -830,7 +840,7 @@ __device__ __noinline__
 inline
 #endif
 int learned_start(const Phys& ph, const Side& L, const Side& R, RSInfo& info, double& ps, double& us, int& iters,
-                  const float* vpre)
+                  const LearnedPre* pre)
 {
   int st = -1;
   double p0 = 0.0;
@@ -860,17 +870,23 @@ int learned_start(const Phys& ph, const Side& L, const Side& R, RSInfo& info, do
     }
   } else {
     // inference: the start in FP32 (the same decisions and correction; Newton
-    // converges from it to the same p*).  vpre: the network's output for these
-    // features, evaluated beforehand by the whole warp (learned_warp_outputs)
+    // converges from it to the same p*).  pre: the decisions, features and
+    // network output worked out beforehand (the network by the whole warp)
     LearnedPrep q;
-    learned_prep_f32(ph, L, R, info.x, q);
+    if (pre) {
+      q = pre->q;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) info.x[i] = pre->x[i];
+    } else {
+      learned_prep_f32(ph, L, R, info.x, q);
+    }
     ok = q.ok;
     info.base = q.base;
     info.s3 = q.s3;
     info.has_x = q.has_x;
     p0 = q.base;
     if (ph.guess == 2 && ph.mlp_w && ok && info.has_x) {
-      v = q.inbox ? (vpre ? *vpre : mlp_eval(ph.mlp_w, info.x)) : 0.0f;
+      v = q.inbox ? (pre ? pre->v : mlp_eval(ph.mlp_w, info.x)) : 0.0f;
       const float y = (float)MLP_T_SCALE * q.s3 * v;
       go = q.inbox && v == v && fabsf(v) <= MLP_VMAX && fabsf(y) <= (float)MLP_YMAX;
       p0 = (double)(q.base * expf(y));
@@ -894,16 +910,20 @@ int learned_start(const Phys& ph, const Side& L, const Side& R, RSInfo& info, do
 // from the network's prediction (or from p_TR for two rarefactions); an input
 // outside the training box, a prediction out of range or not finite, or no
 // convergence within MLP_GUESS_MAX_ITER iterations falls back to PVRS
-// (iterations add up).
+// (iterations add up).  pre: strong data whose learned-start decisions are
+// worked out already; strong: 0 data known not to be strong, -1 not known
+// (tested here).
 template <bool G75>
 static GRP_HD int riemann_sides(const Phys& ph, const Side& L, const Side& R, bool allow_vacuum, double Q[3],
-                                Prim& W, int& iters, RSInfo* info, const float* vpre = nullptr)
+                                Prim& W, int& iters, RSInfo* info, const LearnedPre* pre = nullptr,
+                                int strong = -1)
 {
   double ps = 0.0, us = 0.0;
   int st = -1;
   iters = 0;
   // the learned-guess path (out of line) only for strong data
-  if (ph.features && info && strong_data(ph, L, R)) st = learned_start<G75>(ph, L, R, *info, ps, us, iters, vpre);
+  if (ph.features && info && (pre || (strong < 0 && strong_data(ph, L, R))))
+    st = learned_start<G75>(ph, L, R, *info, ps, us, iters, pre);
   if (st != ST_OK && st != ST_VACUUM) {
     int it2 = 0;
     Phys pv = ph;

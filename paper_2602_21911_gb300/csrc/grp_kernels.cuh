@@ -752,14 +752,15 @@ __global__ void __launch_bounds__(GRP_HARD_TPB, GRP_HARD_MIN_BLOCKS) k_flux_hard
     }
     if (NET) {
       Side L, R;
-      float x[6], v = 0.0f;
-      bool want = false;
+      LearnedPre pre;
+      pre.v = 0.0f;
+      bool strong = false, want = false;
       if (d >= 0) {
         const double QL[3] = {tL[0][0], tL[1][0], tL[2][0]}, QR[3] = {tR[0][0], tR[1][0], tR[2][0]};
         L = make_side(a.ph, QL);
         R = make_side(a.ph, QR);
-        LearnedPrep q;
-        want = strong_data(a.ph, L, R) && learned_prep_f32(a.ph, L, R, x, q);
+        strong = strong_data(a.ph, L, R);
+        if (strong) want = learned_prep_f32(a.ph, L, R, pre.x, pre.q);
       }
       unsigned m = __ballot_sync(0xffffffffu, want);
       while (m) {
@@ -767,13 +768,14 @@ __global__ void __launch_bounds__(GRP_HARD_TPB, GRP_HARD_MIN_BLOCKS) k_flux_hard
         m &= m - 1u;
         float xs[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) xs[k] = __shfl_sync(0xffffffffu, x[k], src);
+        for (int k = 0; k < 6; ++k) xs[k] = __shfl_sync(0xffffffffu, pre.x[k], src);
         const float y = mlp_eval_warp(a.ph.mlp_w, xs, hs[threadIdx.x >> 5]);
-        if (lane == src) v = y;
+        if (lane == src) pre.v = y;
       }
       if (d >= 0) {
         Lead ld;
-        ld.st = riemann_sides<G75>(a.ph, L, R, false, ld.Q0, ld.W0, ld.iters, &ld.info, &v);
+        ld.st = riemann_sides<G75>(a.ph, L, R, false, ld.Q0, ld.W0, ld.iters, &ld.info, strong ? &pre : nullptr,
+                                   strong ? 1 : 0);
         const long long i0 = a.if_off[d], c0 = a.cell_off[d];
         const int N = (int)(a.cell_off[d + 1] - c0);
         grp_at<SYS_EULER, M, G75, false>(a, gj, d, c0, N, a.bc[d], (int)(gj - i0), tL, tR, st, &ld);
