@@ -41,6 +41,10 @@ struct grp_ctx {
   long long* hard_idx = nullptr;
   unsigned* hard_count = nullptr;
   long long hard_cap = 0;
+  // admissibility flags of the interface data, one buffer per state buffer;
+  // adm_valid: the flags of the current buffer were written by the last step
+  unsigned char* gadm[2] = {nullptr, nullptr};
+  bool adm_valid = false;
   unsigned char *low = nullptr, *troubled = nullptr;
   double *t = nullptr, *dt_prev = nullptr;
   int *nstep = nullptr, *status = nullptr;
@@ -75,6 +79,7 @@ struct grp_ctx {
     cudaGraphExec_t x = nullptr;
     int start_cur = 0;
     bool smax_ready = false;
+    bool adm_valid = false, adm_end = false;   // flags valid at the graph's start and end
     unsigned long long t_end_bits = 0;
     int steps = 0;
     int cur_end = 0;                 // buffer parity after the graph
@@ -132,7 +137,7 @@ void free_all(grp_ctx* c)
                   c->status, c->smax_bits, c->bad, c->inad, c->fail, c->any_bad, c->tlist0, c->tlist1,
                   c->ilist, c->lcount, c->stats,
                   c->scratch_norm, c->mlp, c->mlp_norm, c->grp, c->tiles, c->tile_zeros, c->tile_flag,
-                  c->hard_tr, c->hard_idx, c->hard_count};
+                  c->hard_tr, c->hard_idx, c->hard_count, c->gadm[0], c->gadm[1]};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -272,6 +277,7 @@ int build_groups(grp_ctx* c)
 // nsteps steps of the persistent batched kernel in one launch
 int enqueue_batch(grp_ctx* c, int nsteps, double t_end)
 {
+  c->adm_valid = false;               // this form keeps no admissibility flags
   if (!c->grp) { const int rc = build_groups(c); if (rc) return rc; }
   c->smax_ready = false;
   const StepArgs a = make_args(c, t_end);
@@ -300,6 +306,7 @@ int enqueue_batch(grp_ctx* c, int nsteps, double t_end)
 // one step in the split form: grid-wide k_flux, then k_post per domain group
 int enqueue_split(grp_ctx* c, double t_end)
 {
+  c->adm_valid = false;               // this form keeps no admissibility flags
   if (!c->grp) { const int rc = build_groups(c); if (rc) return rc; }
   const StepArgs a = make_args(c, t_end);
   cudaStream_t s = c->stream;
@@ -383,6 +390,7 @@ int build_tiles(grp_ctx* c)
 // steps_per_launch steps of every domain in one tile launch (t_end = inf)
 int enqueue_tiled(grp_ctx* c)
 {
+  c->adm_valid = false;               // this form keeps no admissibility flags
   if (!c->tiles) { const int rc = build_tiles(c); if (rc) return rc; }
   c->smax_ready = false;
   const StepArgs a = make_args(c, INFINITY);
@@ -428,7 +436,14 @@ int enqueue_tiled(grp_ctx* c)
 int enqueue_step(grp_ctx* c, double t_end)
 {
   c->smax_ready = false;
-  const StepArgs a = make_args(c, t_end);
+  StepArgs a = make_args(c, t_end);
+  // the flat flux kernel at degrees 2 and 4 keeps the interface data's
+  // admissibility flags; the first step after new data tests the data
+  const bool flags = c->gadm[0] && flux_defers(a);
+  if (flags) {
+    a.adm_in = c->adm_valid ? c->gadm[c->cur] : nullptr;
+    a.adm_out = c->gadm[c->cur ^ 1];
+  }
   cudaStream_t s = c->stream;
   const bool euler = c->p.system == GRP_EULER_IDEAL;
   if (euler) {
@@ -474,6 +489,7 @@ int enqueue_step(grp_ctx* c, double t_end)
   k_finish<<<blocks(c->D, 128), 128, 0, s>>>(a);
   c->launches++;
   CK(cudaGetLastError());
+  c->adm_valid = flags;
   c->cur ^= 1;
   c->host_steps += 1;
   return GRP_OK;
@@ -589,6 +605,7 @@ int grp_create(grp_ctx** out, const grp_problem* p)
       p->source == GRP_SOURCE_NONE && (p->M == 2 || p->M == 4)) {
     c->hard_cap = hard_list_cap(c->nif);
     AL(hard_tr, (long long)hard_doubles_per_slot(p->M) * c->hard_cap) AL(hard_idx, c->hard_cap) AL(hard_count, 3)
+    AL(gadm[0], c->nif) AL(gadm[1], c->nif)
     if ((e = cudaMemset(c->hard_count, 0, 3 * sizeof(unsigned))) != cudaSuccess) {
       free_all(c); delete c; return cuda_fail(e, "cudaMemset hard_count");
     }
@@ -631,6 +648,7 @@ int grp_set_initial(grp_ctx* c, const double* averages, const double* lim_minus,
   CK(cudaSetDevice(c->p.device));
   const cudaMemcpyKind k = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   cudaStream_t s = c->stream;
+  c->adm_valid = false;
   c->cur = 0;
   CK(cudaMemcpyAsync(c->avg[0], averages, sizeof(double) * c->C * c->ncell, k, s));
   if (!lim_plus) {
@@ -788,12 +806,14 @@ int capture_graph(grp_ctx* c, int steps, double t_end, grp_ctx::Graph& out)
   out = grp_ctx::Graph();
   out.start_cur = c->cur;
   out.smax_ready = c->smax_ready;
+  out.adm_valid = c->adm_valid;
   out.t_end_bits = bits_of(t_end);
   out.steps = steps;
   const int cur0 = c->cur;
   const long long launches0 = c->launches;
   const size_t ev0 = c->ev_pending.size();
   const bool smax0 = c->smax_ready;
+  const bool adm0 = c->adm_valid;
   cudaStream_t user = c->stream;
   CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   c->stream = c->cap_stream;
@@ -807,6 +827,8 @@ int capture_graph(grp_ctx* c, int steps, double t_end, grp_ctx::Graph& out)
   c->stream = user;
   c->capturing = false;
   out.launches = c->launches - launches0;
+  out.adm_end = c->adm_valid;
+  c->adm_valid = adm0;
   out.cur_end = c->cur;
   c->host_steps = hs0;
   // the timing events recorded during capture become nodes of the graph
@@ -848,7 +870,8 @@ int replay_graph(grp_ctx* c, double t_end)
   const unsigned long long tb = bits_of(t_end);
   grp_ctx::Graph* G = nullptr;
   for (auto& g : c->graphs)
-    if (g.start_cur == c->cur && g.smax_ready == c->smax_ready && g.t_end_bits == tb && g.steps == c->graph_steps)
+    if (g.start_cur == c->cur && g.smax_ready == c->smax_ready && g.adm_valid == c->adm_valid &&
+        g.t_end_bits == tb && g.steps == c->graph_steps)
       G = &g;
   if (!G) {
     if (c->graphs.size() >= 8) drop_graphs(c);      // t_end changed repeatedly: start over
@@ -870,6 +893,7 @@ int replay_graph(grp_ctx* c, double t_end)
   CK(cudaGraphLaunch(G->x, c->stream));
   c->launches += G->launches;
   c->cur = G->cur_end;
+  c->adm_valid = G->adm_end;
   c->host_steps += G->steps;
   if (launch_form(c) == GRP_LAUNCH_SPLIT) c->smax_ready = true;
   else c->smax_ready = false;

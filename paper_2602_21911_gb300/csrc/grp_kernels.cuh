@@ -74,6 +74,13 @@ struct StepArgs {
   // solved in a second pass with dense warps; hard_cap = 0 defers nothing
   double* hard_tr = nullptr;         // [2 C (M+1)][hard_cap]: tL then tR, coefficient-major
   long long* hard_idx = nullptr;     // [hard_cap] interface
+  // admissibility of the interface data (Euler, flat form at degrees 2 and 4):
+  // adm_in[j] = 1 when the current datum at j is admissible (null: test the
+  // data), adm_out[j] written with every new datum (null: not kept).  Each
+  // datum is tested once, where it is written, instead of twice, as the edge
+  // value of the two cells it bounds.
+  const unsigned char* adm_in = nullptr;   // [nif]
+  unsigned char* adm_out = nullptr;        // [nif]
   unsigned* hard_count = nullptr;    // [3]: interfaces offered this step, blocks of k_flux_hard done,
                                      //   interfaces taken by k_flux_hard
   int hard_cap = 0;
@@ -364,10 +371,26 @@ static __device__ int first_order(const StepArgs& a, long long c0, int N, int bc
   return ST_OK;
 }
 
+// The admissibility of one or two conserved states as a flag, out of line:
+// the flux kernels call these only where no flag was kept (the first step
+// after new data, a truncated series, a first-order datum), and a call is a
+// branch the compiler cannot turn into predicated FP64 instructions that every
+// lane would issue.
+static __device__ __noinline__ unsigned char adm_flag(double g, double r, double m, double E)
+{
+  return admissible(g, r, m, E) ? 1 : 0;
+}
+static __device__ __noinline__ bool adm_pair(double g, double r0, double m0, double E0, double r1, double m1, double E1)
+{
+  return admissible(g, r0, m0, E0) && admissible(g, r1, m1, E1);
+}
+
 // ------------------------------------------------------------------ k_flux
 // Taylor coefficients of cell `cell`'s reconstruction at its left (em) and
 // right (ep) edge, all components; fb: the degree-0 fallback was taken.
-template <int SYS, int M, bool NL>
+// FLAGS: the kernel keeps admissibility flags of the interface data (read
+// when a.adm_in is set, else the data are tested out of line).
+template <int SYS, int M, bool NL, bool FLAGS = false>
 __device__ __forceinline__ void cell_edges(const StepArgs& a, long long c0, long long i0, int N, int bc, int cell,
                                            double em[][M + 1], double ep[][M + 1], bool& fb)
 {
@@ -392,8 +415,15 @@ __device__ __forceinline__ void cell_edges(const StepArgs& a, long long c0, long
       gr[c] = G[jr];
       grprec_coeffs<M>(qm, q0[c], qp, gl[c], gr[c], b[c]);
     }
-    fb = SYS == SYS_EULER && (!admissible(a.ph.gamma, gl[0], gl[1], gl[2]) ||
-                              !admissible(a.ph.gamma, gr[0], gr[1], gr[2]));
+    fb = false;
+    if (SYS == SYS_EULER) {
+      if (!FLAGS)
+        fb = !admissible(a.ph.gamma, gl[0], gl[1], gl[2]) || !admissible(a.ph.gamma, gr[0], gr[1], gr[2]);
+      else if (a.adm_in)
+        fb = !(a.adm_in[i0 + jl] & a.adm_in[i0 + jr]);
+      else
+        fb = !adm_pair(a.ph.gamma, gl[0], gl[1], gl[2], gr[0], gr[1], gr[2]);
+    }
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       double tm[M + 1], tp[M + 1];
@@ -470,6 +500,9 @@ __device__ __forceinline__ void grp_at(const StepArgs& a, long long gj, int d, l
     bool trunc = false;
     RSInfo info;
     int rs_st = grp_euler<M, G75, SRC>(a.ph, nu, tL, tR, F, gnew, iters, trunc, &info, hsrc, lead);
+    // an untruncated series passed the admissibility test at tau = dt: its
+    // datum is admissible without a second test
+    const bool adm_known = rs_st == ST_OK && !trunc;
     st[2] = 1;
     st[3] = trunc ? 1u : 0u;
     st[6] = info.guess == 1 ? 1u : 0u;
@@ -487,6 +520,11 @@ __device__ __forceinline__ void grp_at(const StepArgs& a, long long gj, int d, l
     }
     st[0] = (unsigned)iters;
     st[1] = (unsigned)iters;
+    if (a.adm_out) {
+      unsigned char f = 1;
+      if (!adm_known) f = adm_flag(a.ph.gamma, gnew[0], gnew[1], gnew[2]);
+      a.adm_out[gj] = f;
+    }
   }
 #pragma unroll
   for (int c = 0; c < C; ++c) {
@@ -582,7 +620,7 @@ __device__ __forceinline__ void flux_warp(const StepArgs& a, long long gbase, lo
     bc = a.bc[d];
     active = a.ds[d].active != 0;
     cl = bc == 0 ? (j == 0 ? N - 1 : j - 1) : j - 1;
-    if (active && cl >= 0) cell_edges<SYS, M, NL>(a, c0, i0, N, bc, cl, em, ep, fb);
+    if (active && cl >= 0) cell_edges<SYS, M, NL, DEFER>(a, c0, i0, N, bc, cl, em, ep, fb);
     // each cell is the left cell of exactly one interface (lane 31 supplies a
     // reconstruction only; its interface is the next warp's lane 0)
     if (SRC && active && cl >= 0 && lane < 31) cell_source<SYS, M>(a, c0, i0, N, bc, cl, fb, d);
@@ -599,6 +637,8 @@ __device__ __forceinline__ void flux_warp(const StepArgs& a, long long gbase, lo
     if (!active) {
 #pragma unroll
       for (int c = 0; c < C; ++c) a.ifc_new[c * a.nif + gj] = a.ifc[c * a.nif + gj];
+      if (SYS == SYS_EULER && a.adm_out)
+        a.adm_out[gj] = a.adm_in ? a.adm_in[gj] : adm_flag(a.ph.gamma, a.ifc[gj], a.ifc[a.nif + gj], a.ifc[2 * a.nif + gj]);
     } else {
       // both traces by register moves (ghost states at transmissive ends), so
       // that the lanes of a warp reach the one GRP below together
@@ -619,7 +659,7 @@ __device__ __forceinline__ void flux_warp(const StepArgs& a, long long gbase, lo
         // last interface of a periodic domain: its right cell is cell N - 1
         double tx[C][M + 1];
         bool fb2;
-        cell_edges<SYS, M, NL>(a, c0, i0, N, bc, N - 1, rm, tx, fb2);
+        cell_edges<SYS, M, NL, DEFER>(a, c0, i0, N, bc, N - 1, rm, tx, fb2);
       }
       const bool ghost_r = j >= jlast && bc != 0;
 #pragma unroll
@@ -936,6 +976,7 @@ __device__ __forceinline__ void repair_iface(const StepArgs& a, int pass, long l
     a.flux[c * a.nif + gj] = F[c];
     a.ifc_new[c * a.nif + gj] = Q0[c];
   }
+  if (a.adm_out) a.adm_out[gj] = admissible(a.ph.gamma, Q0[0], Q0[1], Q0[2]) ? 1 : 0;
   a.low[gj] = (unsigned char)(2 + pass);
   a.ilist[atomicAdd(a.lcount + MAX_REPAIR + 1 + pass, 1)] = (int)gj;
 }
