@@ -77,3 +77,45 @@ def test_flat_form_with_graphs_equals_direct_launches(M):
         s.close()
     for x, y in zip(out[0], out[1]):
         assert np.array_equal(x, y)
+
+
+def test_admissibility_flags_across_forms_restarts_and_graphs():
+    """The flat flux kernel keeps the interface data's admissibility flags from
+    one step to the next; other launch forms and new initial data invalidate
+    them.  Switching forms mid-run, restarting from new data and replaying
+    graphs of a length that does not divide the step count must give the
+    oracle's results (and a restart the same bits as a fresh solver)."""
+    from paper_2602_21911_gb300 import grprec
+    from parity import oracle_run, rel_diff, rel_diff_iface
+    ids = np.arange(0, 65536, 151)[:300]
+    prob, avg, lm, lp = I.batched(M=2, domains=ids)
+    s = grprec.Solver(prob)
+    s.set_graph(4)
+    s.set_initial(avg, lm, lp)
+    s.set_launch(grprec.GRP_LAUNCH_FLAT)
+    s.step(7)
+    s.set_launch(grprec.GRP_LAUNCH_FUSED, 256, 2048, 1)
+    s.step(5)
+    s.set_launch(grprec.GRP_LAUNCH_FLAT)
+    s.step(9)
+    a, g, t = s.get_state()
+    S = oracle_run(prob, avg, lm, lp, 21, np.inf)
+    ok = S.status == 0
+    assert rel_diff(a, S.avg, prob)[ok].max() <= DISC_TOL
+    assert rel_diff_iface(g, S.iface, prob)[ok].max() <= DISC_TOL
+    # a restart from new data (every conserved variable scaled by 1.01: the
+    # same velocities, admissible), then steps: the same bits as a fresh solver
+    prob2, avg2, lm2, lp2 = prob, 1.01 * avg, 1.01 * lm, 1.01 * lp
+    s.set_initial(avg2, lm2, lp2)
+    s.step(11)
+    r1 = s.get_state()
+    s.close()
+    f = grprec.Solver(prob2)
+    f.set_graph(4)
+    f.set_launch(grprec.GRP_LAUNCH_FLAT)
+    f.set_initial(avg2, lm2, lp2)
+    f.step(11)
+    r2 = f.get_state()
+    f.close()
+    for x, y in zip(r1, r2):
+        assert np.array_equal(x, y)
