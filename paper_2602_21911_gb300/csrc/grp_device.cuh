@@ -1163,17 +1163,20 @@ GRP_HD __forceinline__ void ck_euler(double gm1, double rho[Tri<M>::N], double m
   }
 }
 
+// Node a of the G-point Gauss-Legendre rule on [0, 1].
+GRP_HD __forceinline__ double gauss_node(int G, int a)
+{
+  if (G == 1) return 0.5;
+  if (G == 2) return a == 0 ? 0.5 - 0.28867513459481288225 : 0.5 + 0.28867513459481288225;
+  return a == 0 ? 0.5 - 0.38729833462074168852 : (a == 1 ? 0.5 : 0.5 + 0.38729833462074168852);
+}
+
 // Gauss-Legendre rule with G = ceil((M+1)/2) points on [0, 1]: nodes
 // (1 + s)/2 and weights summing to 1.
 template <int M>
 struct Gauss {
   static constexpr int G = (M + 2) / 2;
-  GRP_HD static __forceinline__ double node(int a)
-  {
-    if (G == 1) return 0.5;
-    if (G == 2) return a == 0 ? 0.5 - 0.28867513459481288225 : 0.5 + 0.28867513459481288225;
-    return a == 0 ? 0.5 - 0.38729833462074168852 : (a == 1 ? 0.5 : 0.5 + 0.38729833462074168852);
-  }
+  GRP_HD static __forceinline__ double node(int a) { return gauss_node(G, a); }
   GRP_HD static __forceinline__ double weight(int a)
   {
     if (G == 1) return 1.0;
@@ -1270,7 +1273,7 @@ template <int M, bool G75, bool SRC = false>
 GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[3][M + 1],
                                      const double tR[3][M + 1], double F[3], double gnew[3], int& iters,
                                      bool& truncated, RSInfo* info = nullptr, double hs = 0.0,
-                                     const Lead* lead = nullptr)
+                                     const Lead* lead = nullptr, const double* tg = nullptr)
 {
   const double g = ph.gamma;
   const double QL[3] = {tL[0][0], tL[1][0], tL[2][0]}, QR[3] = {tR[0][0], tR[1][0], tR[2][0]};
@@ -1323,7 +1326,8 @@ GRP_HD __forceinline__ int grp_euler(const Phys& ph, double nu, const double tL[
   bool ok = true;
 #pragma unroll
   for (int al = 0; al <= G; ++al) {
-    const double Tn = al < G ? nu * Gauss<M>::node(al) : nu;
+    // tg: nu x the nodes, formed once per domain (the same products)
+    const double Tn = al < G ? (tg ? tg[al] : nu * Gauss<M>::node(al)) : nu;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       double v = s[c][M];

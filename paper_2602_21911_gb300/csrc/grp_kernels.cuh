@@ -25,6 +25,7 @@ constexpr double DMP_REL = 1e-2; // relaxation of the discrete maximum principle
 struct DomStep {
   double dt, nu, dt_cfl;             // dt (clipped at t_end), dt / dx, the CFL dt kept for dt_hold
   int active, last;                  // the domain steps; this step reaches t_end
+  double tg[3];                      // nu x the Gauss nodes of the flux time integral (degree M: (M+2)/2 nodes)
 };
 
 struct StepArgs {
@@ -144,7 +145,7 @@ __device__ __forceinline__ void warp_flux_stats(unsigned long long* stats, int d
 // Time step of domain d from its words (S_max complete): one division.
 __device__ __forceinline__ void compute_domain_step(const StepArgs& a, int d)
 {
-  DomStep r{0.0, 0.0, 0.0, 0, 0};
+  DomStep r{0.0, 0.0, 0.0, 0, 0, {0.0, 0.0, 0.0}};
   const double t = a.t[d];
   if (a.status[d] == ST_OK && t < a.t_end) {
     const double dtp = a.dt_prev[d];
@@ -160,6 +161,9 @@ __device__ __forceinline__ void compute_domain_step(const StepArgs& a, int d)
     r.dt = dt;
     r.dt_cfl = dt_cfl;
     r.nu = __ddiv_rn(dt, a.dx[d]);
+    // the GRP's Gauss times, formed once per domain instead of per interface
+    const int G = (a.M + 2) / 2;
+    for (int al = 0; al < G; ++al) r.tg[al] = __dmul_rn(r.nu, gauss_node(G, al));
     r.active = 1;
   }
   a.ds[d] = r;
@@ -499,7 +503,7 @@ __device__ __forceinline__ void grp_at(const StepArgs& a, long long gj, int d, l
     int iters = 0;
     bool trunc = false;
     RSInfo info;
-    int rs_st = grp_euler<M, G75, SRC>(a.ph, nu, tL, tR, F, gnew, iters, trunc, &info, hsrc, lead);
+    int rs_st = grp_euler<M, G75, SRC>(a.ph, nu, tL, tR, F, gnew, iters, trunc, &info, hsrc, lead, a.ds[d].tg);
     // an untruncated series passed the admissibility test at tau = dt: its
     // datum is admissible without a second test
     const bool adm_known = rs_st == ST_OK && !trunc;
